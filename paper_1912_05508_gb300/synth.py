@@ -1,0 +1,159 @@
+"""Seeded synthetic inputs shaped like the paper's least-squares workloads.
+
+This module builds test and benchmark matrices only; it contains none of the
+factorization or solver arithmetic, and both the CPU oracle tests and the
+GPU path draw their inputs from it.
+
+Matrix families follow the paper's experiment section (Sec. 4.2): i.i.d.
+uniform (0,1) and (-1,1), standard normal, and A = U diag(sigma) V^T with a
+prescribed condition number and a geometric, arithmetic or clustered singular
+value distribution (the paper used MAGMA's generator, which is not available;
+these are rebuilt from the definitions).
+
+Conventions: every matrix is returned column-major-ready as a numpy array of
+shape (m, n); callers that need Fortran order use ``np.asfortranarray``.
+A is rounded to FP32 (the problem is defined for the stored FP32 A); b and
+x_true are FP64.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+SPECTRA = ("geometric", "arithmetic", "cluster")
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.PCG64(seed))
+
+
+def haar_orthonormal(rng: np.random.Generator, m: int, n: int) -> np.ndarray:
+    """m x n matrix with Haar-distributed orthonormal columns (FP64).
+
+    Q factor of an m x n standard normal matrix with its columns multiplied by
+    sign(diag R), which makes the distribution Haar (Mezzadri 2007).
+    """
+    g = rng.standard_normal((m, n))
+    q, r = np.linalg.qr(g, mode="reduced")
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    return q * d
+
+
+def spectrum(kind: str, n: int, kappa: float) -> np.ndarray:
+    """Singular values sigma_1 >= ... >= sigma_n with sigma_1 / sigma_n = kappa.
+
+    geometric : log sigma_i evenly spaced from 0 to -log kappa (matrix type 3 of Sec. 4.2)
+    arithmetic: sigma_i evenly spaced from 1 to 1/kappa (type 4)
+    cluster   : all ones except the smallest, which is 1/kappa (type 5)
+    """
+    if n == 1:
+        return np.ones(1)
+    i = np.arange(n, dtype=np.float64)
+    if kind == "geometric":
+        return kappa ** (-i / (n - 1))
+    if kind == "arithmetic":
+        return 1.0 - i * (1.0 - 1.0 / kappa) / (n - 1)
+    if kind == "cluster":
+        s = np.ones(n)
+        s[-1] = 1.0 / kappa
+        return s
+    raise ValueError(f"unknown spectrum {kind!r}")
+
+
+@dataclass
+class LLSProblem:
+    A: np.ndarray        # (m, n) float32
+    b: np.ndarray        # (m,) float64
+    x_true: np.ndarray   # (n,) float64, exact LS solution of the FP64 problem before A is rounded
+    sigma: np.ndarray    # singular values used to build A
+    kind: str
+    kappa: float
+    seed: int
+
+
+def svd_lls(m: int, n: int, kind: str = "geometric", kappa: float = 1e3,
+            seed: int = 1, noise: float = 1e-6) -> LLSProblem:
+    """A = U diag(sigma) V^T (Haar U, V), x_true ~ N(0, I), b = A x_true + e.
+
+    e is orthogonal to range(A) with ||e|| = noise * ||A x_true||, so x_true is
+    the exact least-squares solution of the FP64 problem. A is then rounded to
+    FP32; after that rounding x_true is no longer exact (perturbation of order
+    kappa * u32), and exact solutions must come from solving the rounded problem.
+    """
+    rng = rng_for(seed)
+    U = haar_orthonormal(rng, m, n)
+    V = haar_orthonormal(rng, n, n)
+    sig = spectrum(kind, n, kappa)
+    A64 = (U * sig) @ V.T
+    x = rng.standard_normal(n)
+    Ax = A64 @ x
+    b = Ax.copy()
+    if noise > 0.0 and m > n:
+        g = rng.standard_normal(m)
+        w = g - U @ (U.T @ g)
+        w -= U @ (U.T @ w)          # second pass keeps w orthogonal to range(U) to ~1e-16
+        b = Ax + noise * np.linalg.norm(Ax) * w / np.linalg.norm(w)
+    return LLSProblem(A=A64.astype(np.float32), b=b, x_true=x, sigma=sig,
+                      kind=kind, kappa=kappa, seed=seed)
+
+
+def random_dense(m: int, n: int, kind: str = "normal", seed: int = 0) -> np.ndarray:
+    """i.i.d. matrices of Sec. 4.2 types 1 and 2: 'uniform01', 'uniform11', 'normal'."""
+    rng = rng_for(seed)
+    if kind == "uniform01":
+        A = rng.random((m, n))
+    elif kind == "uniform11":
+        A = 2.0 * rng.random((m, n)) - 1.0
+    elif kind == "normal":
+        A = rng.standard_normal((m, n))
+    else:
+        raise ValueError(kind)
+    return A.astype(np.float32)
+
+
+def scaled_gaussian(m: int, n: int, seed: int = 11, lo: float = -2.0, hi: float = 2.0,
+                    dtype=np.float32) -> np.ndarray:
+    """N(0,1) entries with column j rescaled to norm 10**U(lo, hi).
+
+    Stresses per-column range handling of the low-precision products.
+    Generated column block by column block to bound host memory.
+    """
+    rng = rng_for(seed)
+    expo = rng.uniform(lo, hi, size=n)
+    A = np.empty((m, n), dtype=dtype, order="F")
+    blk = max(1, min(n, (1 << 26) // max(m, 1)))
+    for j0 in range(0, n, blk):
+        j1 = min(n, j0 + blk)
+        g = rng.standard_normal((m, j1 - j0))
+        g *= (10.0 ** expo[j0:j1]) / np.linalg.norm(g, axis=0)
+        A[:, j0:j1] = g
+    return A
+
+
+def batched_shapes(count: int = 4096, seed: int = 13, m_range=(256, 4096),
+                   n_range=(16, 512), ratio: int = 4, kappa_exp=(1.0, 5.0)):
+    """Rejection-sampled uneven shapes: n ~ U{n_range}, m ~ U{m_range}, kept if m >= ratio*n.
+
+    Returns (ms, ns, kappas) as int32, int32, float64 arrays.
+    """
+    rng = rng_for(seed)
+    ms, ns = [], []
+    while len(ms) < count:
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        if m >= ratio * n:
+            ms.append(m)
+            ns.append(n)
+    kap = 10.0 ** rng.uniform(kappa_exp[0], kappa_exp[1], size=count)
+    return np.array(ms, np.int32), np.array(ns, np.int32), kap
+
+
+def upper_triangular_test(n: int, seed: int = 0, diag_lo: float = 0.5) -> np.ndarray:
+    """Well-conditioned upper-triangular matrix with positive diagonal (FP64)."""
+    rng = rng_for(seed)
+    T = np.triu(rng.standard_normal((n, n))) / math.sqrt(n)
+    T[np.diag_indices(n)] = diag_lo + rng.random(n)
+    return T
