@@ -1,0 +1,126 @@
+/*
+ * lls_gb300.h -- C ABI of the GB300 (sm_103a) mixed-precision QR and least-squares library.
+ *
+ * Problem (Eq. opt:lls, Sec. 2.2): x* = argmin_x ||A x - b||_2 for a full-column-rank
+ * A (m x n, m >= n). Method: a recursive Gram-Schmidt QR (RGSQRF, Alg. 2, Eq. recqr)
+ * whose two products per recursion step run on the tensor cores in FP16 / BF16 with
+ * FP32 accumulation, a communication-avoiding tall-skinny panel (Eq. caqr) with CGS2
+ * leaves, and the resulting R used as a right preconditioner for CGLS (Alg. 5) or
+ * LSQR, which recovers FP32- or FP64-level accuracy (Sec. 3.2.3).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *  - Matrix and vector pointers are DEVICE pointers owned by the caller, unless a
+ *    parameter says "host". The library never allocates device memory: scratch comes
+ *    from the caller's workspace, sized by the matching *_workspace_size query.
+ *    Workspace pointers must be 256-byte aligned.
+ *  - Work is enqueued on `stream` (0 = legacy default stream). Inputs must not be
+ *    modified and outputs not read until the stream reaches that point.
+ *  - Return value is a status code (lls_status); no C++ exception crosses the ABI.
+ *    Argument errors are detected before anything is enqueued.
+ *  - Calls are thread-safe as long as concurrent calls use distinct workspaces.
+ */
+#ifndef LLS_GB300_H
+#define LLS_GB300_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. Negative = error (outputs undefined), 0 = success, positive = warning. */
+typedef enum {
+    LLS_OK = 0,
+    LLS_NOT_CONVERGED = 1,     /* iteration limit reached; x holds the last iterate, info filled */
+    LLS_ERR_ARG = -1,          /* bad size, leading dimension, null pointer or option value */
+    LLS_ERR_SINGULAR = -2,     /* R has a zero or non-finite diagonal entry (rank deficient / inf / nan input) */
+    LLS_ERR_CUDA = -3,         /* a CUDA runtime or driver call failed */
+    LLS_ERR_WORKSPACE = -4,    /* workspace too small or misaligned */
+    LLS_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired (the kernel returned early) */
+    LLS_ERR_UNSUPPORTED = -6   /* valid but unimplemented option combination */
+} lls_status;
+
+/* Precision of the two tensor-core products of each recursion step (Alg. 2 lines 8-9).
+ * FP16 is the paper's choice (Sec. 2.1); BF16 trades resolution for range; FP32 runs the
+ * products on the FP32 units (no rounding of the inputs), a reference mode. */
+typedef enum { LLS_PREC_FP16 = 0, LLS_PREC_BF16 = 1, LLS_PREC_FP32 = 3 } lls_gemm_prec;
+
+/* Accuracy target of the Krylov refinement (Sec. 3.2.3). */
+typedef enum { LLS_TARGET_FP32 = 0, LLS_TARGET_FP64 = 1 } lls_target;
+
+/* Krylov method: CGLS (Alg. 5) or LSQR (Paige-Saunders; named in Sec. 5). */
+typedef enum { LLS_KRYLOV_CGLS = 0, LLS_KRYLOV_LSQR = 1 } lls_krylov;
+
+typedef struct {
+    int gemm_prec;     /* lls_gemm_prec, default LLS_PREC_FP16 */
+    int target;        /* lls_target, default LLS_TARGET_FP64 */
+    double tol;        /* stop tolerance; <= 0 selects the target's default:
+                          FP64: eta_est = ||R^-T A^T r|| / (||A||_F ||x||) <= 1e-12
+                          FP32: fwd_est = ||R^-1||_F ||R^-T A^T r|| / ||x|| <= 1e-6 */
+    int max_iter;      /* iteration cap, default 200 (the paper's cap, Sec. 4.2.3) */
+    int panel_width;   /* recursion leaf width b (columns per panel), 0 = default 32 (Sec. 3.1.3); 1..32 */
+    int krylov;        /* lls_krylov, default CGLS */
+    int leaf_rows;     /* rows per CAQR leaf block, 0 = default 256 (Sec. 3.1.3); 64..256, multiple of 32 */
+} lls_options;
+
+typedef struct {
+    int status;        /* lls_status of the call */
+    int iters;         /* Krylov iterations performed */
+    double eta;        /* eta_est of the returned x, from a freshly computed residual b - A x */
+    double fwd_est;    /* ||R^-1||_F ||R^-T A^T r|| / ||x||: estimated relative forward error bound */
+    double res_norm;   /* ||b - A x||_2 */
+    double atr_norm;   /* ||A^T (b - A x)||_2 */
+    double anorm_f;    /* ||A||_F */
+    double xnorm;      /* ||x||_2 */
+    float qr_ms;       /* device time of the factorization (and preconditioner set-up) */
+    float krylov_ms;   /* device time of the Krylov iteration */
+} lls_info;
+
+/* Fill *opts with the defaults listed above. */
+void lls_default_options(lls_options* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* lls_status_string(int status);
+
+/* ---------------------------------------------------------------------------
+ * QR factorization (Alg. 2 + Eq. caqr): A = Q R, Q m x n with orthonormal columns
+ * (to the GEMM precision), R n x n upper triangular with positive diagonal.
+ *
+ *  A  [in]  m x n FP32, lda >= m. Not modified.
+ *  Q  [out] m x n FP32, ldq >= m, or NULL when Q is not wanted.
+ *  R  [out] n x n FP32, ldr >= n; the strictly lower triangle is set to zero.
+ *  ws [in]  workspace of ws_bytes >= qr_factor_workspace_size(m, n, opts), 256-B aligned.
+ *  opts     may be NULL (defaults). Only gemm_prec, panel_width and leaf_rows are used.
+ * Errors: LLS_ERR_ARG (n < 1, m < n, ld too small, null A/R/ws), LLS_ERR_WORKSPACE,
+ *         LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA. Rank deficiency is not an error here:
+ *         it shows up as a zero diagonal entry of R.
+ * -------------------------------------------------------------------------- */
+size_t qr_factor_workspace_size(int m, int n, const lls_options* opts);
+int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
+              void* ws, size_t ws_bytes, const lls_options* opts, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Least-squares solve (Alg. 5 with the QR above as right preconditioner).
+ *
+ *  A     [in]  m x n FP32, lda >= m; the problem is defined for these FP32 values.
+ *  b     [in]  m FP64.
+ *  x     [out] n FP64 (the FP32 target also returns FP64).
+ *  R_out [out] n x n FP32 (ldr >= n) receives the preconditioner R, or NULL.
+ *  info  [out] HOST pointer or NULL. When non-NULL the call synchronizes `stream`
+ *              before returning and fills *info; when NULL the call is fully
+ *              asynchronous (and can be captured in a CUDA graph) and the status
+ *              returned covers argument checks and launches only.
+ * Errors: as qr_factor, plus LLS_ERR_SINGULAR, LLS_ERR_TIMEOUT (reported only through
+ *         info), LLS_NOT_CONVERGED (warning).
+ * -------------------------------------------------------------------------- */
+size_t lls_solve_workspace_size(int m, int n, const lls_options* opts);
+int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
+              float* R_out, int ldr, void* ws, size_t ws_bytes, const lls_options* opts,
+              lls_info* info, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LLS_GB300_H */

@@ -1,0 +1,182 @@
+// Shared device/host helpers for the GB300 least-squares library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lls_gb300.h"
+
+#define LLS_CUDA_TRY(expr)                                  \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return LLS_ERR_CUDA;          \
+    } while (0)
+
+#define LLS_TRY(expr)                                        \
+    do {                                                     \
+        int _s = (expr);                                     \
+        if (_s != LLS_OK) return _s;                         \
+    } while (0)
+
+namespace lls {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Device error word values (written by kernels that hit a bounded-wait limit or bad data).
+enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2 };
+
+// Maximum wait of any device-side spin before it gives up, in nanoseconds.
+constexpr unsigned long long kSpinLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with two FP32 numbers. GB300's FP64 rate is
+// about 1/70 of its FP32 rate, so the FP64-accurate Krylov products use error-free
+// transformations on FP32 instead: TwoProduct via FMA (exact a*b = p + e) and Knuth's
+// TwoSum (exact a + b = s + e). The _rn intrinsics keep the compiler from contracting or
+// reassociating the steps.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Compensated dot-product step (Ogita, Rump, Oishi 2005, "Dot2"): accumulates
+// a * (th + tl) into the running sum s with the rounding errors collected in c.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float a, float th, float tl) {
+    float p = __fmul_rn(a, th);
+    float e = __fmaf_rn(a, th, -p);       // exact: a*th = p + e
+    e = __fmaf_rn(a, tl, e);              // low part of t, product rounded once (~u^2 relative)
+    float s2, e2;
+    two_sum(s, p, s2, e2);
+    s = s2;
+    c = __fadd_rn(c, __fadd_rn(e, e2));
+}
+
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
+
+__device__ __forceinline__ double join_df(float s, float c) {
+    return __dadd_rn((double)s, (double)c);
+}
+
+// ---------------------------------------------------------------------------------------
+// Low-precision element types of the tensor-core products.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct LowPrec;
+template <> struct LowPrec<__half> {
+    static __device__ __forceinline__ __half from_float(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
+};
+template <> struct LowPrec<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 from_float(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+};
+template <> struct LowPrec<float> {
+    static __device__ __forceinline__ float from_float(float x) { return x; }
+    static __device__ __forceinline__ float to_float(float x) { return x; }
+};
+
+// Column scale exponent e with max|x| * 2^e in [2^14, 2^15) (FP16 target range, largest
+// finite FP16 is 65504). Zero (or non-finite) maximum gives 0; clamped to [-100, 100].
+__device__ __forceinline__ int fp16_scale_exponent(float mx) {
+    if (!(mx > 0.0f) || !isfinite(mx)) return 0;
+    int ex;
+    frexpf(mx, &ex);                      // mx = f * 2^ex, f in [0.5, 1)
+    int e = 15 - ex;
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// 2^e as an FP32 number for e in [-126, 127] (exponent field only): multiplying by it is exact
+// whenever the product is a normal number.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// ---------------------------------------------------------------------------------------
+// Warp reductions.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFullMask, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFullMask, v, o));
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier for cooperative (co-resident) launches. Sense by generation counter;
+// the wait is bounded by kSpinLimitNs, after which the error word is set and the caller
+// must return. `bar[0]` = arrival count, `bar[1]` = generation.
+// Returns false when the barrier timed out or an error was already flagged.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            while (*gen == g) {
+                if (*(volatile int*)err != DEV_OK) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                    atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)err != DEV_OK) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace lls
+
+// Host-side helpers shared by the translation units.
+namespace lls {
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Bump allocator over the caller's workspace (all offsets 256-B aligned).
+struct WsArena {
+    char* base;
+    size_t cap;
+    size_t off;
+    bool ok;
+    WsArena(void* p, size_t c) : base((char*)p), cap(c), off(0), ok(true) {}
+    template <typename T> T* take(size_t count) {
+        size_t bytes = align_up(count * sizeof(T), 256);
+        if (off + bytes > cap) { ok = false; off += bytes; return nullptr; }
+        T* r = base ? (T*)(base + off) : nullptr;
+        off += bytes;
+        return r;
+    }
+};
+
+}  // namespace lls

@@ -1,0 +1,221 @@
+// FP32-accumulating GEMMs on the CUDA cores (SIMT), column-major.
+//
+// Used for (a) the FP32 reference precision of the recursion's products (no input
+// rounding), (b) the R^{-1} recursion M12 = -M11 R12 M22 of the preconditioner set-up,
+// and (c) the split-K reduction / epilogues shared with the tensor-core kernels.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lls {
+
+constexpr int kSB = 64;      // output tile (square)
+constexpr int kSK = 16;      // K step
+constexpr int kSThreads = 256;
+
+enum SimtEpi { EPI_PARTIAL = 0, EPI_AXPBY = 1, EPI_UPDATE = 2 };
+
+// op(A)[i,k] = TA ? A[k + i*lda] : A[i + k*lda];  op(B)[k,j] = TB ? B[j + k*ldb] : B[k + j*ldb]
+template <typename TIA, typename TIB, bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(kSThreads)
+gemm_simt_kernel(int M, int N, int K, int kchunk, const TIA* __restrict__ A, int lda,
+                 const TIB* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                 float alpha, float beta, const int* __restrict__ fexp) {
+    __shared__ float As[kSK][kSB + 4];
+    __shared__ float Bs[kSK][kSB + 4];
+    const int t = threadIdx.x;
+    const int i0 = blockIdx.x * kSB, j0 = blockIdx.y * kSB;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int ti = (t % 16) * 4, tj = (t / 16) * 4;
+    float acc[4][4] = {};
+    for (int k0 = kb; k0 < ke; k0 += kSK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = t + r * kSThreads;            // 0..1023
+            int ii, kk;
+            if (TA) { kk = idx % kSK; ii = idx / kSK; } else { ii = idx % kSB; kk = idx / kSB; }
+            int gi = i0 + ii, gk = k0 + kk;
+            float v = 0.f;
+            if (gi < M && gk < ke)
+                v = LowPrec<TIA>::to_float(TA ? A[(size_t)gk + (size_t)gi * lda] : A[(size_t)gi + (size_t)gk * lda]);
+            As[kk][ii] = v;
+            int jj;
+            if (TB) { jj = idx % kSB; kk = idx / kSB; } else { kk = idx % kSK; jj = idx / kSK; }
+            int gj = j0 + jj;
+            gk = k0 + kk;
+            float w = 0.f;
+            if (gj < N && gk < ke)
+                w = LowPrec<TIB>::to_float(TB ? B[(size_t)gj + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gj * ldb]);
+            Bs[kk][jj] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kSK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[kk][ti + u]; b[u] = Bs[kk][tj + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        int j = j0 + tj + v;
+        if (j >= N) continue;
+        float fs = (EPI == EPI_UPDATE && fexp) ? pow2f(-fexp[j]) : 1.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int i = i0 + ti + u;
+            if (i >= M) continue;
+            if (EPI == EPI_PARTIAL) {
+                C[(size_t)blockIdx.z * M * N + (size_t)i + (size_t)j * M] = acc[u][v];
+            } else if (EPI == EPI_AXPBY) {
+                size_t idx = (size_t)i + (size_t)j * ldc;
+                C[idx] = beta == 0.f ? alpha * acc[u][v] : fmaf(alpha, acc[u][v], beta * C[idx]);
+            } else {
+                size_t idx = (size_t)i + (size_t)j * ldc;
+                C[idx] = C[idx] - acc[u][v] * fs;
+            }
+        }
+    }
+}
+
+int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, int lda,
+          const float* B, int ldb, float beta, float* C, int ldc, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return LLS_OK;
+    dim3 grid(ceil_div(M, kSB), ceil_div(N, kSB), 1);
+    int kc = K > 0 ? K : 1;
+#define LLS_SG(TAv, TBv) gemm_simt_kernel<float, float, TAv, TBv, EPI_AXPBY><<<grid, kSThreads, 0, st>>>(M, N, K, kc, A, lda, B, ldb, C, ldc, alpha, beta, nullptr)
+    if (!ta && !tb) LLS_SG(false, false);
+    else if (ta && !tb) LLS_SG(true, false);
+    else if (!ta && tb) LLS_SG(false, true);
+    else LLS_SG(true, true);
+#undef LLS_SG
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Split-K reduction and epilogue of the projection R12 = Q1^T A2 (Alg. 2 line 8):
+// R12[i, j] = (sum_s part[s][i, j]) * 2^-e_j in a fixed order, stored in FP32; then the
+// column exponent f_j of R12 and R12l = round(R12 * 2^f_j) for the update product.
+// One CTA per column j.
+// ---------------------------------------------------------------------------------------
+template <typename TL>
+__global__ void __launch_bounds__(256)
+proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
+                   const int* __restrict__ e, float* __restrict__ R12, int ldr,
+                   TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int want_scale) {
+    const int j = blockIdx.x;
+    const float se = e ? pow2f(-e[j]) : 1.f;
+    const size_t plane = (size_t)w1 * w2;
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < w1; i += 256) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * plane + (size_t)i + (size_t)j * w1];
+        s *= se;
+        R12[(size_t)i + (size_t)j * ldr] = s;
+        mx = fmaxf(mx, fabsf(s));
+    }
+    if (!R12l) return;
+    __shared__ float s_red[8];
+    __shared__ int s_f;
+    mx = warp_max_f(mx);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t = fmaxf(t, s_red[w]);
+        s_f = want_scale ? fp16_scale_exponent(t) : 0;
+        f[j] = s_f;
+    }
+    __syncthreads();
+    const float sc = pow2f(s_f);
+    for (int i = threadIdx.x; i < w1; i += 256)
+        R12l[(size_t)i + (size_t)j * ldrl] = LowPrec<TL>::from_float(R12[(size_t)i + (size_t)j * ldr] * sc);
+}
+
+int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, float* R12, int ldr,
+                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st) {
+    if (lowp == 0)
+        proj_reduce_kernel<__half><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, R12, ldr, (__half*)R12l, ldrl, f, 1);
+    else if (lowp == 1)
+        proj_reduce_kernel<__nv_bfloat16><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, R12, ldr, (__nv_bfloat16*)R12l, ldrl, f, 0);
+    else
+        proj_reduce_kernel<float><<<w2, 256, 0, st>>>(part, splits, w1, w2, nullptr, R12, ldr, (float*)nullptr, 0, f, 0);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+// Number of K splits for a projection of M = w1, N = w2, K = m: enough CTAs to fill the GPU.
+int proj_splits_simt(int m, int w1, int w2) {
+    int tiles = ceil_div(w1, kSB) * ceil_div(w2, kSB);
+    int want = ceil_div(4 * 152, tiles);
+    int maxs = ceil_div(m, 512);
+    int s = want < maxs ? want : maxs;
+    return s < 1 ? 1 : s;
+}
+
+// SIMT projection / update for the FP32 reference precision (inputs are the FP32 matrices).
+int simt_projection_f32(const float* Q1, const float* A2, int ldw, int m, int w1, int w2,
+                        float* R12, int ldr, float* part, cudaStream_t st) {
+    int splits = proj_splits_simt(m, w1, w2);
+    int kc = align_up((size_t)ceil_div(m, splits), kSK);
+    splits = ceil_div(m, kc);
+    dim3 grid(ceil_div(w1, kSB), ceil_div(w2, kSB), splits);
+    gemm_simt_kernel<float, float, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
+        w1, w2, m, kc, Q1, ldw, A2, ldw, part, 0, 1.f, 0.f, nullptr);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return proj_reduce(part, splits, w1, w2, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st);
+}
+
+int simt_update_f32(const float* Q1, int ldw, const float* R12, int ldr, float* A2, int m, int w1,
+                    int w2, cudaStream_t st) {
+    dim3 grid(ceil_div(m, kSB), ceil_div(w2, kSB), 1);
+    gemm_simt_kernel<float, float, false, false, EPI_UPDATE><<<grid, kSThreads, 0, st>>>(
+        m, w2, w1, w1, Q1, ldw, R12, ldr, A2, ldw, 1.f, 0.f, nullptr);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+// Low-precision operands on the CUDA cores (products of FP16/BF16 values are exact in FP32,
+// accumulation in FP32 as on the tensor cores).
+template <typename TL>
+static int simt_lowp_projection(const ProjCall& c, cudaStream_t st) {
+    int splits = proj_splits_simt(c.m, c.w1, c.w2);
+    int kc = align_up((size_t)ceil_div(c.m, splits), kSK);
+    splits = ceil_div(c.m, kc);
+    if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
+    dim3 grid(ceil_div(c.w1, kSB), ceil_div(c.w2, kSB), splits);
+    gemm_simt_kernel<TL, TL, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
+        c.w1, c.w2, c.m, kc, (const TL*)c.Q1l, c.ldh, (const TL*)c.A2l, c.ldh, c.part, 0, 1.f, 0.f, nullptr);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+}
+
+template <typename TL>
+static int simt_lowp_update(const UpdCall& c, cudaStream_t st) {
+    dim3 grid(ceil_div(c.m, kSB), ceil_div(c.w2, kSB), 1);
+    gemm_simt_kernel<TL, TL, false, false, EPI_UPDATE><<<grid, kSThreads, 0, st>>>(
+        c.m, c.w2, c.w1, c.w1, (const TL*)c.Q1l, c.ldh, (const TL*)c.R12l, c.ldrl, c.A2, c.ldw, 1.f, 0.f, c.f);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+int simt_projection_lowp(const ProjCall& c, cudaStream_t st) {
+    return c.lowp == 0 ? simt_lowp_projection<__half>(c, st) : simt_lowp_projection<__nv_bfloat16>(c, st);
+}
+int simt_update_lowp(const UpdCall& c, cudaStream_t st) {
+    return c.lowp == 0 ? simt_lowp_update<__half>(c, st) : simt_lowp_update<__nv_bfloat16>(c, st);
+}
+
+size_t simt_partial_floats(int m, int w1, int w2) {
+    int splits = proj_splits_simt(m, w1, w2);
+    int kc = align_up((size_t)ceil_div(m, splits), kSK);
+    splits = ceil_div(m, kc);
+    return (size_t)splits * w1 * w2;
+}
+
+}  // namespace lls

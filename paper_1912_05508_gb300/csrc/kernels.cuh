@@ -1,0 +1,88 @@
+// Internal launch interfaces between the library's translation units.
+#pragma once
+#include "common.cuh"
+
+namespace lls {
+
+constexpr int kMaxPanelLevels = 8;
+
+// ---- panel (panel.cu) -------------------------------------------------------------------
+struct PanelCall {
+    float* W; int ldw;
+    void* Wh; int ldh;
+    float* R; int ldr;
+    int m, c0, b;
+    int lowp;              // 0 FP16, 1 BF16, 3 none
+    float* rbuf; float* qbuf; unsigned* cnt;
+};
+void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t& cnt_words);
+int panel_qr(const PanelCall& c, cudaStream_t st);
+
+// ---- scale / cast (cast.cu) ---------------------------------------------------------------
+// For columns [c0, c0 + w) of the FP32 matrix X (m rows, ldx): e_j = column scale exponent
+// (FP16 rule; 0 for BF16), Xh[:, j] = round(X[:, j] * 2^e_j). Writes exps[j - c0].
+int scale_cast_columns(const float* X, int ldx, int m, int c0, int w, void* Xh, int ldh,
+                       int lowp, int* exps, cudaStream_t st);
+
+// ---- tensor-core products (gemm_tc.cu) ----------------------------------------------------
+// G1 (Alg. 2 line 8): part[s] = Q1l^T A2l over K-split s; then R12 = sum_s part[s] * 2^-e_j
+//     written to R (FP32), and R12l = round(R12 * 2^f_j) with its own column exponents f_j.
+// G2 (Alg. 2 line 9): A2 -= (Q1l R12l) * 2^-f_j, FP32 in place.
+struct ProjCall {
+    const void* Q1l; const void* A2l; int ldh;   // low-precision operands (column-major, ld ldh)
+    int m, w1, w2;                                // M = w1, N = w2, K = m
+    const int* e;                                 // A2 column exponents (w2)
+    float* R12; int ldr;                          // FP32 output block of R
+    void* R12l; int ldrl;                         // low-precision scaled copy for G2 (w1 x w2)
+    int* f;                                       // R12 column exponents (w2)
+    float* part; size_t part_floats;              // split-K partials scratch
+    int lowp;
+};
+struct UpdCall {
+    const void* Q1l; int ldh;                     // m x w1 low precision
+    const void* R12l; int ldrl;                   // w1 x w2 low precision (scaled by 2^f)
+    const int* f;
+    float* A2; int ldw;                           // m x w2 FP32, updated in place
+    int m, w1, w2;
+    int lowp;
+};
+size_t proj_partial_floats(int m, int w1, int w2);
+int gemm_projection(const ProjCall& c, cudaStream_t st);
+int gemm_update(const UpdCall& c, cudaStream_t st);
+
+// ---- FP32 SIMT GEMM (gemm_simt.cu): reference-precision products and the R^-1 recursion --
+// C = alpha * op(A) op(B) + beta * C, column-major, op(X) = X or X^T.
+int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, int lda,
+          const float* B, int ldb, float beta, float* C, int ldc, cudaStream_t st);
+
+// ---- triangular inverse (trinv.cu) ----------------------------------------------------------
+// Minv = R^{-1} (upper triangular, n x n, ld n) via diagonal-block inverses and the recursion
+// M12 = -M11 R12 M22 over the same column split as the QR; Mt = Minv^T. tmp: n*n floats.
+int tri_inverse(const float* R, int ldr, int n, int pw, float* Minv, float* Mt, float* tmp,
+                int* dev_err, cudaStream_t st);
+
+// ---- Krylov (krylov.cu) -----------------------------------------------------------------------
+struct KrylovCall {
+    int m, n;
+    const float* A; int lda;
+    const double* b;
+    double* x;
+    const float* Minv;      // R^{-1}, column-major n x n
+    const float* Mt;        // (R^{-1})^T, column-major n x n
+    int method;             // lls_krylov
+    int target;             // lls_target
+    double tol;
+    int max_iter;
+    void* scratch; size_t scratch_bytes;
+    int* dev_err;
+    double* dev_info;       // [iters, eta, fwd, res, atr, anorm, xnorm, status]
+};
+size_t krylov_scratch_bytes(int m, int n, int grid);
+int krylov_solve(const KrylovCall& c, cudaStream_t st);
+
+// ---- misc (util.cu) -------------------------------------------------------------------------
+int copy_matrix(const float* src, int lds, float* dst, int ldd, int m, int n, cudaStream_t st);
+int check_diag(const float* R, int ldr, int n, int* dev_err, cudaStream_t st);
+int zero_lower(float* R, int ldr, int n, cudaStream_t st);
+
+}  // namespace lls

@@ -1,0 +1,81 @@
+// Small helper kernels: matrix copies, R diagonal check, Frobenius norm.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lls {
+
+int copy_matrix(const float* src, int lds, float* dst, int ldd, int m, int n, cudaStream_t st) {
+    if (m <= 0 || n <= 0) return LLS_OK;
+    LLS_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(float) * (size_t)ldd, src, sizeof(float) * (size_t)lds,
+                                   sizeof(float) * (size_t)m, (size_t)n, cudaMemcpyDeviceToDevice, st));
+    return LLS_OK;
+}
+
+__global__ void check_diag_kernel(const float* __restrict__ R, int ldr, int n, int* err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float d = R[(size_t)i + (size_t)i * ldr];
+        if (!(d > 0.f) || !isfinite(d)) atomicCAS(err, DEV_OK, DEV_SINGULAR);
+    }
+}
+
+int check_diag(const float* R, int ldr, int n, int* dev_err, cudaStream_t st) {
+    check_diag_kernel<<<ceil_div(n, 256) < 64 ? ceil_div(n, 256) : 64, 256, 0, st>>>(R, ldr, n, dev_err);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+__global__ void zero_lower_kernel(float* R, int ldr, int n) {
+    int j = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x + j + 1; i < n; i += gridDim.x * blockDim.x)
+        R[(size_t)i + (size_t)j * ldr] = 0.f;
+}
+
+int zero_lower(float* R, int ldr, int n, cudaStream_t st) {
+    if (n <= 1) return LLS_OK;
+    dim3 grid(ceil_div(n, 256) < 16 ? ceil_div(n, 256) : 16, n);
+    zero_lower_kernel<<<grid, 256, 0, st>>>(R, ldr, n);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+// Sum of squares of an m x n FP32 matrix: compensated (double-float) accumulation per
+// thread, FP64 across threads; per-block partials, then one warp sums them in a fixed order.
+__global__ void sumsq_kernel(const float* __restrict__ A, int lda, int m, int n, double* part) {
+    // compensated FP32 accumulation (FP64 arithmetic is ~70x slower on this GPU)
+    float hs = 0.f, hc = 0.f;
+    for (int j = blockIdx.y; j < n; j += gridDim.y) {
+        const float* col = A + (size_t)j * lda;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            float v = col[i];
+            dot2_step(hs, hc, v, v, 0.f);
+        }
+    }
+    double s = warp_sum_d(join_df(hs, hc));
+    __shared__ double sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x + blockIdx.y * gridDim.x] = t;
+    }
+}
+
+__global__ void sum_parts_kernel(const double* part, int np, double* out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 32) s += part[i];
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// out = ||A||_F^2 (FP64, device). part: >= 64*64 doubles.
+int fro_sumsq(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t st) {
+    dim3 grid(ceil_div(m, 256) < 8 ? ceil_div(m, 256) : 8, n < 512 ? n : 512);
+    sumsq_kernel<<<grid, 256, 0, st>>>(A, lda, m, n, part);
+    LLS_CUDA_TRY(cudaGetLastError());
+    sum_parts_kernel<<<1, 32, 0, st>>>(part, (int)(grid.x * grid.y), out);
+    LLS_CUDA_TRY(cudaGetLastError());
+    return LLS_OK;
+}
+
+}  // namespace lls

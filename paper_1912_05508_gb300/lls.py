@@ -1,0 +1,198 @@
+"""Python binding of the C ABI in include/lls_gb300.h (ctypes; argument marshalling only).
+
+The raw functions keep the C names and take integer device pointers, sizes and a CUDA
+stream handle. The torch helpers below them (``qr``, ``solve``) only allocate device
+memory with torch and pass pointers; every arithmetic step runs in the library's kernels.
+Loading fails loudly when the compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblls_gb300.so")
+
+PREC = {"fp16": 0, "bf16": 1, "fp32": 3}
+TARGET = {"fp32": 0, "fp64": 1}
+KRYLOV = {"cgls": 0, "lsqr": 1}
+STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
+          -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED"}
+
+EXPORTS = ("lls_default_options", "lls_status_string", "qr_factor_workspace_size", "qr_factor",
+           "lls_solve_workspace_size", "lls_solve")
+
+
+class lls_options(C.Structure):
+    _fields_ = [("gemm_prec", C.c_int), ("target", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("panel_width", C.c_int), ("krylov", C.c_int),
+                ("leaf_rows", C.c_int)]
+
+
+class lls_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("eta", C.c_double),
+                ("fwd_est", C.c_double), ("res_norm", C.c_double), ("atr_norm", C.c_double),
+                ("anorm_f", C.c_double), ("xnorm", C.c_double), ("qr_ms", C.c_float),
+                ("krylov_ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LLSError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (built by paper_1912_05508_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    i, sz, vp, dp = C.c_int, C.c_size_t, C.c_void_p, C.c_double
+    lib.lls_default_options.argtypes = [C.POINTER(lls_options)]
+    lib.lls_default_options.restype = None
+    lib.lls_status_string.argtypes = [i]
+    lib.lls_status_string.restype = C.c_char_p
+    lib.qr_factor_workspace_size.argtypes = [i, i, C.POINTER(lls_options)]
+    lib.qr_factor_workspace_size.restype = sz
+    lib.qr_factor.argtypes = [i, i, vp, i, vp, i, vp, i, vp, sz, C.POINTER(lls_options), vp]
+    lib.qr_factor.restype = i
+    lib.lls_solve_workspace_size.argtypes = [i, i, C.POINTER(lls_options)]
+    lib.lls_solve_workspace_size.restype = sz
+    lib.lls_solve.argtypes = [i, i, vp, i, vp, vp, vp, i, vp, sz, C.POINTER(lls_options),
+                              C.POINTER(lls_info), vp]
+    lib.lls_solve.restype = i
+    _lib = lib
+    return lib
+
+
+def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=32,
+                 krylov="cgls", leaf_rows=256) -> lls_options:
+    o = lls_options()
+    load().lls_default_options(C.byref(o))
+    o.gemm_prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.target = TARGET[target] if isinstance(target, str) else int(target)
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.panel_width = int(panel_width)
+    o.krylov = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
+    o.leaf_rows = int(leaf_rows)
+    return o
+
+
+# ---- raw C entry points (same names as the C ABI) ------------------------------------------
+
+def lls_default_options() -> lls_options:
+    o = lls_options()
+    load().lls_default_options(C.byref(o))
+    return o
+
+
+def lls_status_string(status: int) -> str:
+    return load().lls_status_string(int(status)).decode()
+
+
+def qr_factor_workspace_size(m, n, opts=None) -> int:
+    return load().qr_factor_workspace_size(m, n, C.byref(opts) if opts is not None else None)
+
+
+def qr_factor(m, n, A, lda, Q, ldq, R, ldr, ws, ws_bytes, opts, stream) -> int:
+    return load().qr_factor(m, n, A, lda, Q, ldq, R, ldr, ws, ws_bytes,
+                            C.byref(opts) if opts is not None else None, stream)
+
+
+def lls_solve_workspace_size(m, n, opts=None) -> int:
+    return load().lls_solve_workspace_size(m, n, C.byref(opts) if opts is not None else None)
+
+
+def lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream) -> int:
+    return load().lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes,
+                            C.byref(opts) if opts is not None else None,
+                            C.byref(info) if info is not None else None, stream)
+
+
+# ---- torch helpers (allocation and pointer passing only) -----------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(A, dtype=None, device="cuda"):
+    """Column-major copy of a 2-D array/tensor on the device: shape (m, n), strides (1, m)."""
+    torch = _torch()
+    t = torch.as_tensor(A)
+    dtype = dtype or torch.float32
+    out = torch.empty((t.shape[1], t.shape[0]), dtype=dtype, device=device).t()
+    out.copy_(t.to(device=device, dtype=dtype))
+    return out
+
+
+def _check_colmajor(A):
+    assert A.dim() == 2 and A.stride(0) == 1 and A.stride(1) >= A.shape[0], "A must be column-major"
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def workspace(nbytes: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def qr(A, prec="fp16", panel_width=32, want_q=True, ws=None, stream=None):
+    """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False."""
+    torch = _torch()
+    _check_colmajor(A)
+    m, n = A.shape
+    o = make_options(prec=prec, panel_width=panel_width)
+    nb = qr_factor_workspace_size(m, n, o)
+    if nb == 0:
+        raise LLSError(-1, "qr_factor_workspace_size")
+    ws = ws if ws is not None and ws.numel() >= nb else workspace(nb, A.device)
+    R = torch.empty((n, n), dtype=torch.float32, device=A.device).t()
+    Q = torch.empty((n, m), dtype=torch.float32, device=A.device).t() if want_q else None
+    st = qr_factor(m, n, A.data_ptr(), A.stride(1), Q.data_ptr() if want_q else None, m,
+                   R.data_ptr(), n, ws.data_ptr(), ws.numel(), o, _stream(stream))
+    if st != 0:
+        raise LLSError(st, "qr_factor")
+    return Q, R
+
+
+def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=32,
+          krylov="cgls", want_r=False, ws=None, stream=None, check=True):
+    """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
+
+    Returns (x, info_dict[, R]). Synchronizes the stream (to fill info)."""
+    torch = _torch()
+    _check_colmajor(A)
+    m, n = A.shape
+    o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter,
+                     panel_width=panel_width, krylov=krylov)
+    nb = lls_solve_workspace_size(m, n, o)
+    if nb == 0:
+        raise LLSError(-1, "lls_solve_workspace_size")
+    ws = ws if ws is not None and ws.numel() >= nb else workspace(nb, A.device)
+    b = b.to(device=A.device, dtype=torch.float64).contiguous()
+    x = torch.empty(n, dtype=torch.float64, device=A.device)
+    R = torch.empty((n, n), dtype=torch.float32, device=A.device).t() if want_r else None
+    info = lls_info()
+    st = lls_solve(m, n, A.data_ptr(), A.stride(1), b.data_ptr(), x.data_ptr(),
+                   R.data_ptr() if want_r else None, n, ws.data_ptr(), ws.numel(), o, info,
+                   _stream(stream))
+    if check and st < 0:
+        raise LLSError(st, "lls_solve")
+    d = info.as_dict()
+    d["status_code"] = st
+    return (x, d, R) if want_r else (x, d)

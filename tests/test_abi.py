@@ -1,0 +1,56 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every entry point
+declared in include/lls_gb300.h, and argument checks answer without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1912_05508_gb300 import build, lls
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "lls_gb300.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\**([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lls.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert "qr_factor" in names and "lls_solve" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(lls.EXPORTS) <= set(names)
+
+
+def test_defaults_and_status_strings(lib):
+    o = lls.lls_default_options()
+    assert (o.gemm_prec, o.target, o.max_iter, o.panel_width, o.krylov) == (0, 1, 200, 32, 0)
+    assert lls.lls_status_string(0) == "ok"
+    assert "singular" in lls.lls_status_string(-2)
+
+
+def test_workspace_queries_and_argument_errors(lib):
+    o = lls.make_options()
+    assert lls.qr_factor_workspace_size(1000, 100, o) > 1000 * 100 * 6
+    assert lls.qr_factor_workspace_size(10, 20, o) == 0          # m < n
+    assert lls.lls_solve_workspace_size(1000, 100, o) > lls.qr_factor_workspace_size(1000, 100, o)
+    bad = lls.make_options(panel_width=40)
+    assert lls.qr_factor_workspace_size(100, 10, bad) == 0
+    # argument errors are detected before any device work: null pointers, ld < m
+    assert lls.qr_factor(100, 10, None, 100, None, 0, None, 10, None, 0, o, None) == -1
+    assert lls.qr_factor(100, 10, 256, 50, None, 0, 256, 10, 256, 1 << 20, o, None) == -1
+    info = lls.lls_info()
+    assert lls.lls_solve(5, 10, 256, 5, 256, 256, None, 0, 256, 1 << 20, o, info, None) == -1
+    # misaligned / too small workspace
+    assert lls.qr_factor(100, 10, 256, 100, None, 0, 256, 10, 257, 1 << 30, o, None) == -4
+    assert lls.qr_factor(100, 10, 256, 100, None, 0, 256, 10, 256, 1024, o, None) == -4

@@ -1,0 +1,93 @@
+"""GPU parity of qr_factor (Alg. 2 + Eq. caqr) against the CPU oracle, through the C ABI.
+
+Tolerances
+----------
+* FP32 products: the factorization is a recursive Gram-Schmidt QR in FP32, so R matches
+  the unique (positive-diagonal) FP64 R to c * kappa * u32 normwise, ||A - QR|| / ||A|| <=
+  c * u32 and ||I - Q^T Q|| <= c * kappa * u32 (Sec. 3.2.1), with c ~ sqrt(n).
+* FP16 / BF16 products: the oracle runs the same recursion with the same rounding points
+  in FP64. Rounding decisions can differ where the GPU's FP32 operand and the oracle's
+  FP64 operand straddle a rounding boundary, so R agrees to c * u_low normwise (u16 = 2^-11,
+  ubf16 = 2^-8); backward error <= 4 u_low; orthogonality <= c * kappa * u_low.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct, metrics, rgsqrf
+from paper_1912_05508_gb300 import lls, synth
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+ULOW = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def svd_matrix(m, n, kappa, seed, kind="geometric"):
+    return synth.svd_lls(m, n, kind, kappa, seed=seed, noise=0.0).A
+
+
+def gpu_qr(A32, prec, pw=32):
+    Q, R = lls.qr(lls.colmajor(A32), prec=prec, panel_width=pw)
+    torch.cuda.synchronize()
+    return Q.cpu().numpy().astype(np.float64), R.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("m,n", [(1000, 100), (4000, 32), (5000, 7), (300, 300), (257, 64)])
+def test_fp32_products_match_householder(m, n):
+    kappa = 1e3
+    A = svd_matrix(m, n, kappa, seed=m + n)
+    Q, R = gpu_qr(A, "fp32")
+    Qh, Rh = direct.householder_qr(A)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert (np.diag(R) > 0).all()
+    assert np.linalg.norm(R - Rh) / np.linalg.norm(Rh) <= 20 * kappa * U32 * n ** 0.5
+    assert metrics.qr_factorization_error(A, Q, R) <= 10 * U32 * n ** 0.5
+    # the recursion orthogonalises each right half once, so orthogonality decays like
+    # kappa * u (Sec. 3.2.1), not like CGS2's O(u)
+    assert metrics.orthogonality(Q, "2") <= 10 * kappa * U32 * n ** 0.5
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("m,n,pw", [(1000, 100, 32), (2048, 256, 32), (777, 96, 16)])
+def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
+    kappa = 1e3
+    A = svd_matrix(m, n, kappa, seed=3 * m + n)
+    Q, R = gpu_qr(A, prec, pw)
+    Qo, Ro = rgsqrf.rgsqrf(A, pw, prec, leaf_rows=256)
+    u = ULOW[prec]
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    fe = metrics.qr_factorization_error(A, Q, R)
+    assert fe <= 4 * u
+    assert metrics.orthogonality(Q, "2") <= 4 * u * kappa * n ** 0.5
+    # the oracle's own figures are of the same size (the products really are rounded)
+    assert fe >= metrics.qr_factorization_error(A, Qo, Ro) / 16
+
+
+def test_column_scaling_handles_wide_column_range():
+    # Column norms 10^U(-2, 2): without per-column scaling FP16 would lose the small columns.
+    A = synth.scaled_gaussian(2000, 64, seed=11)
+    Q, R = gpu_qr(A, "fp16")
+    Qo, Ro = rgsqrf.rgsqrf(A, 32, "fp16")
+    assert metrics.qr_factorization_error(A, Q, R) <= 4 * ULOW["fp16"]
+    # columnwise relative error of A - QR stays at the FP16 level even for tiny columns
+    E = A.astype(np.float64) - Q @ R
+    colrel = np.linalg.norm(E, axis=0) / np.linalg.norm(A.astype(np.float64), axis=0)
+    assert colrel.max() <= 16 * ULOW["fp16"]
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * ULOW["fp16"]
+
+
+def test_rank_deficient_column_gives_zero_diagonal():
+    A = svd_matrix(600, 40, 10.0, seed=5)
+    A[:, 17] = 0.0
+    _, R = gpu_qr(A, "fp32")
+    assert abs(R[17, 17]) <= 1e-6 * np.abs(np.diag(R)).max()
+
+
+def test_q_optional_and_repeatable():
+    A = svd_matrix(1500, 96, 1e2, seed=9)
+    Ad = lls.colmajor(A)
+    _, R1 = lls.qr(Ad, prec="fp16", want_q=False)
+    _, R2 = lls.qr(Ad, prec="fp16", want_q=False)
+    torch.cuda.synchronize()
+    assert torch.equal(R1, R2)     # fixed reduction order: bitwise repeatable
