@@ -1,0 +1,321 @@
+"""Benchmark: least-squares time-to-1e-12 backward error and QR TFLOP/s on one GB300.
+
+Workload (one step = one full solve of the hot path): A is 32768 x 4096 FP32,
+A = U diag(sigma) V^T with Haar U, V and a geometric spectrum from 1 to 1/kappa
+(kappa = 1e3, seed 2), x_true ~ N(0, I), b = A x_true + e with e orthogonal to range(A),
+||e|| = 1e-6 ||A x_true||. Recursive Gram-Schmidt QR with FP16 tensor-core products,
+then R-preconditioned CGLS to the FP64 target (eta_est <= 1e-12, confirmed on a fresh
+residual). Inputs are generated on the device in FP64 and rounded to FP32.
+
+Prints ONE JSON line (rank 0). `value` is the mean device time per solve in ms
+(lower is better); `qr_tflops` is (2 m n^2 - 2/3 n^3) / QR time. `--impl reference`
+times the CPU oracle (FP64 Householder, Alg. 1) instead, on a column sample.
+
+Multi-GPU: the path solves one independent problem per GPU (replicas, no collective);
+`value` is then the max-over-ranks time per solve and `problems_per_s` counts all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LLS time-to-1e-12 backward error & QR TFLOP/s vs plain FP64 Householder, GB300"
+
+
+def qr_flops(m, n):
+    return 2.0 * m * n * n - 2.0 / 3.0 * n ** 3
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--m", type=int, default=32768)
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--kind", default="geometric")
+    ap.add_argument("--kappa", type=float, default=1e3)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--prec", default="fp16")
+    ap.add_argument("--target", default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cols", type=int, default=1024)
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return rank, ws
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(A32_dev, b_dev, cols, m, n):
+    """Oracle (FP64 Householder LLS, Alg. 1) on the first `cols` columns, scaled by flops."""
+    import numpy as np
+    from oracle import direct
+    A_s = A32_dev[:, :cols].cpu().numpy()
+    b = b_dev.cpu().numpy()
+    direct.lib()
+    t0 = time.perf_counter()
+    direct.lls(A_s.astype(np.float64), b)
+    dt = time.perf_counter() - t0
+    scale = qr_flops(m, n) / qr_flops(m, cols)
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 Householder LLS on the first {cols} of {n} columns ({m} rows), "
+                      f"{dt:.2f} s measured, scaled by the flop ratio {scale:.1f}"}
+
+
+def run_reference(args):
+    rank, ws = dist_setup("gloo")
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import direct
+    from paper_1912_05508_gb300 import synth
+    cols = 512
+    rng = synth.rng_for(args.seed)
+    A = rng.standard_normal((args.m, cols)).astype(np.float32)
+    b = rng.standard_normal(args.m)
+    A64 = A.astype(np.float64)
+    for _ in range(args.warmup):
+        direct.lls(A64, b)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        direct.lls(A64, b)
+        times.append(time.perf_counter() - t0)
+    scale = qr_flops(args.m, args.n) / qr_flops(args.m, cols)
+    ms = statistics.mean(times) * 1e3 * scale
+    cfg = {"workload": f"single LLS {args.m}x{args.n} FP32, {args.kind} kappa={args.kappa:g}",
+           "sample": f"{cols}-column Gaussian sample, scaled by flops x{scale:.1f}"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                      "cpu_baseline": {"value": ms, "unit": "ms", "cores": os.cpu_count(),
+                                       "kind": "oracle", "sample": cfg["sample"]},
+                      "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
+def make_inputs(args, m, n, rank, dev):
+    """Generate the problem on the device; keep a host copy in /tmp so a rerun of the same
+    command (e.g. under a profiler, where torch's linear-algebra plugin may not load) reuses it."""
+    import torch
+    from paper_1912_05508_gb300 import synth
+    path = os.path.join(tempfile.gettempdir(),
+                        f"lls_bench_{m}x{n}_{args.kind}_{args.kappa:g}_{args.seed + rank}.pt")
+    if os.path.exists(path):
+        d = torch.load(path)
+        A = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+        A.copy_(d["A"])
+        return A, d["b"].to(dev)
+    A, b, _ = synth.svd_lls_torch(m, n, args.kind, args.kappa, seed=args.seed + rank, device=dev)
+    try:
+        torch.save({"A": A.cpu(), "b": b.cpu()}, path + ".tmp")
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+    return A, b
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, ws = dist_setup("nccl")
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n = args.m, args.n
+    A, b = make_inputs(args, m, n, rank, dev)
+    o = lls.make_options(prec=args.prec, target=args.target)
+    nb = lls.lls_solve_workspace_size(m, n, o)
+    wsbuf = lls.workspace(nb, dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def solve_once(info):
+        st = lls.lls_solve(m, n, A.data_ptr(), A.stride(1), b.data_ptr(), x.data_ptr(), None, n,
+                           wsbuf.data_ptr(), wsbuf.numel(), o, info, sh)
+        if st < 0:
+            raise RuntimeError(f"lls_solve failed: {lls.STATUS.get(st, st)}")
+        return st
+
+    info = lls.lls_info()
+    for _ in range(args.warmup):
+        solve_once(info)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = lls.lls_kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solve_once(info)
+        infos.append(info.as_dict())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    launches = lls.lls_kernel_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = total_ms / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # QR alone (for the QR TFLOP/s half of the metric)
+    qo = lls.make_options(prec=args.prec)
+    qnb = lls.qr_factor_workspace_size(m, n, qo)
+    qws = wsbuf if qnb <= wsbuf.numel() else lls.workspace(qnb, dev)
+    R = torch.empty((n, n), dtype=torch.float32, device=dev).t()
+    for _ in range(2):
+        lls.qr_factor(m, n, A.data_ptr(), A.stride(1), None, m, R.data_ptr(), n, qws.data_ptr(),
+                      qws.numel(), qo, sh)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qsteps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(qsteps):
+        lls.qr_factor(m, n, A.data_ptr(), A.stride(1), None, m, R.data_ptr(), n, qws.data_ptr(),
+                      qws.numel(), qo, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qr_ms = e0.elapsed_time(e1) / qsteps
+
+    # end to end through the C ABI with host buffers: H2D of A and b, solve, D2H of x
+    Ah = torch.empty((n, m), dtype=torch.float32, pin_memory=True).t()
+    Ah.copy_(A)
+    bh = b.cpu().pin_memory()
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    Ad = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+    bd = torch.empty_like(b)
+    e2e_steps = max(2, min(args.steps, 5))
+    e2e_ms = []
+    for it in range(e2e_steps + 1):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        Ad.copy_(Ah, non_blocking=True)
+        bd.copy_(bh, non_blocking=True)
+        st = lls.lls_solve(m, n, Ad.data_ptr(), Ad.stride(1), bd.data_ptr(), x.data_ptr(), None, n,
+                           wsbuf.data_ptr(), wsbuf.numel(), o, info, sh)
+        xh.copy_(x, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(s0.elapsed_time(s1))
+
+    last = infos[-1]
+    kry_ms = statistics.mean(i["krylov_ms"] for i in infos)
+    a_passes = statistics.mean(i["a_passes"] for i in infos)
+    m_passes = statistics.mean(i["m_passes"] for i in infos)
+    kry_bytes = a_passes * 4.0 * m * n + m_passes * 4.0 * n * (n + 1) / 2.0
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    achieved = kry_bytes / (kry_ms * 1e-3) / 1e9
+    roofline = {"kernel": "cgls_kernel (persistent CGLS iteration)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                "traffic": None,
+                "algorithmic_bytes_per_launch": kry_bytes}
+    out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "fp16 products / f32 panel / double-float Krylov",
+           "data": "synthetic",
+           "config": {"workload": f"single LLS {m}x{n} FP32, {args.kind} spectrum kappa={args.kappa:g}, "
+                                  f"{args.prec.upper()} products, {args.target.upper()} target",
+                      "m": m, "n": n, "prec": args.prec, "target": args.target,
+                      "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
+                      "parallelism": f"replicas x{ws}"},
+           "qr_ms": qr_ms, "qr_tflops": qr_flops(m, n) / (qr_ms * 1e-3) / 1e12,
+           "krylov_ms": kry_ms, "iters": last["iters"], "eta": last["eta"],
+           "status": last["status"], "problems_per_s": ws * 1e3 / ms,
+           "roofline": roofline,
+           "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms",
+                   "h2d_bytes_per_step": m * n * 4 + m * 8, "d2h_bytes_per_step": n * 8},
+           "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+           "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(A, b, min(args.cpu_sample_cols, n), m, n)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

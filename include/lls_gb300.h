@@ -76,6 +76,8 @@ typedef struct {
     double xnorm;      /* ||x||_2 */
     float qr_ms;       /* device time of the factorization (and preconditioner set-up) */
     float krylov_ms;   /* device time of the Krylov iteration */
+    int a_passes;      /* full passes over A made by the Krylov kernel (A x, A^T r products) */
+    int m_passes;      /* products with the n x n preconditioner R^{-1} or its transpose */
 } lls_info;
 
 /* Fill *opts with the defaults listed above. */
@@ -83,6 +85,10 @@ void lls_default_options(lls_options* opts);
 
 /* Human-readable name of a status code (static string). */
 const char* lls_status_string(int status);
+
+/* Number of GPU kernels this process has enqueued through the library so far (all
+ * threads, all devices). Lets a caller count launches per call or per captured graph. */
+unsigned long long lls_kernel_launch_count(void);
 
 /* ---------------------------------------------------------------------------
  * QR factorization (Alg. 2 + Eq. caqr): A = Q R, Q m x n with orthonormal columns

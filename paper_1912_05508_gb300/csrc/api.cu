@@ -144,9 +144,18 @@ static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, cons
 
 }  // namespace lls
 
+#include <atomic>
+
+namespace lls {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace lls
+
 using namespace lls;
 
 extern "C" {
+
+unsigned long long lls_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void lls_default_options(lls_options* o) {
     if (!o) return;
@@ -273,6 +282,8 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     info->atr_norm = hinfo[4];
     info->anorm_f = hinfo[5];
     info->xnorm = hinfo[6];
+    info->a_passes = (int)hinfo[10];
+    info->m_passes = (int)hinfo[11];
     int st = (int)hinfo[7] == 0 ? LLS_OK : LLS_NOT_CONVERGED;
     if (herr == DEV_SINGULAR) st = LLS_ERR_SINGULAR;
     else if (herr == DEV_TIMEOUT) st = LLS_ERR_TIMEOUT;

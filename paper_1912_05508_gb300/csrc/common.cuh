@@ -15,6 +15,14 @@
         if (_e != cudaSuccess) return LLS_ERR_CUDA;          \
     } while (0)
 
+namespace lls { void note_launch(); }
+// After every kernel launch: count it and surface launch-configuration errors.
+#define LLS_LAUNCH_CHECK()                                   \
+    do {                                                     \
+        ::lls::note_launch();                                \
+        LLS_CUDA_TRY(cudaGetLastError());                    \
+    } while (0)
+
 #define LLS_TRY(expr)                                        \
     do {                                                     \
         int _s = (expr);                                     \

@@ -169,7 +169,7 @@ cgls_kernel(KArgs a) {
     const int gtid = blockIdx.x * kKThreads + threadIdx.x, gthreads = gridDim.x * kKThreads;
     const double anorm = sqrt(*a.anorm2);
     const double mnorm = sqrt(*a.mnorm2);
-    int iters = 0, status = 1;
+    int iters = 0, status = 1, apasses = 0, mpasses = 0;
     double eta = 0.0, fwd = 0.0, rn2 = 0.0, un2 = 0.0, xn2 = 0.0, gamma = 0.0;
     bool xzero = a.x_zero != 0;
 
@@ -183,6 +183,7 @@ cgls_kernel(KArgs a) {
         } else {
             stage_vec(a.x, a.n);
             a_times_partials(a);
+            ++apasses;
             KB_SYNC();
             double sq = 0.0;
             for (int i = gtid; i < a.m; i += gthreads) {
@@ -199,6 +200,7 @@ cgls_kernel(KArgs a) {
         rn2 = grid_total(a.bpart, 0);
         // ---- u = A^T r, s = M^T u, gamma = ||s||^2 ----
         at_times_partials(a, a.r);
+        ++apasses;
         KB_SYNC();
         {
             double sq = 0.0;
@@ -218,6 +220,7 @@ cgls_kernel(KArgs a) {
         xn2 = grid_total(a.bpart, 3);
         stage_vec(a.u, a.n);
         block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
+        ++mpasses;
         KB_SYNC();
         gamma = grid_total(a.bpart, 2);
         {
@@ -237,10 +240,12 @@ cgls_kernel(KArgs a) {
             // t = M p
             stage_vec(a.p, a.n);
             tri_gemv(a.Mt, a.n, false, a.t);
+            ++mpasses;
             KB_SYNC();
             // q = A t, delta = ||q||^2
             stage_vec(a.t, a.n);
             a_times_partials(a);
+            ++apasses;
             KB_SYNC();
             {
                 double sq = 0.0;
@@ -270,6 +275,7 @@ cgls_kernel(KArgs a) {
             KB_SYNC();
             // s = M^T (A^T r)
             at_times_partials(a, a.r);
+            ++apasses;
             KB_SYNC();
             for (int j = gtid; j < a.n; j += gthreads) {
                 double v = 0.0;
@@ -279,6 +285,7 @@ cgls_kernel(KArgs a) {
             KB_SYNC();
             stage_vec(a.u, a.n);
             block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
+            ++mpasses;
             KB_SYNC();
             const double gnew = grid_total(a.bpart, 2);
             const double xn = sqrt(grid_total(a.bpart, 3));
@@ -303,6 +310,8 @@ cgls_kernel(KArgs a) {
         a.info[5] = anorm;
         a.info[6] = sqrt(xn2);
         a.info[7] = status;
+        a.info[10] = apasses;
+        a.info[11] = mpasses;
     }
 }
 
@@ -377,6 +386,7 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cgls_kernel, dim3(grid), dim3(kKThreads), args, smem, st));
+    note_launch();
     return LLS_OK;
 }
 

@@ -278,9 +278,9 @@ int panel_qr(const PanelCall& c, cudaStream_t st) {
     panel_levels(c.m, c.b, a.lv, a.P0, a.fanin);
     if (a.lv.nlev > kMaxPanelLevels || c.b < 1 || c.b > 32) return LLS_ERR_UNSUPPORTED;
     panel_leaf_tree_kernel<<<a.P0, kPanelThreads, 0, st>>>(a);
-    LLS_CUDA_TRY(cudaGetLastError());
+    LLS_LAUNCH_CHECK();
     panel_reconstruct_kernel<<<a.P0, kPanelThreads, 0, st>>>(a);
-    LLS_CUDA_TRY(cudaGetLastError());
+    LLS_LAUNCH_CHECK();
     return LLS_OK;
 }
 

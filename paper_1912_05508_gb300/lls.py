@@ -19,8 +19,8 @@ KRYLOV = {"cgls": 0, "lsqr": 1}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
           -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED"}
 
-EXPORTS = ("lls_default_options", "lls_status_string", "qr_factor_workspace_size", "qr_factor",
-           "lls_solve_workspace_size", "lls_solve")
+EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
+           "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve")
 
 
 class lls_options(C.Structure):
@@ -33,7 +33,7 @@ class lls_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("eta", C.c_double),
                 ("fwd_est", C.c_double), ("res_norm", C.c_double), ("atr_norm", C.c_double),
                 ("anorm_f", C.c_double), ("xnorm", C.c_double), ("qr_ms", C.c_float),
-                ("krylov_ms", C.c_float)]
+                ("krylov_ms", C.c_float), ("a_passes", C.c_int), ("m_passes", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,6 +61,8 @@ def load(path: str = LIB_PATH):
     lib.lls_default_options.restype = None
     lib.lls_status_string.argtypes = [i]
     lib.lls_status_string.restype = C.c_char_p
+    lib.lls_kernel_launch_count.argtypes = []
+    lib.lls_kernel_launch_count.restype = C.c_ulonglong
     lib.qr_factor_workspace_size.argtypes = [i, i, C.POINTER(lls_options)]
     lib.qr_factor_workspace_size.restype = sz
     lib.qr_factor.argtypes = [i, i, vp, i, vp, i, vp, i, vp, sz, C.POINTER(lls_options), vp]
@@ -98,6 +100,10 @@ def lls_default_options() -> lls_options:
 
 def lls_status_string(status: int) -> str:
     return load().lls_status_string(int(status)).decode()
+
+
+def lls_kernel_launch_count() -> int:
+    return int(load().lls_kernel_launch_count())
 
 
 def qr_factor_workspace_size(m, n, opts=None) -> int:

@@ -157,3 +157,44 @@ def upper_triangular_test(n: int, seed: int = 0, diag_lo: float = 0.5) -> np.nda
     T = np.triu(rng.standard_normal((n, n))) / math.sqrt(n)
     T[np.diag_indices(n)] = diag_lo + rng.random(n)
     return T
+
+
+def svd_lls_torch(m: int, n: int, kind: str = "geometric", kappa: float = 1e3, seed: int = 2,
+                  noise: float = 1e-6, device="cuda"):
+    """Device-side version of ``svd_lls`` for large problems (FP64 generation with torch).
+
+    Returns (A, b, x_true): A an (m, n) column-major FP32 device tensor (strides (1, m)),
+    b and x_true FP64 device vectors. The Haar factors come from torch.linalg.qr of
+    Gaussian matrices; this is input construction only.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = torch.float64
+
+    def haar(rows, cols):
+        G = torch.randn(rows, cols, generator=g, dtype=f64, device=device)
+        Q, R = torch.linalg.qr(G)
+        d = torch.sign(torch.diagonal(R))
+        d[d == 0] = 1.0
+        return Q * d
+
+    U = haar(m, n)
+    V = haar(n, n)
+    sig = torch.from_numpy(spectrum(kind, n, kappa)).to(device=device, dtype=f64)
+    A64 = (U * sig) @ V.T
+    del V
+    x = torch.randn(n, generator=g, dtype=f64, device=device)
+    Ax = A64 @ x
+    b = Ax.clone()
+    if noise > 0.0 and m > n:
+        w = torch.randn(m, generator=g, dtype=f64, device=device)
+        w = w - U @ (U.T @ w)
+        w = w - U @ (U.T @ w)
+        b = Ax + noise * torch.linalg.norm(Ax) * w / torch.linalg.norm(w)
+    del U
+    A = torch.empty((n, m), dtype=torch.float32, device=device).t()
+    A.copy_(A64)
+    del A64
+    torch.cuda.empty_cache()
+    return A, b, x

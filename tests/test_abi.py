@@ -14,7 +14,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def header_functions():
     txt = open(os.path.join(ROOT, "include", "lls_gb300.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\**([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    txt = re.sub(r"^\s*#.*$", "", txt, flags=re.M)
+    names = []
+    for stmt in txt.split(";"):
+        if "(" not in stmt or "typedef" in stmt or "{" in stmt.split("(")[0]:
+            continue
+        head = stmt.split("(")[0].split()
+        if len(head) >= 2:
+            names.append(head[-1].lstrip("*"))
     return sorted(set(names))
 
 
