@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--prec", default="fp16")
     ap.add_argument("--target", default="fp64")
+    ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=1024)
     return ap.parse_args()
@@ -190,11 +191,13 @@ def main():
     dev = torch.device("cuda", local)
     m, n = args.m, args.n
     A, b = make_inputs(args, m, n, rank, dev)
-    o = lls.make_options(prec=args.prec, target=args.target)
+    o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw)
     nb = lls.lls_solve_workspace_size(m, n, o)
     wsbuf = lls.workspace(nb, dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library replays each repeated call as one CUDA graph on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
 
     def solve_once(info):
@@ -235,7 +238,7 @@ def main():
         ms = float(t.item())
 
     # QR alone (for the QR TFLOP/s half of the metric)
-    qo = lls.make_options(prec=args.prec)
+    qo = lls.make_options(prec=args.prec, panel_width=args.pw)
     qnb = lls.qr_factor_workspace_size(m, n, qo)
     qws = wsbuf if qnb <= wsbuf.numel() else lls.workspace(qnb, dev)
     R = torch.empty((n, n), dtype=torch.float32, device=dev).t()
@@ -299,6 +302,7 @@ def main():
            "config": {"workload": f"single LLS {m}x{n} FP32, {args.kind} spectrum kappa={args.kappa:g}, "
                                   f"{args.prec.upper()} products, {args.target.upper()} target",
                       "m": m, "n": n, "prec": args.prec, "target": args.target,
+                      "panel_width": o.panel_width,
                       "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
                       "parallelism": f"replicas x{ws}"},
            "qr_ms": qr_ms, "qr_tflops": qr_flops(m, n) / (qr_ms * 1e-3) / 1e12,

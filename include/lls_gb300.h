@@ -126,6 +126,34 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
               float* R_out, int ldr, void* ws, size_t ws_bytes, const lls_options* opts,
               lls_info* info, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Kernel-level building blocks: the two tensor-core products of one recursion step of
+ * Alg. 2 (line 8: R12 = Q1^T A2; line 9: A2 = A2 - Q1 R12), with the operands already
+ * rounded to FP16 or BF16 (prec = LLS_PREC_FP16 / LLS_PREC_BF16) and FP32 accumulation.
+ * Exposed for testing and for callers that run their own recursion.
+ *
+ * lls_lowp_projection:
+ *   Q1l  [in]  m x w1 low-precision, column-major, ldh >= m (ldh * 2 bytes multiple of 16,
+ *              base 16-byte aligned); A2l [in] m x w2 low-precision, same ldh.
+ *   e    [in]  w2 ints: A2l column j holds A2[:, j] * 2^e[j].
+ *   R12  [out] w1 x w2 FP32 (ldr >= w1): (Q1l^T A2l)[:, j] * 2^-e[j], summed in a fixed order.
+ *   R12l [out] w1 x w2 low-precision (ldrl >= w1, multiple of 8): R12[:, j] * 2^f[j] rounded
+ *              to nearest even, f [out] w2 ints chosen so max|R12[:, j]| 2^f[j] lies in
+ *              [2^14, 2^15) for FP16 (f = 0 for BF16).
+ *   ws        workspace of lls_lowp_projection_workspace_size(m, w1, w2) bytes, 256-B aligned.
+ * lls_lowp_update:
+ *   A2 [in/out] m x w2 FP32 (lda >= m): A2 -= (Q1l R12l)[:, j] * 2^-f[j].
+ *   ws          >= 256 bytes of 256-B aligned scratch (device error word).
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED (alignment), LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+size_t lls_lowp_projection_workspace_size(int m, int w1, int w2);
+int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l, int ldh,
+                        const int* e, float* R12, int ldr, void* R12l, int ldrl, int* f,
+                        void* ws, size_t ws_bytes, cudaStream_t stream);
+int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
+                    int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
+                    cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

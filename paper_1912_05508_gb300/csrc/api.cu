@@ -120,11 +120,11 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         pc.Q1l = Whb + esz * (size_t)c0 * c.w.ldh;
         pc.A2l = Whb + esz * (size_t)(c0 + w1) * c.w.ldh;
         pc.ldh = c.w.ldh; pc.m = c.m; pc.w1 = w1; pc.w2 = w2; pc.e = c.w.eA;
-        pc.R12 = R12; pc.ldr = c.ldr; pc.R12l = c.w.R12l; pc.ldrl = w1; pc.f = c.w.f;
-        pc.part = c.w.part; pc.part_floats = c.w.part_floats; pc.lowp = c.lowp;
+        pc.R12 = R12; pc.ldr = c.ldr; pc.R12l = c.w.R12l; pc.ldrl = (int)align_up((size_t)w1, 8); pc.f = c.w.f;
+        pc.part = c.w.part; pc.part_floats = c.w.part_floats; pc.lowp = c.lowp; pc.err = c.w.err;
         LLS_TRY(gemm_projection(pc, c.st));
         UpdCall uc;
-        uc.Q1l = pc.Q1l; uc.ldh = c.w.ldh; uc.R12l = c.w.R12l; uc.ldrl = w1; uc.f = c.w.f;
+        uc.Q1l = pc.Q1l; uc.ldh = c.w.ldh; uc.R12l = c.w.R12l; uc.ldrl = pc.ldrl; uc.f = c.w.f; uc.err = c.w.err;
         uc.A2 = A2; uc.ldw = c.w.ldw; uc.m = c.m; uc.w1 = w1; uc.w2 = w2; uc.lowp = c.lowp;
         LLS_TRY(gemm_update(uc, c.st));
     }
@@ -134,6 +134,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
                   QrWs& w, cudaStream_t st) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
+    LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
     LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
     QrCtx c;
@@ -147,8 +148,7 @@ static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, cons
 #include <atomic>
 
 namespace lls {
-static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern std::atomic<unsigned long long> g_launches;
 }  // namespace lls
 
 using namespace lls;
@@ -193,6 +193,26 @@ size_t qr_factor_workspace_size(int m, int n, const lls_options* opts) {
     return ar.off;
 }
 
+struct QrCall {
+    int m, n, lda, ldq, ldr;
+    const float* A; float* Q; float* R;
+    lls_options o;
+    QrWs w;
+};
+
+static int enqueue_qr(void* p, cudaStream_t st, cudaEvent_t*, bool) {
+    QrCall& c = *(QrCall*)p;
+    LLS_TRY(run_qr(c.m, c.n, c.A, c.lda, c.R, c.ldr, c.o, c.w, st));
+    if (c.Q) LLS_TRY(copy_matrix(c.w.W, c.w.ldw, c.Q, c.ldq, c.m, c.n, st));
+    return LLS_OK;
+}
+
+static int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
 int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
               void* ws, size_t ws_bytes, const lls_options* opts, cudaStream_t stream) {
     lls_options o;
@@ -202,12 +222,59 @@ int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R
     if (!valid_opts(o)) return LLS_ERR_ARG;
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
     WsArena ar(ws, ws_bytes);
-    QrWs w;
-    qr_layout(ar, m, n, o, w);
+    QrCall c;
+    qr_layout(ar, m, n, o, c.w);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
-    LLS_TRY(run_qr(m, n, A, lda, R, ldr, o, w, stream));
-    if (Q) LLS_TRY(copy_matrix(w.W, w.ldw, Q, ldq, m, n, stream));
+    c.m = m; c.n = n; c.lda = lda; c.ldq = ldq; c.ldr = ldr; c.A = A; c.Q = Q; c.R = R; c.o = o;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.op = 1; key.device = current_device();
+    key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda; key.ints[3] = Q ? ldq : 0; key.ints[4] = ldr;
+    key.ptrs[0] = A; key.ptrs[1] = Q; key.ptrs[2] = R; key.ptrs[3] = ws;
+    key.ws_bytes = ws_bytes; key.opts = o;
+    trace_mark(stream);
+    LLS_TRY(run_graphed(key, stream, enqueue_qr, &c, nullptr));
+    trace_flush();
     return LLS_OK;
+}
+
+size_t lls_lowp_projection_workspace_size(int m, int w1, int w2) {
+    if (m < 1 || w1 < 1 || w2 < 1) return 0;
+    return align_up(sizeof(float) * proj_partial_floats(m, w1, w2), 256) + 256;
+}
+
+int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l, int ldh,
+                        const int* e, float* R12, int ldr, void* R12l, int ldrl, int* f, void* ws,
+                        size_t ws_bytes, cudaStream_t stream) {
+    if (m < 1 || w1 < 1 || w2 < 1 || ldh < m || ldr < w1 || ldrl < w1 || (ldrl & 7) != 0) return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP16 && prec != LLS_PREC_BF16) return LLS_ERR_ARG;
+    if (!Q1l || !A2l || !e || !R12 || !R12l || !f || !ws) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, ws_bytes);
+    ProjCall pc;
+    pc.part_floats = proj_partial_floats(m, w1, w2);
+    pc.part = ar.take<float>(pc.part_floats);
+    pc.err = ar.take<int>(16);
+    if (!ar.ok) return LLS_ERR_WORKSPACE;
+    LLS_CUDA_TRY(cudaMemsetAsync(pc.err, 0, sizeof(int) * 16, stream));
+    pc.Q1l = Q1l; pc.A2l = A2l; pc.ldh = ldh; pc.m = m; pc.w1 = w1; pc.w2 = w2; pc.e = e;
+    pc.R12 = R12; pc.ldr = ldr; pc.R12l = R12l; pc.ldrl = ldrl; pc.f = f; pc.lowp = lowp_code(prec);
+    return gemm_projection(pc, stream);
+}
+
+int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
+                    int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
+                    cudaStream_t stream) {
+    if (m < 1 || w1 < 1 || w2 < 1 || ldh < m || lda < m || ldrl < w1 || (ldrl & 7) != 0) return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP16 && prec != LLS_PREC_BF16) return LLS_ERR_ARG;
+    if (!Q1l || !R12l || !f || !A2 || !ws) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0 || ws_bytes < 256) return LLS_ERR_WORKSPACE;
+    UpdCall uc;
+    uc.err = (int*)ws;
+    LLS_CUDA_TRY(cudaMemsetAsync(uc.err, 0, sizeof(int) * 16, stream));
+    uc.Q1l = Q1l; uc.ldh = ldh; uc.R12l = R12l; uc.ldrl = ldrl; uc.f = f; uc.A2 = A2; uc.ldw = lda;
+    uc.m = m; uc.w1 = w1; uc.w2 = w2; uc.lowp = lowp_code(prec);
+    return gemm_update(uc, stream);
 }
 
 static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w, float*& R,
@@ -231,6 +298,36 @@ size_t lls_solve_workspace_size(int m, int n, const lls_options* opts) {
     return ar.off;
 }
 
+struct SolveCall {
+    int m, n, lda, ldr;
+    const float* A; const double* b; double* x; float* R_out;
+    lls_options o;
+    QrWs w;
+    float *R, *Minv, *Mt, *tmp;
+    void* ks; size_t kb;
+};
+
+static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+    SolveCall& c = *(SolveCall*)p;
+    const int m = c.m, n = c.n;
+    if (ev) record_phase(ev[0], st, capturing);
+    LLS_CUDA_TRY(cudaMemsetAsync(c.w.dinfo, 0, sizeof(double) * 16, st));
+    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.w, st));
+    if (c.R_out) LLS_TRY(copy_matrix(c.R, n, c.R_out, c.ldr, n, n, st));
+    LLS_TRY(check_diag(c.R, n, n, c.w.err, st));
+    LLS_TRY(tri_inverse(c.R, n, n, c.o.panel_width, c.Minv, c.Mt, c.tmp, c.w.err, st));
+    LLS_TRY(fro_sumsq(c.A, c.lda, m, n, c.w.red, c.w.dinfo + 8, st));
+    LLS_TRY(fro_sumsq(c.Minv, n, n, n, c.w.red + 4096, c.w.dinfo + 9, st));
+    if (ev) record_phase(ev[1], st, capturing);
+    KrylovCall kc;
+    kc.m = m; kc.n = n; kc.A = c.A; kc.lda = c.lda; kc.b = c.b; kc.x = c.x; kc.Minv = c.Minv; kc.Mt = c.Mt;
+    kc.method = c.o.krylov; kc.target = c.o.target; kc.tol = c.o.tol; kc.max_iter = c.o.max_iter;
+    kc.scratch = c.ks; kc.scratch_bytes = c.kb; kc.dev_err = c.w.err; kc.dev_info = c.w.dinfo;
+    LLS_TRY(krylov_solve(kc, st));
+    if (ev) record_phase(ev[2], st, capturing);
+    return LLS_OK;
+}
+
 int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
               int ldr, void* ws, size_t ws_bytes, const lls_options* opts, lls_info* info,
               cudaStream_t stream) {
@@ -243,38 +340,38 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     if (o.krylov != LLS_KRYLOV_CGLS) return LLS_ERR_UNSUPPORTED;
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
     WsArena ar(ws, ws_bytes);
-    QrWs w; float *R, *Minv, *Mt, *tmp; void* ks; size_t kb;
-    lls_layout(ar, m, n, o, w, R, Minv, Mt, tmp, ks, kb);
+    SolveCall c;
+    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
+    c.m = m; c.n = n; c.lda = lda; c.ldr = ldr; c.A = A; c.b = b; c.x = x; c.R_out = R_out; c.o = o;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.op = 2; key.device = current_device();
+    key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda; key.ints[3] = R_out ? ldr : 0;
+    key.ptrs[0] = A; key.ptrs[1] = b; key.ptrs[2] = x; key.ptrs[3] = R_out; key.ptrs[4] = ws;
+    key.ws_bytes = ws_bytes; key.opts = o;
 
+    cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (info)
-        for (auto& e : ev) LLS_CUDA_TRY(cudaEventCreate(&e));
-    if (info) LLS_CUDA_TRY(cudaEventRecord(ev[0], stream));
-    LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, stream));
-    LLS_CUDA_TRY(cudaMemsetAsync(w.dinfo, 0, sizeof(double) * 16, stream));
-    LLS_TRY(run_qr(m, n, A, lda, R, n, o, w, stream));
-    if (R_out) LLS_TRY(copy_matrix(R, n, R_out, ldr, n, n, stream));
-    LLS_TRY(check_diag(R, n, n, w.err, stream));
-    LLS_TRY(tri_inverse(R, n, n, o.panel_width, Minv, Mt, tmp, w.err, stream));
-    LLS_TRY(fro_sumsq(A, lda, m, n, w.red, w.dinfo + 8, stream));
-    LLS_TRY(fro_sumsq(Minv, n, n, n, w.red + 4096, w.dinfo + 9, stream));
-    if (info) LLS_CUDA_TRY(cudaEventRecord(ev[1], stream));
-    KrylovCall kc;
-    kc.m = m; kc.n = n; kc.A = A; kc.lda = lda; kc.b = b; kc.x = x; kc.Minv = Minv; kc.Mt = Mt;
-    kc.method = o.krylov; kc.target = o.target; kc.tol = o.tol; kc.max_iter = o.max_iter;
-    kc.scratch = ks; kc.scratch_bytes = kb; kc.dev_err = w.err; kc.dev_info = w.dinfo;
-    LLS_TRY(krylov_solve(kc, stream));
-    if (!info) return LLS_OK;
-    LLS_CUDA_TRY(cudaEventRecord(ev[2], stream));
+    if (info) {
+        for (int i = 0; i < 3; ++i) LLS_CUDA_TRY(cudaEventCreate(&own[i]));
+        for (int i = 0; i < 3; ++i) ev[i] = own[i];
+    }
+    trace_mark(stream);
+    int rc = run_graphed(key, stream, enqueue_solve, &c, info ? ev : nullptr);
+    trace_flush();
+    if (rc != LLS_OK || !info) {
+        for (auto& e : own) if (e) cudaEventDestroy(e);
+        return rc;
+    }
     double hinfo[16];
     int herr = 0;
-    LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
-    LLS_CUDA_TRY(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, c.w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
+    LLS_CUDA_TRY(cudaMemcpyAsync(&herr, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     LLS_CUDA_TRY(cudaStreamSynchronize(stream));
     cudaEventElapsedTime(&info->qr_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&info->krylov_ms, ev[1], ev[2]);
-    for (auto& e : ev) cudaEventDestroy(e);
+    for (auto& e : own) cudaEventDestroy(e);
     info->iters = (int)hinfo[0];
     info->eta = hinfo[1];
     info->fwd_est = hinfo[2];

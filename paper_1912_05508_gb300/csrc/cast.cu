@@ -53,7 +53,7 @@ int scale_cast_columns(const float* X, int ldx, int m, int c0, int w, void* Xh, 
         scale_cast_kernel<__nv_bfloat16><<<w, kCastThreads, 0, st>>>(X, ldx, m, c0, (__nv_bfloat16*)Xh, ldh, 0, exps);
     else
         return LLS_ERR_UNSUPPORTED;
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("scale_cast", st);
     return LLS_OK;
 }
 

@@ -15,11 +15,16 @@
         if (_e != cudaSuccess) return LLS_ERR_CUDA;          \
     } while (0)
 
-namespace lls { void note_launch(); }
-// After every kernel launch: count it and surface launch-configuration errors.
-#define LLS_LAUNCH_CHECK()                                   \
+namespace lls {
+void note_launch(const char* name, cudaStream_t st);
+void trace_mark(cudaStream_t st);
+void trace_flush();
+}
+// After every kernel launch: count it (and, under LLS_TRACE, time it) and surface
+// launch-configuration errors.
+#define LLS_LAUNCH_CHECK(name, st)                           \
     do {                                                     \
-        ::lls::note_launch();                                \
+        ::lls::note_launch(name, st);                        \
         LLS_CUDA_TRY(cudaGetLastError());                    \
     } while (0)
 

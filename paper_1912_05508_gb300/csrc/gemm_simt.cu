@@ -93,7 +93,7 @@ int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, in
     else if (!ta && tb) LLS_SG(false, true);
     else LLS_SG(true, true);
 #undef LLS_SG
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("sgemm", st);
     return LLS_OK;
 }
 
@@ -145,7 +145,7 @@ int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, flo
         proj_reduce_kernel<__nv_bfloat16><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, R12, ldr, (__nv_bfloat16*)R12l, ldrl, f, 0);
     else
         proj_reduce_kernel<float><<<w2, 256, 0, st>>>(part, splits, w1, w2, nullptr, R12, ldr, (float*)nullptr, 0, f, 0);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("proj_reduce", st);
     return LLS_OK;
 }
 
@@ -167,7 +167,7 @@ int simt_projection_f32(const float* Q1, const float* A2, int ldw, int m, int w1
     dim3 grid(ceil_div(w1, kSB), ceil_div(w2, kSB), splits);
     gemm_simt_kernel<float, float, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         w1, w2, m, kc, Q1, ldw, A2, ldw, part, 0, 1.f, 0.f, nullptr);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("simt_proj_f32", st);
     return proj_reduce(part, splits, w1, w2, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st);
 }
 
@@ -176,7 +176,7 @@ int simt_update_f32(const float* Q1, int ldw, const float* R12, int ldr, float* 
     dim3 grid(ceil_div(m, kSB), ceil_div(w2, kSB), 1);
     gemm_simt_kernel<float, float, false, false, EPI_UPDATE><<<grid, kSThreads, 0, st>>>(
         m, w2, w1, w1, Q1, ldw, R12, ldr, A2, ldw, 1.f, 0.f, nullptr);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("simt_proj_f32", st);
     return LLS_OK;
 }
 
@@ -191,7 +191,7 @@ static int simt_lowp_projection(const ProjCall& c, cudaStream_t st) {
     dim3 grid(ceil_div(c.w1, kSB), ceil_div(c.w2, kSB), splits);
     gemm_simt_kernel<TL, TL, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         c.w1, c.w2, c.m, kc, (const TL*)c.Q1l, c.ldh, (const TL*)c.A2l, c.ldh, c.part, 0, 1.f, 0.f, nullptr);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("simt_upd_f32", st);
     return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
 }
 
@@ -200,7 +200,7 @@ static int simt_lowp_update(const UpdCall& c, cudaStream_t st) {
     dim3 grid(ceil_div(c.m, kSB), ceil_div(c.w2, kSB), 1);
     gemm_simt_kernel<TL, TL, false, false, EPI_UPDATE><<<grid, kSThreads, 0, st>>>(
         c.m, c.w2, c.w1, c.w1, (const TL*)c.Q1l, c.ldh, (const TL*)c.R12l, c.ldrl, c.A2, c.ldw, 1.f, 0.f, c.f);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("simt_proj_lowp", st);
     return LLS_OK;
 }
 

@@ -1,16 +1,399 @@
-// Tensor-core products of the recursion (Alg. 2 lines 8-9). Placeholder dispatch to the
-// CUDA-core kernels until the tcgen05 kernels are in place.
+// Tensor-core products of the recursion (Alg. 2 lines 8-9) on sm_103a: tcgen05.mma with the
+// accumulator in tensor memory (TMEM), operands staged in shared memory by TMA.
+//
+//   projection  P = Q1l^T A2l       M = w1, N = w2, K = m   (both operands K-major)
+//               split over K; partial tiles go to a scratch buffer and are reduced in a
+//               fixed order (proj_reduce in gemm_simt.cu), which also unscales by 2^-e_j.
+//   update      A2 -= (Q1l R12l) 2^-f_j   M = m, N = w2, K = w1   (Q1l is M-major)
+//               the epilogue reads the FP32 A2 tile, subtracts, writes it back.
+//
+// Inputs are FP16 or BF16 with FP32 accumulation (kind::f16). One CTA computes one
+// 128 x BN output tile (one K range): warp 0 lane 0 issues TMA loads into a STAGES-deep
+// ring of shared-memory buffers, warp 1 lane 0 issues the MMAs (M = 128, N = BN, K = 16
+// per instruction) and commits each stage back to the producer; after the last MMA all
+// four warps read their 32 TMEM lanes (rows) and run the epilogue.
+//
+// Shared-memory operand layout is the canonical 128-byte-swizzled one that TMA writes:
+//   K-major tile (rows x 64 elements of 2 bytes): row r at r*128 B, 8-row groups 1024 B apart
+//     -> descriptor SBO = 1024 B, LBO unused (1); the k-th 16-element slice starts at +32k B.
+//   M-major tile (64 K-rows x 128 M-elements): two TMA boxes of 64 M-elements, each K-row
+//     128 B, box 1 at +8 KB -> descriptor LBO = 8192 B (next 64 M-elements), SBO = 1024 B
+//     (next 8 K-rows); the k-th 16-row slice starts at +2048k B.
+// Every wait is bounded (globaltimer); on expiry the error word is set and the CTA unwinds.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace lls {
 
-int simt_projection_lowp(const ProjCall& c, cudaStream_t st);
-int simt_update_lowp(const UpdCall& c, cudaStream_t st);
-size_t simt_partial_floats(int m, int w1, int w2);
+int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, float* R12, int ldr,
+                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st);
 
-size_t proj_partial_floats(int m, int w1, int w2) { return simt_partial_floats(m, w1, w2); }
-int gemm_projection(const ProjCall& c, cudaStream_t st) { return simt_projection_lowp(c, st); }
-int gemm_update(const UpdCall& c, cudaStream_t st) { return simt_update_lowp(c, st); }
+constexpr int kTcThreads = 128;
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 64;
+constexpr int kTcStages = 4;
+constexpr int kTcABytes = kTcBM * kTcBK * 2;     // 16 KB
+enum TcEpi { TC_EPI_PARTIAL = 0, TC_EPI_UPDATE = 1 };
+
+struct TcArgs {
+    int M, N, K;
+    int k_tiles_per_split;
+    uint32_t idesc;
+    float* out;          // partial base (PARTIAL) or A2 (UPDATE)
+    int ldo;
+    const int* fexp;     // UPDATE: column exponents of R12l
+    int* err;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the error word set) if the phase does not complete in time or
+// another thread already flagged an error.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int*)err != DEV_OK) return false;
+        if (globaltimer_ns() - t0 > kSpinLimitNs) {
+            atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in [0,14), LBO >> 4 in [16,30),
+// SBO >> 4 in [32,46), fixed 0b01 in [46,48), base offset 0, layout type in [61,64)
+// (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+template <int BN, bool A_MN, int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    constexpr int kBBytes = BN * kTcBK * 2;
+    constexpr int kStageBytes = kTcABytes + kBBytes;
+    extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + kTcStages * kStageBytes);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kTcStages + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages);
+    const uint32_t accb = smem_u32(bars + 2 * kTcStages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
+    const int kt_total = (a.K + kTcBK - 1) / kTcBK;
+    const int kt0 = blockIdx.z * a.k_tiles_per_split;
+    const int kt1 = min(kt_total, kt0 + a.k_tiles_per_split);
+    const int nk = kt1 - kt0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (nk > 0) {
+        if (warp == 0 && lane == 0) {
+            // ---- TMA producer ----
+            for (int i = 0; i < nk && ok; ++i) {
+                const int s = i % kTcStages;
+                const uint32_t ph = (i / kTcStages) & 1;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1, a.err)) { ok = false; break; }
+                const uint32_t sa = smem_u32(smem + s * kStageBytes);
+                const uint32_t sb = sa + kTcABytes;
+                mbar_expect_tx(full0 + 8 * s, kStageBytes);
+                const int k0 = (kt0 + i) * kTcBK;
+                if (A_MN) {
+                    tma_load_2d(sa, &tmA, m0, k0, full0 + 8 * s);
+                    tma_load_2d(sa + kTcABytes / 2, &tmA, m0 + 64, k0, full0 + 8 * s);
+                } else {
+                    tma_load_2d(sa, &tmA, k0, m0, full0 + 8 * s);
+                }
+                tma_load_2d(sb, &tmB, k0, n0, full0 + 8 * s);
+            }
+        } else if (warp == 1 && lane == 0) {
+            // ---- MMA issuer ----
+            for (int i = 0; i < nk && ok; ++i) {
+                const int s = i % kTcStages;
+                const uint32_t ph = (i / kTcStages) & 1;
+                if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * kStageBytes);
+                const uint32_t sb = sa + kTcABytes;
+#pragma unroll
+                for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                    const uint64_t ad = A_MN ? smem_desc(sa + kk * 2048, 8192, 1024)
+                                             : smem_desc(sa + kk * 32, 16, 1024);
+                    const uint64_t bd = smem_desc(sb + kk * 32, 16, 1024);
+                    mma_f16(tmem, ad, bd, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            if (ok) mma_commit(accb);
+        }
+        // ---- epilogue: all four warps, thread (warp, lane) owns tile row 32*warp + lane ----
+        __syncwarp();
+        const bool ready = mbar_wait(accb, 0, a.err);
+        __syncwarp();
+        tc_fence_after();
+        if (ready) {
+            const int i = m0 + warp * 32 + lane;
+            float fs[BN / 16];
+            (void)fs;
+#pragma unroll 1
+            for (int c = 0; c < BN / 16; ++c) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+                if (i < a.M) {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const int j = n0 + c * 16 + r;
+                        if (j < a.N) {
+                            if (EPI == TC_EPI_PARTIAL) {
+                                a.out[(size_t)blockIdx.z * a.M * a.N + (size_t)i + (size_t)j * a.M] = v[r];
+                            } else {
+                                const size_t idx = (size_t)i + (size_t)j * a.ldo;
+                                a.out[idx] = a.out[idx] - v[r] * pow2f(-a.fexp[j]);
+                            }
+                        }
+                    }
+                }
+            }
+        } else {
+            // The pipeline gave up: let in-flight TMA writes into this CTA's shared memory
+            // land before the CTA exits (bounded).
+            if (warp == 0 && lane == 0) {
+                const unsigned long long t0 = globaltimer_ns();
+                for (int s = 0; s < kTcStages; ++s)
+                    while (!mbar_try_wait(full0 + 8 * s, 0) && !mbar_try_wait(full0 + 8 * s, 1) &&
+                           globaltimer_ns() - t0 < kSpinLimitNs) {
+                    }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D tensor map over a column-major matrix: `inner` contiguous elements per column,
+// `outer` columns `ld` elements apart, boxes of box_inner x box_outer, 128-byte swizzle.
+static int make_tmap(CUtensorMap* tm, const void* base, int lowp, uint64_t inner, uint64_t outer, uint64_t ld,
+                     uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return LLS_ERR_CUDA;
+    if (((uintptr_t)base & 15) != 0 || ((ld * 2) & 15) != 0) return LLS_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(tm, lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? LLS_OK : LLS_ERR_CUDA;
+}
+
+static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
+    const uint32_t fmt = lowp == 0 ? 0u : 1u;       // 0 = F16, 1 = BF16
+    uint32_t d = 0;
+    d |= 1u << 4;                                    // D = F32
+    d |= fmt << 7;                                   // A type
+    d |= fmt << 10;                                  // B type
+    d |= (a_mn ? 1u : 0u) << 15;                     // A major (0 = K, 1 = MN)
+    d |= (uint32_t)(bn >> 3) << 17;                  // N / 8
+    d |= (uint32_t)(kTcBM >> 4) << 24;               // M / 16
+    return d;
+}
+
+static int pick_bn(int n) { return n <= 64 ? 64 : (n <= 128 ? 128 : 256); }
+
+template <int BN, bool A_MN, int EPI>
+static int launch_tc(const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
+    constexpr int smem = kTcStages * (kTcABytes + BN * kTcBK * 2) + 1024 + 256;
+    auto k = tc_gemm_kernel<BN, A_MN, EPI>;
+    static bool attr = false;
+    if (!attr) {
+        LLS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    k<<<grid, kTcThreads, smem, st>>>(tA, tB, a);
+    LLS_LAUNCH_CHECK(EPI == TC_EPI_PARTIAL ? "tc_projection" : "tc_update", st);
+    return LLS_OK;
+}
+
+template <bool A_MN, int EPI>
+static int launch_bn(int bn, const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
+    if (bn == 64) return launch_tc<64, A_MN, EPI>(tA, tB, a, grid, st);
+    if (bn == 128) return launch_tc<128, A_MN, EPI>(tA, tB, a, grid, st);
+    return launch_tc<256, A_MN, EPI>(tA, tB, a, grid, st);
+}
+
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+    }
+    return sms;
+}
+
+static void proj_split(int m, int w1, int w2, int& splits, int& ktps) {
+    const int bn = pick_bn(w2);
+    const int tiles = ceil_div(w1, kTcBM) * ceil_div(w2, bn);
+    const int kt = ceil_div(m, kTcBK);
+    int want = ceil_div(2 * sm_count(), tiles);             // about two waves of CTAs
+    int maxs = kt / 8 > 0 ? kt / 8 : 1;                      // at least 8 K tiles per CTA
+    splits = want < maxs ? want : maxs;
+    if (splits < 1) splits = 1;
+    ktps = ceil_div(kt, splits);
+    splits = ceil_div(kt, ktps);
+}
+
+size_t proj_partial_floats(int m, int w1, int w2) {
+    int splits, ktps;
+    proj_split(m, w1, w2, splits, ktps);
+    return (size_t)splits * w1 * w2;
+}
+
+int gemm_projection(const ProjCall& c, cudaStream_t st) {
+    int splits, ktps;
+    proj_split(c.m, c.w1, c.w2, splits, ktps);
+    if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
+    const int bn = pick_bn(c.w2);
+    CUtensorMap tA, tB;
+    LLS_TRY(make_tmap(&tA, c.Q1l, c.lowp, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, kTcBK, kTcBM));
+    LLS_TRY(make_tmap(&tB, c.A2l, c.lowp, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldh, kTcBK, (uint32_t)bn));
+    TcArgs a;
+    a.M = c.w1; a.N = c.w2; a.K = c.m; a.k_tiles_per_split = ktps;
+    a.idesc = make_idesc(c.lowp, bn, false);
+    a.out = c.part; a.ldo = c.w1; a.fexp = nullptr; a.err = c.err;
+    dim3 grid(ceil_div(c.w1, kTcBM), ceil_div(c.w2, bn), splits);
+    LLS_TRY((launch_bn<false, TC_EPI_PARTIAL>(bn, tA, tB, a, grid, st)));
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+}
+
+int gemm_update(const UpdCall& c, cudaStream_t st) {
+    const int bn = pick_bn(c.w2);
+    CUtensorMap tA, tB;
+    LLS_TRY(make_tmap(&tA, c.Q1l, c.lowp, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, 64, kTcBK));
+    LLS_TRY(make_tmap(&tB, c.R12l, c.lowp, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, kTcBK, (uint32_t)bn));
+    TcArgs a;
+    a.M = c.m; a.N = c.w2; a.K = c.w1; a.k_tiles_per_split = ceil_div(c.w1, kTcBK);
+    a.idesc = make_idesc(c.lowp, bn, true);
+    a.out = c.A2; a.ldo = c.ldw; a.fexp = c.f; a.err = c.err;
+    dim3 grid(ceil_div(c.m, kTcBM), ceil_div(c.w2, bn), 1);
+    return launch_bn<true, TC_EPI_UPDATE>(bn, tA, tB, a, grid, st);
+}
 
 }  // namespace lls

@@ -37,6 +37,7 @@ struct ProjCall {
     int* f;                                       // R12 column exponents (w2)
     float* part; size_t part_floats;              // split-K partials scratch
     int lowp;
+    int* err;                                     // device error word (bounded waits)
 };
 struct UpdCall {
     const void* Q1l; int ldh;                     // m x w1 low precision
@@ -45,6 +46,7 @@ struct UpdCall {
     float* A2; int ldw;                           // m x w2 FP32, updated in place
     int m, w1, w2;
     int lowp;
+    int* err;
 };
 size_t proj_partial_floats(int m, int w1, int w2);
 int gemm_projection(const ProjCall& c, cudaStream_t st);
@@ -79,6 +81,21 @@ struct KrylovCall {
 };
 size_t krylov_scratch_bytes(int m, int n, int grid);
 int krylov_solve(const KrylovCall& c, cudaStream_t st);
+
+// ---- graph replay (graph.cu) -----------------------------------------------------------------
+// Identity of one call: plain-old-data, compared bytewise (zero-initialize before filling).
+struct GraphKey {
+    int op, device;
+    int ints[8];
+    const void* ptrs[8];
+    size_t ws_bytes;
+    lls_options opts;
+};
+// Enqueues one call on `st`; ev (may be null) receives 3 phase events; `capturing` selects
+// external event-record nodes.
+typedef int (*EnqueueFn)(void* ctx, cudaStream_t st, cudaEvent_t* ev, bool capturing);
+int run_graphed(const GraphKey& key, cudaStream_t st, EnqueueFn fn, void* ctx, cudaEvent_t* ev_out);
+void record_phase(cudaEvent_t ev, cudaStream_t st, bool capturing);
 
 // ---- misc (util.cu) -------------------------------------------------------------------------
 int copy_matrix(const float* src, int lds, float* dst, int ldd, int m, int n, cudaStream_t st);

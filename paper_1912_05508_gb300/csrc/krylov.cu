@@ -386,7 +386,7 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cgls_kernel, dim3(grid), dim3(kKThreads), args, smem, st));
-    note_launch();
+    note_launch("cgls", st);
     return LLS_OK;
 }
 

@@ -1,141 +1,264 @@
 // Tall-skinny panel QR: communication-avoiding QR (Eq. caqr, Sec. 3.1.3) with CGS2 leaves.
 //
-// Step 1 (Eq. caqr, circled 1): the m x b panel is split into row blocks of at most
-// 256 rows; each CTA factors one block in shared memory with CGS2 (classical Gram-Schmidt
-// with one reorthogonalization; the paper's leaf is MGS, Alg. 4).
-// Steps 2-3: the b x b R factors are stacked in groups of `fanin` and the stack is
-// factored by the same routine, level by level, until one R remains. The CTA that
-// finishes last in a group does that group's factorization (atomic arrival counter,
-// no spin-wait), so the tree costs no extra launches.
-// Steps 4-5: a second kernel multiplies each block's Q by the product of the b x b
-// slices of the tree Q factors on its path to the root.
+// Step 1 (Eq. caqr, circled 1): the m x b panel is split into row blocks of at most 1024 rows;
+// each CTA factors one block with CGS2 (classical Gram-Schmidt with one reorthogonalization;
+// the paper's leaf is MGS, Alg. 4), holding the block in registers, 4 rows per thread.
+// Steps 2-3: the b x b R factors are stacked in groups of `fanin` (1024 / b rows) and the
+// stack is factored by the same routine, level by level, until one R remains. The CTA that
+// finishes last in a group does that group's factorization (atomic arrival counter, no
+// spin-wait), so the tree costs no extra launches.
+// Steps 4-5: a second kernel multiplies each block's Q by the product of the b x b slices
+// of the tree Q factors on its path to the root (skipped when the panel is one block).
+//
+// CGS2 column k, all in registers: one block-wide reduction gives h = Q_<k^T a_k, then
+// a_k -= Q_<k h; a second gives h' = Q_<k^T a_k together with ||a_k||^2, then a_k -= Q_<k h'
+// and ||a_k''||^2 = ||a_k||^2 - ||h'||^2 (h' is at the rounding level after the first pass;
+// when it is not, the norm is reduced directly). R_<k,k = h + h', R_kk = ||a_k''||,
+// q_k = a_k'' / R_kk (q_k = 0 when R_kk = 0). Each reduction is a butterfly transpose-
+// reduction across the warp followed by one pass through shared memory.
 //
 // Output: Q overwrites the panel in the FP32 work matrix W, a copy rounded to the
 // tensor-core input type goes to Wh (feeds the next products), R goes to the R matrix.
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace lls {
 
-constexpr int kPanelThreads = 256;      // one row per thread: node height <= 256
-constexpr int kPanelLd = 33;            // padded row stride of the smem block (conflict-free)
+constexpr int kPanelThreads = 256;
+constexpr int kPanelWarps = kPanelThreads / 32;
+constexpr int kRPT = 4;                               // rows per thread
+constexpr int kNodeRows = kPanelThreads * kRPT;       // 1024-row blocks and tree nodes
 
 struct PanelLevels {
-    int nlev;                        // tree levels above the leaves
-    int nodes[kMaxPanelLevels + 1];  // node count per level (level 0 = leaves)
-    int rbuf_off[kMaxPanelLevels + 1];   // first R block of each level in rbuf (units of 32x32)
-    int qbuf_off[kMaxPanelLevels + 1];   // first Q block of each level in qbuf (units of 256x32)
-    int cnt_off[kMaxPanelLevels + 1];    // first counter of each level
+    int nlev;                              // tree levels above the leaves
+    int nodes[kMaxPanelLevels + 1];        // node count per level (level 0 = leaves)
+    int rbuf_off[kMaxPanelLevels + 1];     // first R block of each level in rbuf (32x32 blocks)
+    int qbuf_off[kMaxPanelLevels + 1];     // first Q block of each level in qbuf (1024x32 blocks)
+    int cnt_off[kMaxPanelLevels + 1];      // first counter of each level
 };
 
 struct PanelArgs {
-    float* W; int ldw;          // FP32 work matrix, panel at columns [c0, c0+b)
-    void* Wh; int ldh;          // low-precision copy (type per `lowp`)
-    float* R; int ldr;          // R output, block at [c0, c0+b)^2
-    int m, c0, b, fanin, leaf_rows_unused;
-    int P0;                     // number of leaf blocks
-    int lowp;                   // 0 = FP16, 1 = BF16, 3 = none (FP32 products)
-    float* rbuf;                // per-node R factors, 32x32 row-major blocks
-    float* qbuf;                // per-node tree Q factors, 256x32 row-major blocks
-    unsigned* cnt;              // per-node arrival counters (zero on entry, reset on exit)
+    float* W; int ldw;
+    void* Wh; int ldh;
+    float* R; int ldr;
+    int m, c0, b, fanin, P0, lowp;
+    float* rbuf;
+    float* qbuf;
+    unsigned* cnt;
     PanelLevels lv;
 };
 
 __device__ __forceinline__ void leaf_range(int m, int P0, int i, int& s, int& e) {
-    int base = m / P0, extra = m % P0;
+    const int base = m / P0, extra = m % P0;
     s = i * base + min(i, extra);
     e = s + base + (i < extra ? 1 : 0);
 }
 
-// CGS2 of the block held in S (kPanelThreads rows x b columns, row stride kPanelLd, zero
-// padded). Thread t owns row t. Column k: h = Q_<k^T a_k and a_k -= Q_<k h, twice; then
-// R_<k,k = h + h', R_kk = ||a_k||, q_k = a_k / R_kk (q_k = 0 when R_kk = 0).
-// On return S[:, :b] = Q and Rs (32 x 33, row-major) = R.
-__device__ void cgs2_block(float* S, int b, float* red, float* Rs) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    float* myrow = S + t * kPanelLd;
-    const float* wrows = S + (warp * 32) * kPanelLd;
-    int parity = 0;
-    for (int k = 0; k < b; ++k) {
-        float hacc = 0.f;
-        if (k > 0) {
-            for (int pass = 0; pass < 2; ++pass) {
-                // lane j: partial of q_j . a_k over this warp's 32 rows
-                float part = 0.f;
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r)
-                    part = fmaf(wrows[r * kPanelLd + lane], wrows[r * kPanelLd + k], part);
-                float* rb = red + parity * 256;
-                parity ^= 1;
-                rb[warp * 32 + lane] = part;
-                __syncthreads();
-                float h = 0.f;
+__host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
+
+// Butterfly transpose-reduction of S values held by every lane: afterwards lane L holds the
+// warp-wide sum of value index (L mod S).
+template <int S>
+__device__ __forceinline__ float warp_transpose_reduce(float (&x)[S]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) h += rb[w * 32 + lane];
-                if (lane >= k) h = 0.f;
-                hacc += h;
-                float ak = myrow[k];
-                for (int j = 0; j < k; ++j) ak = fmaf(-myrow[j], __shfl_sync(kFullMask, h, j), ak);
-                myrow[k] = ak;
-                if (pass == 0) __syncthreads();
-            }
+    for (int o = S / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? x[i] : x[i + o];
+            const float keep = up ? x[i + o] : x[i];
+            x[i] = keep + __shfl_xor_sync(kFullMask, send, o);
         }
-        float ak = myrow[k];
-        float nn = ak * ak;
+    }
+    float r = x[0];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(kFullMask, nn, o);
-        float* rb = red + parity * 256;
-        parity ^= 1;
-        if (lane == 0) rb[warp] = nn;
-        __syncthreads();
-        float tot = 0.f;
+    for (int o = S; o < 32; o <<= 1) r += __shfl_xor_sync(kFullMask, r, o);
+    return r;
+}
+
+// Block-wide sum of S values (index j valid for j < S); returns, in every lane L, the block
+// total of index (L mod S). red: two buffers of kPanelWarps x 32 floats, alternated.
+template <int S>
+__device__ __forceinline__ float block_reduce_vec(float (&x)[S], float* red, int& parity) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float w = warp_transpose_reduce<S>(x);
+    float* rb = red + parity * (kPanelWarps * 32);
+    parity ^= 1;
+    rb[warp * 32 + lane] = w;
+    __syncthreads();
+    float t = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) tot += rb[w];
-        float nrm = sqrtf(tot);
-        myrow[k] = nrm > 0.f ? ak / nrm : 0.f;
-        if (warp == 0 && lane < k) Rs[lane * kPanelLd + k] = hacc;
-        if (t == 0) Rs[k * kPanelLd + k] = nrm;
-        __syncthreads();
+    for (int q = 0; q < kPanelWarps; ++q) t += rb[q * 32 + (lane % S)];
+    return t;
+}
+
+// One column K of CGS2 on the register-resident block v (see file comment).
+template <int B, int K>
+__device__ __forceinline__ void cgs2_column(float (&v)[kRPT][B], int b, float* red, int& parity,
+                                            float* Rs) {
+    if (K >= b) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float hacc = 0.f;   // lane j < K: R[j][K]
+    if constexpr (K > 0) {
+        constexpr int S1 = pow2ceil(K);
+        float p[S1];
+#pragma unroll
+        for (int j = 0; j < S1; ++j) {
+            float s = 0.f;
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][K], s);
+            }
+            p[j] = s;
+        }
+        const float h = block_reduce_vec<S1>(p, red, parity);
+        hacc = lane < K ? h : 0.f;
+        float acc[kRPT];
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) acc[r] = v[r][K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float hj = __shfl_sync(kFullMask, h, j);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) v[r][K] = acc[r];
+    }
+    // second pass (or the only one for K = 0) together with ||a_K||^2 at index K
+    constexpr int S2 = pow2ceil(K + 1);
+    float p2[S2];
+#pragma unroll
+    for (int j = 0; j < S2; ++j) {
+        float s = 0.f;
+        if (j <= K) {
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][K], s);
+        }
+        p2[j] = s;
+    }
+    const float h2 = block_reduce_vec<S2>(p2, red, parity);
+    const float nn = __shfl_sync(kFullMask, h2, K);
+    float normsq = nn;
+    if constexpr (K > 0) {
+        float acc[kRPT];
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) acc[r] = v[r][K];
+        float hh = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float hj = __shfl_sync(kFullMask, h2, j);
+            hh = fmaf(hj, hj, hh);
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) v[r][K] = acc[r];
+        hacc += lane < K ? h2 : 0.f;
+        normsq = nn - hh;
+        if (!(normsq >= 0.25f * nn)) {     // second pass removed a large part: reduce directly
+            float d[1];
+            d[0] = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) d[0] = fmaf(v[r][K], v[r][K], d[0]);
+            normsq = block_reduce_vec<1>(d, red, parity);
+        }
+    }
+    const float nrm = sqrtf(fmaxf(normsq, 0.f));
+    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+#pragma unroll
+    for (int r = 0; r < kRPT; ++r) v[r][K] *= inv;
+    if (warp == 0) {
+        if (lane < K) Rs[lane * 33 + K] = hacc;
+        if (lane == K) Rs[K * 33 + K] = nrm;
     }
 }
 
-__global__ void __launch_bounds__(kPanelThreads)
+template <int B, int... Ks>
+__device__ __forceinline__ void cgs2_all(float (&v)[kRPT][B], int b, float* red, int& parity, float* Rs,
+                                         std::integer_sequence<int, Ks...>) {
+    (cgs2_column<B, Ks>(v, b, red, parity, Rs), ...);
+}
+
+template <int B>
+__device__ __forceinline__ void cgs2_block(float (&v)[kRPT][B], int b, float* red, float* Rs) {
+    int parity = 0;
+    cgs2_all<B>(v, b, red, parity, Rs, std::make_integer_sequence<int, B>{});
+    __syncthreads();   // Rs complete
+}
+
+template <typename TL>
+__device__ __forceinline__ void store_lowp(void* Wh, size_t idx, float v) {
+    reinterpret_cast<TL*>(Wh)[idx] = LowPrec<TL>::from_float(v);
+}
+
+__device__ __forceinline__ void store_q(const PanelArgs& a, int row, int j, float q) {
+    a.W[(size_t)row + (size_t)(a.c0 + j) * a.ldw] = q;
+    const size_t hidx = (size_t)row + (size_t)(a.c0 + j) * a.ldh;
+    if (a.lowp == 0) store_lowp<__half>(a.Wh, hidx, q);
+    else if (a.lowp == 1) store_lowp<__nv_bfloat16>(a.Wh, hidx, q);
+}
+
+__device__ __forceinline__ void write_r11(const PanelArgs& a, const float* Rs) {
+    for (int i = threadIdx.x; i < a.b * a.b; i += kPanelThreads) {
+        const int r = i % a.b, c = i / a.b;
+        a.R[(size_t)(a.c0 + r) + (size_t)(a.c0 + c) * a.ldr] = r <= c ? Rs[r * 33 + c] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void write_rblock(float* dst, const float* Rs) {
+    for (int i = threadIdx.x; i < 1024; i += kPanelThreads) dst[i] = Rs[(i >> 5) * 33 + (i & 31)];
+}
+
+template <int B>
+__global__ void __launch_bounds__(kPanelThreads, 1)
 panel_leaf_tree_kernel(PanelArgs a) {
-    __shared__ float S[kPanelThreads * kPanelLd];
-    __shared__ float red[2 * 256];
-    __shared__ float Rs[32 * kPanelLd];
+    __shared__ float red[2 * kPanelWarps * 32];
+    __shared__ float Rs[32 * 33];
     __shared__ int s_last;
     const int t = threadIdx.x;
     const int b = a.b;
+    for (int i = t; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
 
-    for (int i = t; i < 32 * kPanelLd; i += kPanelThreads) Rs[i] = 0.f;
-
-    // ---- step 1: factor this CTA's row block ----
+    // ---- step 1: factor this CTA's row block (rows t + 256 r) ----
     int s, e;
     leaf_range(a.m, a.P0, blockIdx.x, s, e);
     const int rows = e - s;
-    float* myrow = S + t * kPanelLd;
-    for (int j = 0; j < 32; ++j) {
-        float v = 0.f;
-        if (t < rows && j < b) v = a.W[(size_t)(s + t) + (size_t)(a.c0 + j) * a.ldw];
-        myrow[j] = v;
+    float v[kRPT][B];
+#pragma unroll
+    for (int r = 0; r < kRPT; ++r) {
+        const int lr = t + r * kPanelThreads;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            v[r][j] = (lr < rows && j < b) ? a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] : 0.f;
     }
     __syncthreads();
-    cgs2_block(S, b, red, Rs);
-    if (t < rows)
-        for (int j = 0; j < b; ++j) a.W[(size_t)(s + t) + (size_t)(a.c0 + j) * a.ldw] = myrow[j];
+    cgs2_block<B>(v, b, red, Rs);
 
-    if (a.P0 == 1) {   // the leaf is the whole panel: R11 is final
-        for (int i = t; i < b * b; i += kPanelThreads) {
-            int r = i % b, c = i / b;
-            a.R[(size_t)(a.c0 + r) + (size_t)(a.c0 + c) * a.ldr] = r <= c ? Rs[r * kPanelLd + c] : 0.f;
+    if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+            const int lr = t + r * kPanelThreads;
+            if (lr < rows)
+#pragma unroll
+                for (int j = 0; j < B; ++j)
+                    if (j < b) store_q(a, s + lr, j, v[r][j]);
         }
+        write_r11(a, Rs);
         return;
     }
-    {
-        float* dst = a.rbuf + (size_t)(a.lv.rbuf_off[0] + blockIdx.x) * 1024;
-        for (int i = t; i < 1024; i += kPanelThreads) dst[i] = Rs[(i >> 5) * kPanelLd + (i & 31)];
+#pragma unroll
+    for (int r = 0; r < kRPT; ++r) {
+        const int lr = t + r * kPanelThreads;
+        if (lr < rows)
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j < b) a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] = v[r][j];
     }
+    write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[0] + blockIdx.x) * 1024, Rs);
 
     // ---- steps 2-3: combine stacked R factors up the tree (last arriver does the work) ----
     int node = blockIdx.x;
@@ -146,106 +269,101 @@ panel_leaf_tree_kernel(PanelArgs a) {
         __syncthreads();
         if (t == 0) {
             unsigned* c = a.cnt + a.lv.cnt_off[l + 1] + parent;
-            unsigned old = atomicAdd(c, 1u);
+            const unsigned old = atomicAdd(c, 1u);
             s_last = (old == (unsigned)(nch - 1));
             if (s_last) atomicExch(c, 0u);   // self-reset for the next panel
         }
         __syncthreads();
         if (!s_last) return;
         __threadfence();
-        // stack the children's R factors: row t = child (t / b), row (t % b) of its R
-        const int child = t / b, rr = t % b;
-        const float* src = a.rbuf + (size_t)(a.lv.rbuf_off[l] + parent * a.fanin + child) * 1024;
-        for (int j = 0; j < 32; ++j) {
-            float v = 0.f;
-            if (child < nch && j < b) v = __ldcg(src + rr * 32 + j);
-            myrow[j] = v;
+        const float* src0 = a.rbuf + (size_t)(a.lv.rbuf_off[l] + parent * a.fanin) * 1024;
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+            const int rho = t + r * kPanelThreads;        // stacked row
+            const int child = rho / b, rr = rho % b;
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                v[r][j] = (child < nch && j < b) ? __ldcg(src0 + (size_t)child * 1024 + rr * 32 + j) : 0.f;
         }
-        for (int i = t; i < 32 * kPanelLd; i += kPanelThreads) Rs[i] = 0.f;
+        for (int i = t; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
         __syncthreads();
-        cgs2_block(S, b, red, Rs);
-        // tree Q of this node (rows = nch*b, row-major 256 x 32 block)
-        float* qdst = a.qbuf + (size_t)(a.lv.qbuf_off[l + 1] + parent) * (256 * 32);
-        for (int j = 0; j < 32; ++j) qdst[t * 32 + j] = myrow[j];
+        cgs2_block<B>(v, b, red, Rs);
+        float* qdst = a.qbuf + (size_t)(a.lv.qbuf_off[l + 1] + parent) * (kNodeRows * 32);
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+            const int rho = t + r * kPanelThreads;
+            if (rho < nch * b)
+#pragma unroll
+                for (int j = 0; j < B; ++j) qdst[rho * 32 + j] = v[r][j];
+        }
         if (a.lv.nodes[l + 1] == 1) {
-            for (int i = t; i < b * b; i += kPanelThreads) {
-                int r = i % b, c = i / b;
-                a.R[(size_t)(a.c0 + r) + (size_t)(a.c0 + c) * a.ldr] = r <= c ? Rs[r * kPanelLd + c] : 0.f;
-            }
+            write_r11(a, Rs);
             return;
         }
-        float* dst = a.rbuf + (size_t)(a.lv.rbuf_off[l + 1] + parent) * 1024;
-        for (int i = t; i < 1024; i += kPanelThreads) dst[i] = Rs[(i >> 5) * kPanelLd + (i & 31)];
+        write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[l + 1] + parent) * 1024, Rs);
         node = parent;
     }
 }
 
-template <typename TL>
-__device__ __forceinline__ void store_lowp(void* Wh, size_t idx, float v) {
-    reinterpret_cast<TL*>(Wh)[idx] = LowPrec<TL>::from_float(v);
-}
-
-// Steps 4-5: Q_i <- Q_i * (S_1 S_2 ... S_top), S_l the b x b slice of the level-l tree Q on
-// the block's path; writes the FP32 Q and its low-precision copy.
+// Steps 4-5: Q_i <- Q_i (S_1 S_2 ... S_top), S_l the b x b slice of the level-l tree Q on the
+// block's path; writes the FP32 Q and its low-precision copy.
+template <int B>
 __global__ void __launch_bounds__(kPanelThreads)
 panel_reconstruct_kernel(PanelArgs a) {
     __shared__ float T[32 * 33];
     __shared__ float U[32 * 33];
     const int t = threadIdx.x;
     const int b = a.b;
-    // T = I
-    for (int i = t; i < 32 * 33; i += kPanelThreads) T[i] = 0.f;
-    __syncthreads();
-    if (t < 32) T[t * 33 + t] = 1.f;
+    for (int i = t; i < 32 * 33; i += kPanelThreads) T[i] = (i / 33 == i % 33) ? 1.f : 0.f;
     __syncthreads();
     int node = blockIdx.x;
     for (int l = 0; l < a.lv.nlev; ++l) {
         const int parent = node / a.fanin, child = node % a.fanin;
-        const float* q = a.qbuf + (size_t)(a.lv.qbuf_off[l + 1] + parent) * (256 * 32) + (size_t)child * b * 32;
-        // U = T * S_l (b x b), S_l[r][c] = q[r*32 + c]
+        const float* q = a.qbuf + (size_t)(a.lv.qbuf_off[l + 1] + parent) * (kNodeRows * 32) + (size_t)child * b * 32;
         for (int i = t; i < b * b; i += kPanelThreads) {
-            int r = i / b, c = i % b;
+            const int r = i / b, c = i % b;
             float acc = 0.f;
             for (int k = 0; k < b; ++k) acc = fmaf(T[r * 33 + k], __ldcg(q + k * 32 + c), acc);
             U[r * 33 + c] = acc;
         }
         __syncthreads();
-        for (int i = t; i < b * b; i += kPanelThreads) {
-            int r = i / b, c = i % b;
-            T[r * 33 + c] = U[r * 33 + c];
-        }
+        for (int i = t; i < b * b; i += kPanelThreads) T[(i / b) * 33 + (i % b)] = U[(i / b) * 33 + (i % b)];
         __syncthreads();
         node = parent;
     }
     int s, e;
     leaf_range(a.m, a.P0, blockIdx.x, s, e);
-    if (t >= e - s) return;
-    const size_t row = (size_t)(s + t);
-    float q[32];
+    const int rows = e - s;
+#pragma unroll 1
+    for (int r = 0; r < kRPT; ++r) {
+        const int lr = t + r * kPanelThreads;
+        if (lr >= rows) break;
+        const size_t row = (size_t)(s + lr);
+        float q[B];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) q[j] = j < b ? a.W[row + (size_t)(a.c0 + j) * a.ldw] : 0.f;
-    for (int j = 0; j < b; ++j) {
-        float acc = 0.f;
+        for (int j = 0; j < B; ++j) q[j] = j < b ? a.W[row + (size_t)(a.c0 + j) * a.ldw] : 0.f;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) acc = fmaf(q[k], T[k * 33 + j], acc);
-        const size_t widx = row + (size_t)(a.c0 + j) * a.ldw;
-        a.W[widx] = acc;
-        const size_t hidx = row + (size_t)(a.c0 + j) * a.ldh;
-        if (a.lowp == 0) store_lowp<__half>(a.Wh, hidx, acc);
-        else if (a.lowp == 1) store_lowp<__nv_bfloat16>(a.Wh, hidx, acc);
+        for (int j = 0; j < B; ++j) {
+            if (j >= b) break;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < B; ++k) acc = fmaf(q[k], T[k * 33 + j], acc);
+            store_q(a, (int)row, j, acc);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
+static int bucket(int b) { return b <= 8 ? 8 : (b <= 16 ? 16 : 32); }
+
 static void panel_levels(int m, int b, PanelLevels& lv, int& P0, int& fanin) {
-    P0 = ceil_div(m, kPanelThreads);
-    int bp = b <= 8 ? 8 : (b <= 16 ? 16 : 32);
-    fanin = kPanelThreads / bp;
+    P0 = ceil_div(m, kNodeRows);
+    fanin = kNodeRows / bucket(b);
     lv.nodes[0] = P0;
     lv.nlev = 0;
-    while (lv.nodes[lv.nlev] > 1) {
+    while (lv.nodes[lv.nlev] > 1 && lv.nlev < kMaxPanelLevels) {
         lv.nodes[lv.nlev + 1] = ceil_div(lv.nodes[lv.nlev], fanin);
         lv.nlev++;
     }
@@ -266,22 +384,33 @@ void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t
     size_t nodes = 0, upper = 0;
     for (int l = 0; l <= lv.nlev; ++l) { nodes += lv.nodes[l]; if (l > 0) upper += lv.nodes[l]; }
     rbuf_floats = nodes * 1024;
-    qbuf_floats = (upper + 1) * 256 * 32;
+    qbuf_floats = (upper + 1) * (size_t)kNodeRows * 32;
     cnt_words = upper + 1;
 }
 
+template <int B>
+static int launch_panel(const PanelArgs& a, cudaStream_t st) {
+    panel_leaf_tree_kernel<B><<<a.P0, kPanelThreads, 0, st>>>(a);
+    LLS_LAUNCH_CHECK("panel_leaf_tree", st);
+    if (a.P0 > 1) {
+        panel_reconstruct_kernel<B><<<a.P0, kPanelThreads, 0, st>>>(a);
+        LLS_LAUNCH_CHECK("panel_reconstruct", st);
+    }
+    return LLS_OK;
+}
+
 int panel_qr(const PanelCall& c, cudaStream_t st) {
+    if (c.b < 1 || c.b > 32) return LLS_ERR_UNSUPPORTED;
     PanelArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
-    a.rbuf = c.rbuf; a.qbuf = c.qbuf; a.cnt = c.cnt; a.leaf_rows_unused = 0;
+    a.rbuf = c.rbuf; a.qbuf = c.qbuf; a.cnt = c.cnt;
     panel_levels(c.m, c.b, a.lv, a.P0, a.fanin);
-    if (a.lv.nlev > kMaxPanelLevels || c.b < 1 || c.b > 32) return LLS_ERR_UNSUPPORTED;
-    panel_leaf_tree_kernel<<<a.P0, kPanelThreads, 0, st>>>(a);
-    LLS_LAUNCH_CHECK();
-    panel_reconstruct_kernel<<<a.P0, kPanelThreads, 0, st>>>(a);
-    LLS_LAUNCH_CHECK();
-    return LLS_OK;
+    if (a.lv.nodes[a.lv.nlev] != 1) return LLS_ERR_UNSUPPORTED;
+    const int bk = bucket(c.b);
+    if (bk == 8) return launch_panel<8>(a, st);
+    if (bk == 16) return launch_panel<16>(a, st);
+    return launch_panel<32>(a, st);
 }
 
 }  // namespace lls

@@ -57,7 +57,7 @@ static int inv_rec(const float* R, int ldr, int c0, int w, int pw, float* M, int
                    int* err, cudaStream_t st) {
     if (w <= pw) {
         diag_block_inverse_kernel<<<1, 32, 0, st>>>(R, ldr, c0, w, M, ldm, err);
-        LLS_LAUNCH_CHECK();
+        LLS_LAUNCH_CHECK("diag_block_inverse", st);
         return LLS_OK;
     }
     const int w1 = split_point_host(w, pw), w2 = w - w1;
@@ -80,7 +80,7 @@ int tri_inverse(const float* R, int ldr, int n, int pw, float* Minv, float* Mt, 
     if (Mt) {
         dim3 grid(ceil_div(n, 32), ceil_div(n, 32));
         transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(Minv, n, Mt, n, n);
-        LLS_LAUNCH_CHECK();
+        LLS_LAUNCH_CHECK("transpose", st);
     }
     return LLS_OK;
 }

@@ -20,7 +20,7 @@ __global__ void check_diag_kernel(const float* __restrict__ R, int ldr, int n, i
 
 int check_diag(const float* R, int ldr, int n, int* dev_err, cudaStream_t st) {
     check_diag_kernel<<<ceil_div(n, 256) < 64 ? ceil_div(n, 256) : 64, 256, 0, st>>>(R, ldr, n, dev_err);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("check_diag", st);
     return LLS_OK;
 }
 
@@ -34,7 +34,7 @@ int zero_lower(float* R, int ldr, int n, cudaStream_t st) {
     if (n <= 1) return LLS_OK;
     dim3 grid(ceil_div(n, 256) < 16 ? ceil_div(n, 256) : 16, n);
     zero_lower_kernel<<<grid, 256, 0, st>>>(R, ldr, n);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("zero_lower", st);
     return LLS_OK;
 }
 
@@ -72,9 +72,9 @@ __global__ void sum_parts_kernel(const double* part, int np, double* out) {
 int fro_sumsq(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t st) {
     dim3 grid(ceil_div(m, 256) < 8 ? ceil_div(m, 256) : 8, n < 512 ? n : 512);
     sumsq_kernel<<<grid, 256, 0, st>>>(A, lda, m, n, part);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("sumsq", st);
     sum_parts_kernel<<<1, 32, 0, st>>>(part, (int)(grid.x * grid.y), out);
-    LLS_LAUNCH_CHECK();
+    LLS_LAUNCH_CHECK("sum_parts", st);
     return LLS_OK;
 }
 

@@ -20,7 +20,8 @@ STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_S
           -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED"}
 
 EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
-           "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve")
+           "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve",
+           "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update")
 
 
 class lls_options(C.Structure):
@@ -72,6 +73,12 @@ def load(path: str = LIB_PATH):
     lib.lls_solve.argtypes = [i, i, vp, i, vp, vp, vp, i, vp, sz, C.POINTER(lls_options),
                               C.POINTER(lls_info), vp]
     lib.lls_solve.restype = i
+    lib.lls_lowp_projection_workspace_size.argtypes = [i, i, i]
+    lib.lls_lowp_projection_workspace_size.restype = sz
+    lib.lls_lowp_projection.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp, sz, vp]
+    lib.lls_lowp_projection.restype = i
+    lib.lls_lowp_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, vp, i, vp, sz, vp]
+    lib.lls_lowp_update.restype = i
     _lib = lib
     return lib
 
@@ -123,6 +130,21 @@ def lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream) 
     return load().lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes,
                             C.byref(opts) if opts is not None else None,
                             C.byref(info) if info is not None else None, stream)
+
+
+def lls_lowp_projection_workspace_size(m, w1, w2) -> int:
+    return load().lls_lowp_projection_workspace_size(m, w1, w2)
+
+
+def lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f, ws, ws_bytes,
+                        stream) -> int:
+    return load().lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f,
+                                      ws, ws_bytes, stream)
+
+
+def lls_lowp_update(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes, stream) -> int:
+    return load().lls_lowp_update(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes,
+                                  stream)
 
 
 # ---- torch helpers (allocation and pointer passing only) -----------------------------------

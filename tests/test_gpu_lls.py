@@ -66,3 +66,33 @@ def test_iteration_cap_reports_not_converged():
     p = synth.svd_lls(1024, 128, "geometric", 1e3, seed=1)
     x, info = run(p, prec="bf16", target="fp64", max_iter=2)
     assert info["status_code"] == 1 and info["iters"] == 2
+
+
+def test_graph_replay_matches_direct_path():
+    # On a non-default stream repeated identical calls are replayed from a captured CUDA
+    # graph; the result must be bitwise identical to the direct (default-stream) path.
+    p = synth.svd_lls(2000, 160, "geometric", 1e3, seed=31)
+    A = lls.colmajor(p.A)
+    b = torch.from_numpy(p.b).cuda()
+    x0, info0 = lls.solve(A, b)
+    s = torch.cuda.Stream()
+    o = lls.make_options()
+    nb = lls.lls_solve_workspace_size(2000, 160, o)
+    ws = lls.workspace(nb)
+    xs = []
+    x = torch.empty(160, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    launches = []
+    for _ in range(3):
+        info = lls.lls_info()
+        c0 = lls.lls_kernel_launch_count()
+        with torch.cuda.stream(s):
+            st = lls.lls_solve(2000, 160, A.data_ptr(), 2000, b.data_ptr(), x.data_ptr(), None, 160,
+                               ws.data_ptr(), ws.numel(), o, info, s.cuda_stream)
+        assert st == 0 and info.iters == info0["iters"]
+        launches.append(lls.lls_kernel_launch_count() - c0)
+        xs.append(x.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(xs[0], x0) and torch.equal(xs[1], x0) and torch.equal(xs[2], x0)
+    # every replay accounts for the same kernel count as the captured call
+    assert launches[0] == launches[1] == launches[2] > 10
