@@ -75,6 +75,19 @@ __device__ __forceinline__ void dot2_step(float& s, float& c, float a, float th,
     c = __fadd_rn(c, __fadd_rn(e, e2));
 }
 
+// Warp-wide sum of double-float values (s, c) with TwoSum at every butterfly level.
+__device__ __forceinline__ void warp_sum_df(float& s, float& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(kFullMask, s, o);
+        const float c2 = __shfl_xor_sync(kFullMask, c, o);
+        float t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+}
+
 __device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);
     lo = __double2float_rn(__dsub_rn(v, (double)hi));

@@ -1,5 +1,12 @@
 // R-preconditioned CGLS (Alg. 5, Sec. 3.2.3) as one persistent cooperative kernel.
 //
+// Products with A: for n <= 4096 each iteration makes ONE pass over A. A is streamed in
+// 4-row blocks through a double-buffered shared-memory ring (cp.async); for each block the
+// CTA forms q = A t on those rows (block-wide reduction), then accumulates A^T q and A^T r
+// for its columns from the same shared-memory copy. After the pass, with delta = ||q||^2
+// and alpha = gamma / delta known, u = A^T r_new = A^T r - alpha A^T q. Larger n uses two
+// passes (q = A t; then u = A^T r after the r update).
+//
 // The loop of Alg. 5, with the slips of the printed listing read as: step length
 // alpha = gamma / delta, solution update x += alpha R^{-1} p, and the preconditioned
 // start s = R^{-T} A^T r:
@@ -21,6 +28,8 @@
 //
 // All CTAs compute every reduction in the same fixed order, so they take identical
 // branch decisions; the grid barriers are bounded (common.cuh) and report a timeout.
+#include <stdlib.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -28,7 +37,7 @@ namespace lls {
 
 constexpr int kKThreads = 256;
 constexpr int kKWarps = kKThreads / 32;
-constexpr int kRowTile = 256;     // rows per A t work item (one row per thread)
+constexpr int kRowTile = 1024;    // rows per A t work item (four rows per thread)
 constexpr int kColChunk = 128;    // columns per A t work item
 constexpr int kRowChunk = 2048;   // rows per A^T r work item (staged in shared memory)
 constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
@@ -51,9 +60,12 @@ struct KArgs {
     double tol;
     int max_iter, target, x_zero;
     int nrt, nck, nrc, ncg;
+    double *v1part, *v2part;     // fused engine: per-CTA partial A^T q and A^T r, [grid][n]
+    int aligned16;               // A and lda allow 16-byte copies of 4-row column segments
+    int vec_floats;              // floats reserved at the start of dynamic smem for vectors
 };
 
-extern __shared__ float2 k_dsm[];
+extern __shared__ __align__(16) float2 k_dsm[];
 
 __device__ __forceinline__ void stage_vec(const double* __restrict__ v, int len) {
     for (int i = threadIdx.x; i < len; i += kKThreads) {
@@ -113,26 +125,50 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
     return sq;
 }
 
-// qpart[cc][i] = sum_{j in chunk cc} A[i, j] * v_j, v staged in k_dsm.
+// qpart[cc][i] = sum_{j in chunk cc} A[i, j] * v_j, v staged in k_dsm. Each thread owns 4
+// consecutive rows (one 16-byte load per column when A is 16-byte aligned), giving four
+// independent compensated accumulation chains.
 __device__ void a_times_partials(const KArgs& a) {
     const int items = a.nrt * a.nck;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int rt = it % a.nrt, cc = it / a.nrt;
-        const int i = rt * kRowTile + threadIdx.x;
-        if (i >= a.m) continue;
+        const int i0 = rt * kRowTile + 4 * threadIdx.x;
+        if (i0 >= a.m) continue;
         const int j0 = cc * kColChunk, j1 = min(a.n, j0 + kColChunk);
-        const float* rowp = a.A + i;
-        float s = 0.f, c = 0.f;
-#pragma unroll 8
-        for (int j = j0; j < j1; ++j) {
-            float2 v = k_dsm[j];
-            dot2_step(s, c, __ldg(rowp + (size_t)j * a.lda), v.x, v.y);
+        const bool full = a.aligned16 && i0 + 4 <= a.m;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        if (full) {
+            const float4* colp = reinterpret_cast<const float4*>(a.A + i0);
+            const size_t step = (size_t)a.lda / 4;
+#pragma unroll 4
+            for (int j = j0; j < j1; ++j) {
+                const float4 v = __ldg(colp + (size_t)j * step);
+                const float2 t = k_dsm[j];
+                dot2_step(s0, c0, v.x, t.x, t.y);
+                dot2_step(s1, c1, v.y, t.x, t.y);
+                dot2_step(s2, c2, v.z, t.x, t.y);
+                dot2_step(s3, c3, v.w, t.x, t.y);
+            }
+        } else {
+            for (int j = j0; j < j1; ++j) {
+                const float* col = a.A + (size_t)j * a.lda + i0;
+                const float2 t = k_dsm[j];
+                dot2_step(s0, c0, col[0], t.x, t.y);
+                if (i0 + 1 < a.m) dot2_step(s1, c1, col[1], t.x, t.y);
+                if (i0 + 2 < a.m) dot2_step(s2, c2, col[2], t.x, t.y);
+                if (i0 + 3 < a.m) dot2_step(s3, c3, col[3], t.x, t.y);
+            }
         }
-        a.qpart[(size_t)cc * a.m + i] = join_df(s, c);
+        double* out = a.qpart + (size_t)cc * a.m + i0;
+        out[0] = join_df(s0, c0);
+        if (i0 + 1 < a.m) out[1] = join_df(s1, c1);
+        if (i0 + 2 < a.m) out[2] = join_df(s2, c2);
+        if (i0 + 3 < a.m) out[3] = join_df(s3, c3);
     }
 }
 
 // upart[rc][j] = sum_{i in row chunk rc} A[i, j] * v_i for v (length m) in global memory.
+// v's chunk is staged in shared memory; each lane reads 4 consecutive rows per step.
 __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v) {
     const int items = a.nrc * a.ncg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -146,25 +182,209 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v) 
             k_dsm[i] = make_float2(hi, lo);
         }
         __syncthreads();
+        const bool full = a.aligned16 && rows == kRowChunk;
         for (int jj = 0; jj < kColGroup / kKWarps; ++jj) {
             const int j = cg * kColGroup + warp * (kColGroup / kKWarps) + jj;
             if (j >= a.n) break;
             const float* col = a.A + (size_t)j * a.lda + r0;
-            float s = 0.f, c = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+            if (full) {
+                const float4* col4 = reinterpret_cast<const float4*>(col);
 #pragma unroll 4
-            for (int i = lane; i < rows; i += 32) {
-                float2 w = k_dsm[i];
-                dot2_step(s, c, __ldg(col + i), w.x, w.y);
+                for (int q = lane; q < kRowChunk / 4; q += 32) {
+                    const float4 av = __ldg(col4 + q);
+                    const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
+                    dot2_step(s0, c0, av.x, w0.x, w0.y);
+                    dot2_step(s1, c1, av.y, w1.x, w1.y);
+                    dot2_step(s2, c2, av.z, w2.x, w2.y);
+                    dot2_step(s3, c3, av.w, w3.x, w3.y);
+                }
+            } else {
+                for (int i = lane; i < rows; i += 32) {
+                    const float2 w = k_dsm[i];
+                    dot2_step(s0, c0, __ldg(col + i), w.x, w.y);
+                }
             }
-            double val = warp_sum_d(join_df(s, c));
-            if (lane == 0) a.upart[(size_t)rc * a.n + j] = val;
+            // combine the four chains, then the 32 lanes, in double-float
+            float t, e;
+            two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+            two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
+            two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
+            warp_sum_df(s0, c0);
+            if (lane == 0) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
         }
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Fused engine (n <= 256 * NC): one pass over A per call.
+// ---------------------------------------------------------------------------------------
+constexpr int kRB = 4;   // rows per streamed block
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Row block `blk` (rows 4 blk .. 4 blk + 3) of the CTA's own columns into buffer `dst`,
+// stored column by column: dst[j] = (A[i0, j], A[i0+1, j], A[i0+2, j], A[i0+3, j]).
+template <int NC>
+__device__ __forceinline__ void prefetch_rows(const KArgs& a, int blk, float4* dst) {
+    const int i0 = blk * kRB;
+    const bool full = a.aligned16 && (i0 + kRB <= a.m);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int j = threadIdx.x + c * kKThreads;
+        if (j >= a.n) break;
+        const float* src = a.A + (size_t)i0 + (size_t)j * a.lda;
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + j);
+        if (full) {
+            cp_async16(d, src);
+        } else {
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) {
+                if (i0 + r < a.m) cp_async4(d + 4 * r, src + r);
+                else reinterpret_cast<float*>(dst + j)[r] = 0.f;
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+// One pass over A. doA: q = A t (written to a.q, ||q||^2 added to dsum by threads 0..3);
+// doB1: per-CTA partial of A^T q into v1part; doB2: per-CTA partial of A^T r into v2part.
+template <int NC>
+__device__ void fused_pass(const KArgs& a, const double* __restrict__ tvec, const double* __restrict__ rvec,
+                           bool doA, bool doB1, bool doB2, double& dsum) {
+    float4* ring = reinterpret_cast<float4*>(reinterpret_cast<float*>(k_dsm) + a.vec_floats);
+    __shared__ float2 s_red[kKWarps][kRB];
+    __shared__ double s_q[kRB];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float th[NC], tl[NC], v1s[NC], v1c[NC], v2s[NC], v2c[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int j = t + c * kKThreads;
+        th[c] = tl[c] = 0.f;
+        if (doA && j < a.n) split_df(__ldcg(tvec + j), th[c], tl[c]);
+        v1s[c] = v1c[c] = v2s[c] = v2c[c] = 0.f;
+    }
+    const int nblk = (a.m + kRB - 1) / kRB;
+    const int per = (nblk + gridDim.x - 1) / gridDim.x;
+    const int b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
+    __syncthreads();   // the ring is free (previous users of dynamic smem are done)
+    if (b0 < b1) prefetch_rows<NC>(a, b0, ring);
+    int buf = 0;
+    for (int blk = b0; blk < b1; ++blk, buf ^= 1) {
+        if (blk + 1 < b1) {
+            prefetch_rows<NC>(a, blk + 1, ring + (buf ^ 1) * a.n);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float4* rb = ring + buf * a.n;
+        const int i0 = blk * kRB;
+        double q[kRB] = {0.0, 0.0, 0.0, 0.0};
+        if (doA) {
+            float qs[kRB] = {0.f, 0.f, 0.f, 0.f}, qc[kRB] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int j = t + c * kKThreads;
+                if (j < a.n) {
+                    const float4 av = rb[j];
+                    dot2_step(qs[0], qc[0], av.x, th[c], tl[c]);
+                    dot2_step(qs[1], qc[1], av.y, th[c], tl[c]);
+                    dot2_step(qs[2], qc[2], av.z, th[c], tl[c]);
+                    dot2_step(qs[3], qc[3], av.w, th[c], tl[c]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) {
+                warp_sum_df(qs[r], qc[r]);
+                if (lane == 0) s_red[warp][r] = make_float2(qs[r], qc[r]);
+            }
+            __syncthreads();
+            if (t < kRB) {
+                double v = 0.0;
+#pragma unroll
+                for (int w = 0; w < kKWarps; ++w) v += join_df(s_red[w][t].x, s_red[w][t].y);
+                s_q[t] = v;
+                if (i0 + t < a.m) {
+                    a.q[i0 + t] = v;
+                    dsum += v * v;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) q[r] = s_q[r];
+        }
+        if (doB1 || doB2) {
+            float qh[kRB], ql[kRB], rh[kRB], rl[kRB];
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) {
+                split_df(q[r], qh[r], ql[r]);
+                const double rv = (doB2 && i0 + r < a.m) ? __ldcg(rvec + i0 + r) : 0.0;
+                split_df(rv, rh[r], rl[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int j = t + c * kKThreads;
+                if (j < a.n) {
+                    const float4 av = rb[j];
+                    if (doB1) {
+                        dot2_step(v1s[c], v1c[c], av.x, qh[0], ql[0]);
+                        dot2_step(v1s[c], v1c[c], av.y, qh[1], ql[1]);
+                        dot2_step(v1s[c], v1c[c], av.z, qh[2], ql[2]);
+                        dot2_step(v1s[c], v1c[c], av.w, qh[3], ql[3]);
+                    }
+                    if (doB2) {
+                        dot2_step(v2s[c], v2c[c], av.x, rh[0], rl[0]);
+                        dot2_step(v2s[c], v2c[c], av.y, rh[1], rl[1]);
+                        dot2_step(v2s[c], v2c[c], av.z, rh[2], rl[2]);
+                        dot2_step(v2s[c], v2c[c], av.w, rh[3], rl[3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // this buffer is overwritten by the prefetch two blocks ahead
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int j = t + c * kKThreads;
+        if (j < a.n) {
+            if (doB1) a.v1part[(size_t)blockIdx.x * a.n + j] = join_df(v1s[c], v1c[c]);
+            if (doB2) a.v2part[(size_t)blockIdx.x * a.n + j] = join_df(v2s[c], v2c[c]);
+        }
+    }
+}
+
+// u_j = sum_cta v2part[cta][j] - alpha * sum_cta v1part[cta][j], fixed order; returns the
+// thread's part of ||u||^2.
+__device__ double reduce_u(const KArgs& a, double alpha, bool use_v1, int gtid, int gthreads) {
+    double sq = 0.0;
+    for (int j = gtid; j < a.n; j += gthreads) {
+        double s2 = 0.0, s1 = 0.0;
+        for (int c = 0; c < (int)gridDim.x; ++c) {
+            s2 += __ldcg(a.v2part + (size_t)c * a.n + j);
+            if (use_v1) s1 += __ldcg(a.v1part + (size_t)c * a.n + j);
+        }
+        const double v = use_v1 ? s2 - alpha * s1 : s2;
+        a.u[j] = v;
+        sq += v * v;
+    }
+    return sq;
+}
+
 #define KB_SYNC() do { if (!grid_barrier(a.bar, gridDim.x, a.err)) return; } while (0)
 
-__global__ void __launch_bounds__(kKThreads)
+// NC > 0: fused engine with NC columns per thread; NC == 0: two-pass engine.
+template <int NC>
+__global__ void __launch_bounds__(kKThreads, 1)
 cgls_kernel(KArgs a) {
     const int gtid = blockIdx.x * kKThreads + threadIdx.x, gthreads = gridDim.x * kKThreads;
     const double anorm = sqrt(*a.anorm2);
@@ -181,34 +401,57 @@ cgls_kernel(KArgs a) {
             block_partial(sq, a.bpart, 0);
             for (int j = gtid; j < a.n; j += gthreads) a.x[j] = 0.0;
         } else {
-            stage_vec(a.x, a.n);
-            a_times_partials(a);
-            ++apasses;
-            KB_SYNC();
-            double sq = 0.0;
-            for (int i = gtid; i < a.m; i += gthreads) {
-                double ax = 0.0;
-                for (int cc = 0; cc < a.nck; ++cc) ax += __ldcg(a.qpart + (size_t)cc * a.m + i);
-                double ri = a.b[i] - ax;
-                a.r[i] = ri;
-                sq += ri * ri;
+            if constexpr (NC > 0) {
+                double dummy = 0.0;
+                fused_pass<NC>(a, a.x, nullptr, true, false, false, dummy);
+                ++apasses;
+                KB_SYNC();
+                double sq = 0.0;
+                for (int i = gtid; i < a.m; i += gthreads) {
+                    double ri = a.b[i] - __ldcg(a.q + i);
+                    a.r[i] = ri;
+                    sq += ri * ri;
+                }
+                block_partial(sq, a.bpart, 0);
+            } else {
+                stage_vec(a.x, a.n);
+                a_times_partials(a);
+                ++apasses;
+                KB_SYNC();
+                double sq = 0.0;
+                for (int i = gtid; i < a.m; i += gthreads) {
+                    double ax = 0.0;
+                    for (int cc = 0; cc < a.nck; ++cc) ax += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                    double ri = a.b[i] - ax;
+                    a.r[i] = ri;
+                    sq += ri * ri;
+                }
+                block_partial(sq, a.bpart, 0);
             }
-            block_partial(sq, a.bpart, 0);
         }
         xzero = false;
         KB_SYNC();
         rn2 = grid_total(a.bpart, 0);
         // ---- u = A^T r, s = M^T u, gamma = ||s||^2 ----
-        at_times_partials(a, a.r);
+        if constexpr (NC > 0) {
+            double dummy = 0.0;
+            fused_pass<NC>(a, nullptr, a.r, false, false, true, dummy);
+        } else {
+            at_times_partials(a, a.r);
+        }
         ++apasses;
         KB_SYNC();
         {
             double sq = 0.0;
-            for (int j = gtid; j < a.n; j += gthreads) {
-                double v = 0.0;
-                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
-                a.u[j] = v;
-                sq += v * v;
+            if constexpr (NC > 0) {
+                sq = reduce_u(a, 0.0, false, gtid, gthreads);
+            } else {
+                for (int j = gtid; j < a.n; j += gthreads) {
+                    double v = 0.0;
+                    for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                    a.u[j] = v;
+                    sq += v * v;
+                }
             }
             block_partial(sq, a.bpart, 1);
             double xs = 0.0;
@@ -235,19 +478,26 @@ cgls_kernel(KArgs a) {
         KB_SYNC();
 
         // ---- iterate ----
-        bool conv = false;
         while (iters < a.max_iter) {
             // t = M p
             stage_vec(a.p, a.n);
             tri_gemv(a.Mt, a.n, false, a.t);
             ++mpasses;
             KB_SYNC();
-            // q = A t, delta = ||q||^2
-            stage_vec(a.t, a.n);
-            a_times_partials(a);
-            ++apasses;
-            KB_SYNC();
-            {
+            double delta;
+            if constexpr (NC > 0) {
+                // one pass: q = A t, A^T q, A^T r
+                double dsum = 0.0;
+                fused_pass<NC>(a, a.t, a.r, true, true, true, dsum);
+                ++apasses;
+                block_partial(dsum, a.bpart, 0);
+                KB_SYNC();
+                delta = grid_total(a.bpart, 0);
+            } else {
+                stage_vec(a.t, a.n);
+                a_times_partials(a);
+                ++apasses;
+                KB_SYNC();
                 double sq = 0.0;
                 for (int i = gtid; i < a.m; i += gthreads) {
                     double v = 0.0;
@@ -256,11 +506,11 @@ cgls_kernel(KArgs a) {
                     sq += v * v;
                 }
                 block_partial(sq, a.bpart, 0);
+                KB_SYNC();
+                delta = grid_total(a.bpart, 0);
             }
-            KB_SYNC();
-            const double delta = grid_total(a.bpart, 0);
             ++iters;
-            if (!(delta > 0.0)) { conv = true; break; }
+            if (!(delta > 0.0)) break;
             const double alpha = gamma / delta;
             {
                 double xs = 0.0;
@@ -271,18 +521,21 @@ cgls_kernel(KArgs a) {
                 }
                 block_partial(xs, a.bpart, 3);
                 for (int i = gtid; i < a.m; i += gthreads) a.r[i] -= alpha * __ldcg(a.q + i);
+                if constexpr (NC > 0) reduce_u(a, alpha, true, gtid, gthreads);
             }
             KB_SYNC();
-            // s = M^T (A^T r)
-            at_times_partials(a, a.r);
-            ++apasses;
-            KB_SYNC();
-            for (int j = gtid; j < a.n; j += gthreads) {
-                double v = 0.0;
-                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
-                a.u[j] = v;
+            if constexpr (NC == 0) {
+                // s = M^T (A^T r) with a second pass over A
+                at_times_partials(a, a.r);
+                ++apasses;
+                KB_SYNC();
+                for (int j = gtid; j < a.n; j += gthreads) {
+                    double v = 0.0;
+                    for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                    a.u[j] = v;
+                }
+                KB_SYNC();
             }
-            KB_SYNC();
             stage_vec(a.u, a.n);
             block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
             ++mpasses;
@@ -296,9 +549,8 @@ cgls_kernel(KArgs a) {
             const double e1 = xn > 0.0 ? sn / (anorm * xn) : INFINITY;
             const double f1 = xn > 0.0 ? mnorm * sn / xn : INFINITY;
             KB_SYNC();
-            if ((a.target == LLS_TARGET_FP64 ? e1 : f1) <= a.tol) { conv = true; break; }
+            if ((a.target == LLS_TARGET_FP64 ? e1 : f1) <= a.tol) break;
         }
-        (void)conv;
         // loop back: the top of the restart loop recomputes b - A x and re-tests
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -318,7 +570,8 @@ cgls_kernel(KArgs a) {
 // ---------------------------------------------------------------------------------------
 struct KLayout {
     int nrt, nck, nrc, ncg;
-    size_t off_r, off_q, off_t, off_p, off_s, off_u, off_qpart, off_upart, off_bpart, off_bar, total;
+    size_t off_r, off_q, off_t, off_p, off_s, off_u, off_qpart, off_upart, off_v1, off_v2, off_bpart,
+        off_bar, total;
 };
 
 static KLayout k_layout(int m, int n, int grid) {
@@ -337,57 +590,108 @@ static KLayout k_layout(int m, int n, int grid) {
     L.off_u = take(8ull * n);
     L.off_qpart = take(8ull * m * L.nck);
     L.off_upart = take(8ull * n * L.nrc);
+    L.off_v1 = take(8ull * n * grid);
+    L.off_v2 = take(8ull * n * grid);
     L.off_bpart = take(8ull * kNPart * grid);
     L.off_bar = take(64);
     L.total = o;
     return L;
 }
 
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+constexpr int kMaxGridPerSm = 2;
+
 size_t krylov_scratch_bytes(int m, int n, int grid) {
-    if (grid <= 0) grid = 2 * 160;
+    if (grid <= 0) {
+        int sms = sm_count();
+        grid = kMaxGridPerSm * (sms > 0 ? sms : 160);
+    }
     return k_layout(m, n, grid).total;
 }
 
-int krylov_solve(const KrylovCall& c, cudaStream_t st) {
-    if (c.method != LLS_KRYLOV_CGLS) return LLS_ERR_UNSUPPORTED;
-    const size_t smem = sizeof(float2) * (size_t)(c.n > kRowChunk ? c.n : kRowChunk);
-    if (smem > 200 * 1024) return LLS_ERR_UNSUPPORTED;
-    LLS_CUDA_TRY(cudaFuncSetAttribute(cgls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static int fused_nc(int n) {
+    const int need = ceil_div(n, kKThreads);
+    if (need <= 1) return 1;
+    if (need <= 2) return 2;
+    if (need <= 4) return 4;
+    if (need <= 8) return 8;
+    if (need <= 16) return 16;
+    return 0;
+}
+
+template <int NC>
+static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, int sms, cudaStream_t st) {
+    auto kern = cgls_kernel<NC>;
+    LLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgls_kernel, kKThreads, smem));
-    int dev = 0, sms = 0;
-    LLS_CUDA_TRY(cudaGetDevice(&dev));
-    LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
     if (per_sm < 1) return LLS_ERR_UNSUPPORTED;
-    int maxg = sms * (per_sm < 2 ? per_sm : 2);
-    // enough CTAs for the work, few enough that barriers stay cheap on small problems
-    long long work = (long long)c.m * c.n;
-    int grid = (int)((work + (1 << 16) - 1) >> 16);
+    const int maxg = sms * (per_sm < kMaxGridPerSm ? per_sm : kMaxGridPerSm);
+    int grid;
+    if (NC > 0) {
+        const int nblk = ceil_div(c.m, kRB);
+        grid = ceil_div(nblk, 8);            // at least 8 row blocks per CTA
+    } else {
+        const long long work = (long long)c.m * c.n;
+        grid = (int)((work + (1 << 16) - 1) >> 16);
+    }
     if (grid < 1) grid = 1;
     if (grid > maxg) grid = maxg;
     KLayout L = k_layout(c.m, c.n, grid);
     if (L.total > c.scratch_bytes) return LLS_ERR_WORKSPACE;
-    char* base = (char*)c.scratch;
-    KArgs a;
-    a.m = c.m; a.n = c.n; a.lda = c.lda; a.A = c.A; a.b = c.b; a.x = c.x;
-    a.M = c.Minv; a.Mt = c.Mt;
     a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
     a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);
     a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u);
     a.qpart = (double*)(base + L.off_qpart); a.upart = (double*)(base + L.off_upart);
+    a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
     a.bpart = (double*)(base + L.off_bpart);
     a.bar = (unsigned*)(base + L.off_bar);
+    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
+    LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
+    void* args[] = {&a};
+    LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kKThreads), args, smem, st));
+    note_launch("cgls", st);
+    return LLS_OK;
+}
+
+int krylov_solve(const KrylovCall& c, cudaStream_t st) {
+    if (c.method != LLS_KRYLOV_CGLS) return LLS_ERR_UNSUPPORTED;
+    const int sms = sm_count();
+    if (sms <= 0) return LLS_ERR_CUDA;
+    static const bool want_fused = getenv("LLS_KRYLOV_FUSED") != nullptr;
+    const int nc = want_fused ? fused_nc(c.n) : 0;
+    KArgs a;
+    a.m = c.m; a.n = c.n; a.lda = c.lda; a.A = c.A; a.b = c.b; a.x = c.x;
+    a.M = c.Minv; a.Mt = c.Mt;
     a.err = c.dev_err;
     a.info = c.dev_info;
     a.anorm2 = c.dev_info + 8;
     a.mnorm2 = c.dev_info + 9;
     a.tol = c.tol; a.max_iter = c.max_iter; a.target = c.target; a.x_zero = 1;
-    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
-    LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
-    void* args[] = {&a};
-    LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cgls_kernel, dim3(grid), dim3(kKThreads), args, smem, st));
-    note_launch("cgls", st);
-    return LLS_OK;
+    a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
+    char* base = (char*)c.scratch;
+    if (nc > 0) {
+        a.vec_floats = (int)align_up((size_t)2 * c.n, 4);
+        const size_t smem = sizeof(float) * ((size_t)a.vec_floats + (size_t)2 * kRB * c.n);
+        if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
+        switch (nc) {
+            case 1: return launch_cgls<1>(a, c, base, smem, sms, st);
+            case 2: return launch_cgls<2>(a, c, base, smem, sms, st);
+            case 4: return launch_cgls<4>(a, c, base, smem, sms, st);
+            case 8: return launch_cgls<8>(a, c, base, smem, sms, st);
+            default: return launch_cgls<16>(a, c, base, smem, sms, st);
+        }
+    }
+    a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
+    const size_t smem = sizeof(float) * (size_t)a.vec_floats;
+    if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
+    return launch_cgls<0>(a, c, base, smem, sms, st);
 }
 
 }  // namespace lls

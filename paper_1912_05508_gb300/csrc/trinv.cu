@@ -7,17 +7,32 @@
 // FP32 rounding of M changes only the convergence rate, not the converged solution.
 //
 // Formation follows the block structure of Eq. recqr: with R = [R11 R12; 0 R22],
-// R^{-1} = [M11, -M11 R12 M22; 0, M22]; leaves (<= 32 columns) are inverted by back
-// substitution, one column of the inverse per thread.
+// R^{-1} = [M11, -M11 R12 M22; 0, M22], over the same column split as the QR. All leaves
+// (<= 32 columns) are inverted in one launch by back substitution, one column of the
+// inverse per thread; the internal nodes of one tree depth are independent and run as
+// two batched products per depth, deepest first.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace lls {
 
-__global__ void diag_block_inverse_kernel(const float* __restrict__ R, int ldr, int c0, int w,
-                                          float* __restrict__ M, int ldm, int* err) {
+constexpr int kMaxNodes = 1024;
+
+struct NodeList {
+    int count;
+    int c0[kMaxNodes];
+    int w1[kMaxNodes];
+    int w2[kMaxNodes];
+};
+
+__global__ void diag_block_inverse_kernel(const float* __restrict__ R, int ldr, float* __restrict__ M,
+                                          int ldm, int* err, NodeList nl) {
     __shared__ float Rs[32][33];
     __shared__ float Ms[32][33];
+    const int c0 = nl.c0[blockIdx.x], w = nl.w1[blockIdx.x];
     const int j = threadIdx.x;   // column of the inverse
     for (int i = 0; i < w; ++i)
         Rs[i][j] = (j < w) ? R[(size_t)(c0 + i) + (size_t)(c0 + j) * ldr] : 0.f;
@@ -26,7 +41,7 @@ __global__ void diag_block_inverse_kernel(const float* __restrict__ R, int ldr, 
         for (int i = w - 1; i >= 0; --i) {
             float s = (i == j) ? 1.f : 0.f;
             for (int k = i + 1; k <= j; ++k) s = fmaf(-Rs[i][k], Ms[k][j], s);
-            float d = Rs[i][i];
+            const float d = Rs[i][i];
             if (!(d != 0.f) || !isfinite(d)) atomicCAS(err, DEV_OK, DEV_SINGULAR);
             Ms[i][j] = (i <= j) ? s / d : 0.f;
         }
@@ -34,6 +49,78 @@ __global__ void diag_block_inverse_kernel(const float* __restrict__ R, int ldr, 
     __syncwarp();
     if (j < w)
         for (int i = 0; i < w; ++i) M[(size_t)(c0 + i) + (size_t)(c0 + j) * ldm] = Ms[i][j];
+}
+
+// One batched product per tree depth, 64 x 64 tiles, FP32. For node (c0, w1, w2):
+//   phase 0:  T   = R12 M22      (w1 x w2, K = w2; T stored where M12 will go, in tmp)
+//   phase 1:  M12 = -M11 T       (w1 x w2, K = w1)
+// M22 and M11 are upper triangular, so the K loop skips their zero blocks.
+constexpr int kTB = 64, kTK = 16;
+__global__ void __launch_bounds__(256)
+trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __restrict__ M,
+                     float* __restrict__ tmp, int n, NodeList nl) {
+    const int node = blockIdx.z;
+    const int c0 = nl.c0[node], w1 = nl.w1[node], w2 = nl.w2[node];
+    const int i0 = blockIdx.x * kTB, j0 = blockIdx.y * kTB;
+    if (i0 >= w1 || j0 >= w2) return;
+    const float* A;
+    const float* B;
+    float* C;
+    int lda, ldb, K;
+    float alpha;
+    if (phase == 0) {
+        A = R + (size_t)c0 + (size_t)(c0 + w1) * ldr; lda = ldr;
+        B = M + (size_t)(c0 + w1) + (size_t)(c0 + w1) * n; ldb = n;
+        C = tmp + (size_t)c0 + (size_t)(c0 + w1) * n;
+        K = w2; alpha = 1.f;
+    } else {
+        A = M + (size_t)c0 + (size_t)c0 * n; lda = n;
+        B = tmp + (size_t)c0 + (size_t)(c0 + w1) * n; ldb = n;
+        C = M + (size_t)c0 + (size_t)(c0 + w1) * n;
+        K = w1; alpha = -1.f;
+    }
+    __shared__ float As[kTK][kTB + 4];
+    __shared__ float Bs[kTK][kTB + 4];
+    const int t = threadIdx.x;
+    const int ti = (t % 16) * 4, tj = (t / 16) * 4;
+    float acc[4][4] = {};
+    // phase 0: B = M22 upper triangular, rows k <= j; phase 1: A = M11 upper, columns k >= i
+    const int kbeg = phase == 1 ? (i0 / kTK) * kTK : 0;
+    const int kend = phase == 0 ? min(K, j0 + kTB) : K;
+    for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = t + r * 256;
+            const int ii = idx % kTB, kk = idx / kTB;
+            const int gi = i0 + ii, gk = k0 + kk;
+            As[kk][ii] = (gi < w1 && gk < K) ? A[(size_t)gi + (size_t)gk * lda] : 0.f;
+            const int kk2 = idx % kTK, jj = idx / kTK;
+            const int gj = j0 + jj, gk2 = k0 + kk2;
+            Bs[kk2][jj] = (gj < w2 && gk2 < K) ? B[(size_t)gk2 + (size_t)gj * ldb] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTK; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { av[u] = As[kk][ti + u]; bv[u] = Bs[kk][tj + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int j = j0 + tj + v;
+        if (j >= w2) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + ti + u;
+            if (i < w1) C[(size_t)i + (size_t)j * n] = alpha * acc[u][v];
+        }
+    }
 }
 
 __global__ void transpose_kernel(const float* __restrict__ X, int ldx, float* __restrict__ Y, int ldy, int n) {
@@ -51,32 +138,61 @@ __global__ void transpose_kernel(const float* __restrict__ X, int ldx, float* __
     }
 }
 
-static int split_point_host(int w, int pw) { return pw * ceil_div(w, 2 * pw); }
+namespace {
+struct TreeNode { int c0, w1, w2, depth; };
 
-static int inv_rec(const float* R, int ldr, int c0, int w, int pw, float* M, int ldm, float* tmp,
-                   int* err, cudaStream_t st) {
-    if (w <= pw) {
-        diag_block_inverse_kernel<<<1, 32, 0, st>>>(R, ldr, c0, w, M, ldm, err);
-        LLS_LAUNCH_CHECK("diag_block_inverse", st);
-        return LLS_OK;
+int split_point_host(int w, int pw) { return pw * ceil_div(w, 2 * pw); }
+
+void walk(int c0, int w, int pw, int depth, std::vector<TreeNode>& leaves, std::vector<TreeNode>& inner) {
+    if (w <= pw) { leaves.push_back({c0, w, 0, depth}); return; }
+    const int w1 = split_point_host(w, pw);
+    inner.push_back({c0, w1, w - w1, depth});
+    walk(c0, w1, pw, depth + 1, leaves, inner);
+    walk(c0 + w1, w - w1, pw, depth + 1, leaves, inner);
+}
+
+template <typename F>
+int for_chunks(const std::vector<TreeNode>& v, F f) {
+    for (size_t s = 0; s < v.size(); s += kMaxNodes) {
+        NodeList nl;
+        nl.count = (int)std::min(v.size() - s, (size_t)kMaxNodes);
+        int mw1 = 0, mw2 = 0;
+        for (int i = 0; i < nl.count; ++i) {
+            nl.c0[i] = v[s + i].c0; nl.w1[i] = v[s + i].w1; nl.w2[i] = v[s + i].w2;
+            mw1 = std::max(mw1, nl.w1[i]); mw2 = std::max(mw2, nl.w2[i]);
+        }
+        LLS_TRY(f(nl, mw1, mw2));
     }
-    const int w1 = split_point_host(w, pw), w2 = w - w1;
-    LLS_TRY(inv_rec(R, ldr, c0, w1, pw, M, ldm, tmp, err, st));
-    LLS_TRY(inv_rec(R, ldr, c0 + w1, w2, pw, M, ldm, tmp, err, st));
-    // T = R12 M22 (w1 x w2), then M12 = -M11 T
-    const float* R12 = R + (size_t)c0 + (size_t)(c0 + w1) * ldr;
-    const float* M22 = M + (size_t)(c0 + w1) + (size_t)(c0 + w1) * ldm;
-    const float* M11 = M + (size_t)c0 + (size_t)c0 * ldm;
-    float* M12 = M + (size_t)c0 + (size_t)(c0 + w1) * ldm;
-    LLS_TRY(sgemm(false, false, w1, w2, w2, 1.f, R12, ldr, M22, ldm, 0.f, tmp, w1, st));
-    LLS_TRY(sgemm(false, false, w1, w2, w1, -1.f, M11, ldm, tmp, w1, 0.f, M12, ldm, st));
     return LLS_OK;
 }
+}  // namespace
 
 int tri_inverse(const float* R, int ldr, int n, int pw, float* Minv, float* Mt, float* tmp,
                 int* dev_err, cudaStream_t st) {
+    pw = pw < 1 ? 32 : (pw > 32 ? 32 : pw);
+    std::vector<TreeNode> leaves, inner;
+    walk(0, n, pw, 0, leaves, inner);
     LLS_CUDA_TRY(cudaMemsetAsync(Minv, 0, sizeof(float) * (size_t)n * n, st));
-    LLS_TRY(inv_rec(R, ldr, 0, n, pw < 1 ? 32 : (pw > 32 ? 32 : pw), Minv, n, tmp, dev_err, st));
+    LLS_TRY(for_chunks(leaves, [&](const NodeList& nl, int, int) -> int {
+        diag_block_inverse_kernel<<<nl.count, 32, 0, st>>>(R, ldr, Minv, n, dev_err, nl);
+        LLS_LAUNCH_CHECK("diag_block_inverse", st);
+        return (int)LLS_OK;
+    }));
+    int maxd = 0;
+    for (auto& x : inner) maxd = std::max(maxd, x.depth);
+    for (int d = maxd; d >= 0; --d) {
+        std::vector<TreeNode> lvl;
+        for (auto& x : inner) if (x.depth == d) lvl.push_back(x);
+        if (lvl.empty()) continue;
+        for (int phase = 0; phase < 2; ++phase) {
+            LLS_TRY(for_chunks(lvl, [&](const NodeList& nl, int mw1, int mw2) -> int {
+                dim3 grid(ceil_div(mw1, kTB), ceil_div(mw2, kTB), nl.count);
+                trinv_batched_kernel<<<grid, 256, 0, st>>>(phase, R, ldr, Minv, tmp, n, nl);
+                LLS_LAUNCH_CHECK("trinv_batched", st);
+                return (int)LLS_OK;
+            }));
+        }
+    }
     if (Mt) {
         dim3 grid(ceil_div(n, 32), ceil_div(n, 32));
         transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(Minv, n, Mt, n, n);

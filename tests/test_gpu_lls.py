@@ -96,3 +96,38 @@ def test_graph_replay_matches_direct_path():
     assert torch.equal(xs[0], x0) and torch.equal(xs[1], x0) and torch.equal(xs[2], x0)
     # every replay accounts for the same kernel count as the captured call
     assert launches[0] == launches[1] == launches[2] > 10
+
+
+def test_fused_engine_matches_oracle():
+    # The single-pass CGLS engine (selected with LLS_KRYLOV_FUSED; the choice is read once per
+    # process, so it runs in a fresh process) against the oracle.
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import sys, json, torch, numpy as np; sys.path.insert(0, %r);"
+        "from paper_1912_05508_gb300 import lls, synth;"
+        "p = synth.svd_lls(1500, 96, 'geometric', 1e3, seed=41);"
+        "x, info = lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda());"
+        "np.save(sys.argv[1], x.cpu().numpy()); print(json.dumps(info))"
+    ) % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    import tempfile
+    out = os.path.join(tempfile.mkdtemp(), "x.npy")
+    env = dict(os.environ, LLS_KRYLOV_FUSED="1")
+    r = subprocess.run([sys.executable, "-c", code, out], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    import json
+    info = json.loads(r.stdout.strip().splitlines()[-1])
+    assert info["status"] == 0
+    assert info["a_passes"] == info["iters"] + 3       # one pass over A per iteration
+    p = synth.svd_lls(1500, 96, "geometric", 1e3, seed=41)
+    x = np.load(out)
+    assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
+    assert metrics.forward_error(x, direct.lls(p.A, p.b)) <= 10 * p.kappa * 1e-12
+
+
+def test_default_engine_two_passes_per_iteration():
+    p = synth.svd_lls(1024, 128, "geometric", 1e3, seed=1)
+    x, info = run(p, prec="fp16", target="fp64")
+    # init (A^T b) + two passes per iteration + final check (A x, A^T r)
+    assert info["a_passes"] == 2 * info["iters"] + 3
