@@ -127,6 +127,30 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
               lls_info* info, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint of the least-squares solution map (the paper has none; this is the textbook
+ * sensitivity of x* = (A^T A)^{-1} A^T b, used by the differentiable solve).
+ * For each problem i of the batch, given x_i = x*(A_i, b_i), the R factor R_i returned by
+ * lls_solve (R_out) and g_i = dL/dx_i:
+ *     z = (A^T A)^{-1} g   by CG on A^T A z = g preconditioned with (R^T R)^{-1}
+ *     grad_b = A z,   grad_A = (b - A x) z^T - (A z) x^T
+ *  m, n, lda, ldr, ldga: HOST arrays of `batch` ints (ldr >= n, lda, ldga >= m).
+ *  A, b, x, R, grad_x, grad_A, grad_b: HOST arrays of `batch` DEVICE pointers:
+ *     A m x n FP32, b m FP64, x n FP64, R n x n FP32 upper triangular, grad_x n FP64,
+ *     grad_A m x n FP32 (written), grad_b m FP64 (written).
+ *  ws: lls_backward_workspace_size(batch, m, n, opts) bytes, 256-byte aligned.
+ *  opts: target FP64 iterates z to ||R^-T (g - A^T A z)|| <= 1e-13 ||R^-T g|| (FP32: 1e-7);
+ *        max_iter caps the CG iterations.
+ * Problems are processed one after another on `stream`.
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+size_t lls_backward_workspace_size(int batch, const int* m, const int* n, const lls_options* opts);
+int lls_backward(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                 const double* const* b, const double* const* x, const float* const* R, const int* ldr,
+                 const double* const* grad_x, float* const* grad_A, const int* ldga,
+                 double* const* grad_b, void* ws, size_t ws_bytes, const lls_options* opts,
+                 cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel-level building blocks: the two tensor-core products of one recursion step of
  * Alg. 2 (line 8: R12 = Q1^T A2; line 9: A2 = A2 - Q1 R12), with the operands already
  * rounded to FP16 or BF16 (prec = LLS_PREC_FP16 / LLS_PREC_BF16) and FP32 accumulation.

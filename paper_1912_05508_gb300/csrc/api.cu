@@ -101,7 +101,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         PanelCall p;
         p.W = c.w.W; p.ldw = c.w.ldw; p.Wh = c.w.Wh; p.ldh = c.w.ldh; p.R = c.R; p.ldr = c.ldr;
         p.m = c.m; p.c0 = c0; p.b = w; p.lowp = c.lowp;
-        p.rbuf = c.w.rbuf; p.qbuf = c.w.qbuf; p.cnt = c.w.cnt;
+        p.rbuf = c.w.rbuf; p.qbuf = c.w.qbuf; p.cnt = c.w.cnt; p.err = c.w.err;
         return panel_qr(p, c.st);
     }
     const int w1 = split_point(w, c.pw), w2 = w - w1;
@@ -387,6 +387,84 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     else if (herr != DEV_OK) st = LLS_ERR_CUDA;
     info->status = st;
     return st;
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint of the least-squares solve (batched over independent problems).
+// ---------------------------------------------------------------------------------------
+struct BwdWs {
+    float *Minv, *Mt, *tmp;
+    double* z;
+    void* ks; size_t kb;
+    int* err; double* dinfo;
+};
+
+static void bwd_layout(WsArena& ar, int mmax, int nmax, BwdWs& w) {
+    w.Minv = ar.take<float>((size_t)nmax * nmax);
+    w.Mt = ar.take<float>((size_t)nmax * nmax);
+    w.tmp = ar.take<float>((size_t)nmax * nmax);
+    w.z = ar.take<double>(nmax);
+    w.kb = krylov_scratch_bytes(mmax, nmax, 0);
+    w.ks = ar.take<char>(w.kb);
+    w.err = ar.take<int>(16);
+    w.dinfo = ar.take<double>(16);
+}
+
+static bool batch_dims(int batch, const int* m, const int* n, int& mmax, int& nmax) {
+    if (batch < 1 || !m || !n) return false;
+    mmax = 0; nmax = 0;
+    for (int i = 0; i < batch; ++i) {
+        if (n[i] < 1 || m[i] < n[i]) return false;
+        if (m[i] > mmax) mmax = m[i];
+        if (n[i] > nmax) nmax = n[i];
+    }
+    return true;
+}
+
+size_t lls_backward_workspace_size(int batch, const int* m, const int* n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    int mmax, nmax;
+    if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return 0;
+    WsArena ar(nullptr, SIZE_MAX);
+    BwdWs w;
+    bwd_layout(ar, mmax, nmax, w);
+    return ar.off;
+}
+
+int lls_backward(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                 const double* const* b, const double* const* x, const float* const* R, const int* ldr,
+                 const double* const* grad_x, float* const* grad_A, const int* ldga,
+                 double* const* grad_b, void* ws, size_t ws_bytes, const lls_options* opts,
+                 cudaStream_t stream) {
+    lls_options o;
+    resolve(opts, o);
+    int mmax, nmax;
+    if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
+    if (!A || !lda || !b || !x || !R || !ldr || !grad_x || !grad_A || !ldga || !grad_b || !ws) return LLS_ERR_ARG;
+    for (int i = 0; i < batch; ++i) {
+        if (!A[i] || !b[i] || !x[i] || !R[i] || !grad_x[i] || !grad_A[i] || !grad_b[i]) return LLS_ERR_ARG;
+        if (lda[i] < m[i] || ldr[i] < n[i] || ldga[i] < m[i]) return LLS_ERR_ARG;
+    }
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, ws_bytes);
+    BwdWs w;
+    bwd_layout(ar, mmax, nmax, w);
+    if (!ar.ok) return LLS_ERR_WORKSPACE;
+    trace_mark(stream);
+    LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, stream));
+    for (int i = 0; i < batch; ++i) {
+        LLS_TRY(tri_inverse(R[i], ldr[i], n[i], o.panel_width, w.Minv, w.Mt, w.tmp, w.err, stream));
+        AdjointCall c;
+        c.m = m[i]; c.n = n[i]; c.A = A[i]; c.lda = lda[i]; c.b = b[i]; c.x = x[i]; c.g = grad_x[i];
+        c.Minv = w.Minv; c.Mt = w.Mt; c.z = w.z; c.gA = grad_A[i]; c.ldga = ldga[i]; c.gb = grad_b[i];
+        c.tol = o.target == LLS_TARGET_FP32 ? 1e-7 : 1e-13;
+        c.max_iter = o.max_iter;
+        c.scratch = w.ks; c.scratch_bytes = w.kb; c.dev_err = w.err; c.dev_info = w.dinfo;
+        LLS_TRY(adjoint_solve(c, stream));
+    }
+    trace_flush();
+    return LLS_OK;
 }
 
 }  // extern "C"

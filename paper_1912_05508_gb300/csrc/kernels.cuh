@@ -14,6 +14,7 @@ struct PanelCall {
     int m, c0, b;
     int lowp;              // 0 FP16, 1 BF16, 3 none
     float* rbuf; float* qbuf; unsigned* cnt;
+    int* err;
 };
 void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t& cnt_words);
 int panel_qr(const PanelCall& c, cudaStream_t st);
@@ -81,6 +82,22 @@ struct KrylovCall {
 };
 size_t krylov_scratch_bytes(int m, int n, int grid);
 int krylov_solve(const KrylovCall& c, cudaStream_t st);
+
+// Adjoint (krylov.cu): z = (A^T A)^{-1} g by M M^T-preconditioned CG, then
+// gb = A z and gA = (b - A x) z^T - (A z) x^T.
+struct AdjointCall {
+    int m, n;
+    const float* A; int lda;
+    const double* b; const double* x; const double* g;
+    const float* Minv; const float* Mt;
+    double* z;              // n, output
+    float* gA; int ldga;    // m x n FP32 output
+    double* gb;             // m FP64 output
+    double tol; int max_iter;
+    void* scratch; size_t scratch_bytes;
+    int* dev_err; double* dev_info;
+};
+int adjoint_solve(const AdjointCall& c, cudaStream_t st);
 
 // ---- graph replay (graph.cu) -----------------------------------------------------------------
 // Identity of one call: plain-old-data, compared bytewise (zero-initialize before filling).

@@ -568,6 +568,144 @@ cgls_kernel(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Adjoint of the least-squares solution map (for the differentiable solve).
+//
+// For a loss L(x*) with g = dL/dx, z = (A^T A)^{-1} g; then dL/db = A z and
+// dL/dA = r z^T - (A z) x^T with r = b - A x (differentiate A^T (b - A x) = 0). z comes from
+// preconditioned CG on A^T A z = g with the preconditioner M M^T = (R^T R)^{-1}, reusing the
+// solve's R; each iteration applies A and A^T with the same compensated products as CGLS.
+//   res = g, u = M^T res, y = M u, rho = ||u||^2, p = y
+//   loop: q = A p, w = A^T q, alpha = rho / (p . w), z += alpha p, res -= alpha w,
+//         u = M^T res, rho' = ||u||^2, beta = rho' / rho, y = M u, p = y + beta p
+//   stop when ||M^T res|| <= tol ||M^T g||.
+// Then r = b - A x and A z are formed and the rank-2 gradient is written in one sweep.
+// Vector roles: z -> x, res -> s, y -> t, q -> q, w -> u, u -> r (n entries), g -> b.
+struct AdjArgs {
+    KArgs k;
+    const double* g;
+    const double* bvec;
+    const double* xsol;
+    float* gA; int ldga;
+    double* gb;
+};
+
+__global__ void __launch_bounds__(kKThreads, 1)
+adjoint_kernel(AdjArgs aa) {
+    KArgs& a = aa.k;
+    const int gtid = blockIdx.x * kKThreads + threadIdx.x, gthreads = gridDim.x * kKThreads;
+    const int n = a.n, m = a.m;
+    double* z = a.x;
+    double* res = a.s;
+    double* y = a.t;
+    double* w = a.u;
+    double* uu = a.r;
+    int iters = 0, status = 1, apasses = 0, mpasses = 0;
+    // res = g, z = 0
+    for (int j = gtid; j < n; j += gthreads) { res[j] = aa.g[j]; z[j] = 0.0; }
+    KB_SYNC();
+    // u = M^T res, rho = ||u||^2
+    stage_vec(res, n);
+    block_partial(tri_gemv(a.M, n, true, uu), a.bpart, 0);
+    ++mpasses;
+    KB_SYNC();
+    double rho = grid_total(a.bpart, 0);
+    const double rho0 = rho;
+    // y = M u, p = y
+    stage_vec(uu, n);
+    tri_gemv(a.Mt, n, false, y);
+    ++mpasses;
+    KB_SYNC();
+    for (int j = gtid; j < n; j += gthreads) a.p[j] = __ldcg(y + j);
+    KB_SYNC();
+    if (!(rho0 > 0.0)) status = 0;
+    while (status != 0 && iters < a.max_iter) {
+        // q = A p
+        stage_vec(a.p, n);
+        a_times_partials(a);
+        ++apasses;
+        KB_SYNC();
+        for (int i = gtid; i < m; i += gthreads) {
+            double v = 0.0;
+            for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+            a.q[i] = v;
+        }
+        KB_SYNC();
+        // w = A^T q, pw = p . w
+        at_times_partials(a, a.q);
+        ++apasses;
+        KB_SYNC();
+        {
+            double pw = 0.0;
+            for (int j = gtid; j < n; j += gthreads) {
+                double v = 0.0;
+                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * n + j);
+                w[j] = v;
+                pw += v * __ldcg(a.p + j);
+            }
+            block_partial(pw, a.bpart, 1);
+        }
+        KB_SYNC();
+        const double pw = grid_total(a.bpart, 1);
+        ++iters;
+        if (!(pw > 0.0)) { status = 0; break; }
+        const double alpha = rho / pw;
+        for (int j = gtid; j < n; j += gthreads) {
+            z[j] += alpha * __ldcg(a.p + j);
+            res[j] -= alpha * __ldcg(w + j);
+        }
+        KB_SYNC();
+        stage_vec(res, n);
+        block_partial(tri_gemv(a.M, n, true, uu), a.bpart, 0);
+        ++mpasses;
+        KB_SYNC();
+        const double rnew = grid_total(a.bpart, 0);
+        const double beta = rnew / rho;
+        rho = rnew;
+        stage_vec(uu, n);
+        tri_gemv(a.Mt, n, false, y);
+        ++mpasses;
+        KB_SYNC();
+        for (int j = gtid; j < n; j += gthreads) a.p[j] = __ldcg(y + j) + beta * a.p[j];
+        KB_SYNC();
+        if (sqrt(rho) <= a.tol * sqrt(rho0)) { status = 0; break; }
+    }
+    // r = b - A x  (into q), then A z (into qpart reduce -> gb)
+    stage_vec(aa.xsol, n);
+    a_times_partials(a);
+    ++apasses;
+    KB_SYNC();
+    for (int i = gtid; i < m; i += gthreads) {
+        double v = 0.0;
+        for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+        a.q[i] = aa.bvec[i] - v;
+    }
+    KB_SYNC();
+    stage_vec(z, n);
+    a_times_partials(a);
+    ++apasses;
+    KB_SYNC();
+    for (int i = gtid; i < m; i += gthreads) {
+        double v = 0.0;
+        for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+        aa.gb[i] = v;
+    }
+    KB_SYNC();
+    // dL/dA[i, j] = r_i z_j - (A z)_i x_j, column by column (coalesced over i)
+    for (size_t e = (size_t)gtid; e < (size_t)m * n; e += (size_t)gthreads) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        const double val = __ldcg(a.q + i) * __ldcg(z + j) - __ldcg(aa.gb + i) * __ldcg(aa.xsol + j);
+        aa.gA[(size_t)i + (size_t)j * aa.ldga] = (float)val;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.info[0] = iters;
+        a.info[1] = rho0 > 0.0 ? sqrt(rho / rho0) : 0.0;
+        a.info[7] = status;
+        a.info[10] = apasses;
+        a.info[11] = mpasses;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 struct KLayout {
     int nrt, nck, nrc, ncg;
     size_t off_r, off_q, off_t, off_p, off_s, off_u, off_qpart, off_upart, off_v1, off_v2, off_bpart,
@@ -692,6 +830,47 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;
     if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
     return launch_cgls<0>(a, c, base, smem, sms, st);
+}
+
+int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
+    const int sms = sm_count();
+    if (sms <= 0) return LLS_ERR_CUDA;
+    AdjArgs aa;
+    KArgs& a = aa.k;
+    a.m = c.m; a.n = c.n; a.lda = c.lda; a.A = c.A; a.b = nullptr; a.x = c.z;
+    a.M = c.Minv; a.Mt = c.Mt;
+    a.err = c.dev_err; a.info = c.dev_info; a.anorm2 = nullptr; a.mnorm2 = nullptr;
+    a.tol = c.tol; a.max_iter = c.max_iter; a.target = LLS_TARGET_FP64; a.x_zero = 1;
+    a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
+    a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
+    const size_t smem = sizeof(float) * (size_t)a.vec_floats;
+    if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
+    aa.g = c.g; aa.bvec = c.b; aa.xsol = c.x; aa.gA = c.gA; aa.ldga = c.ldga; aa.gb = c.gb;
+    LLS_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel, kKThreads, smem));
+    if (per_sm < 1) return LLS_ERR_UNSUPPORTED;
+    const int maxg = sms * (per_sm < kMaxGridPerSm ? per_sm : kMaxGridPerSm);
+    const long long work = (long long)c.m * c.n;
+    int grid = (int)((work + (1 << 16) - 1) >> 16);
+    if (grid < 1) grid = 1;
+    if (grid > maxg) grid = maxg;
+    KLayout L = k_layout(c.m, c.n, grid);
+    if (L.total > c.scratch_bytes) return LLS_ERR_WORKSPACE;
+    char* base = (char*)c.scratch;
+    a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
+    a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);
+    a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u);
+    a.qpart = (double*)(base + L.off_qpart); a.upart = (double*)(base + L.off_upart);
+    a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
+    a.bpart = (double*)(base + L.off_bpart);
+    a.bar = (unsigned*)(base + L.off_bar);
+    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
+    LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
+    void* args[] = {&aa};
+    LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)adjoint_kernel, dim3(grid), dim3(kKThreads), args, smem, st));
+    note_launch("adjoint", st);
+    return LLS_OK;
 }
 
 }  // namespace lls

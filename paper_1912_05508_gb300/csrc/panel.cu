@@ -46,7 +46,9 @@ struct PanelArgs {
     int m, c0, b, fanin, P0, lowp;
     float* rbuf;
     float* qbuf;
-    unsigned* cnt;
+    unsigned* cnt;      // per-node arrival counters (zero on entry, self-resetting)
+    unsigned* sync;     // [0] root-done flag, [1] exit count (one-launch path)
+    int* err;
     PanelLevels lv;
 };
 
@@ -95,98 +97,94 @@ __device__ __forceinline__ float block_reduce_vec(float (&x)[S], float* red, int
     return t;
 }
 
-// One column K of CGS2 on the register-resident block v (see file comment).
-template <int B, int K>
-__device__ __forceinline__ void cgs2_column(float (&v)[kRPT][B], int b, float* red, int& parity,
-                                            float* Rs) {
-    if (K >= b) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float hacc = 0.f;   // lane j < K: R[j][K]
-    if constexpr (K > 0) {
-        constexpr int S1 = pow2ceil(K);
-        float p[S1];
-#pragma unroll
-        for (int j = 0; j < S1; ++j) {
-            float s = 0.f;
-            if (j < K) {
-#pragma unroll
-                for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][K], s);
-            }
-            p[j] = s;
-        }
-        const float h = block_reduce_vec<S1>(p, red, parity);
-        hacc = lane < K ? h : 0.f;
-        float acc[kRPT];
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) acc[r] = v[r][K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const float hj = __shfl_sync(kFullMask, h, j);
-#pragma unroll
-            for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) v[r][K] = acc[r];
-    }
-    // second pass (or the only one for K = 0) together with ||a_K||^2 at index K
-    constexpr int S2 = pow2ceil(K + 1);
-    float p2[S2];
-#pragma unroll
-    for (int j = 0; j < S2; ++j) {
-        float s = 0.f;
-        if (j <= K) {
-#pragma unroll
-            for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][K], s);
-        }
-        p2[j] = s;
-    }
-    const float h2 = block_reduce_vec<S2>(p2, red, parity);
-    const float nn = __shfl_sync(kFullMask, h2, K);
-    float normsq = nn;
-    if constexpr (K > 0) {
-        float acc[kRPT];
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) acc[r] = v[r][K];
-        float hh = 0.f;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const float hj = __shfl_sync(kFullMask, h2, j);
-            hh = fmaf(hj, hj, hh);
-#pragma unroll
-            for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) v[r][K] = acc[r];
-        hacc += lane < K ? h2 : 0.f;
-        normsq = nn - hh;
-        if (!(normsq >= 0.25f * nn)) {     // second pass removed a large part: reduce directly
-            float d[1];
-            d[0] = 0.f;
-#pragma unroll
-            for (int r = 0; r < kRPT; ++r) d[0] = fmaf(v[r][K], v[r][K], d[0]);
-            normsq = block_reduce_vec<1>(d, red, parity);
-        }
-    }
-    const float nrm = sqrtf(fmaxf(normsq, 0.f));
-    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-#pragma unroll
-    for (int r = 0; r < kRPT; ++r) v[r][K] *= inv;
-    if (warp == 0) {
-        if (lane < K) Rs[lane * 33 + K] = hacc;
-        if (lane == K) Rs[K * 33 + K] = nrm;
-    }
-}
-
-template <int B, int... Ks>
-__device__ __forceinline__ void cgs2_all(float (&v)[kRPT][B], int b, float* red, int& parity, float* Rs,
-                                         std::integer_sequence<int, Ks...>) {
-    (cgs2_column<B, Ks>(v, b, red, parity, Rs), ...);
-}
-
+// CGS2 on the register-resident block v (see file comment), one column per loop trip.
+// The block is kept rotated so that every register index is a compile-time constant: at step
+// k the column being orthogonalised is at position 0, the raw columns a_{k+1..} follow, and
+// q_0..q_{k-1} occupy positions B-k..B-1 (q_j at B-k+j). After normalising, the block is
+// rotated left by one, which appends q_k at position B-1. After b steps q_j is at B-b+j.
+// Rs (32 x 33, row-major) receives R.
 template <int B>
-__device__ __forceinline__ void cgs2_block(float (&v)[kRPT][B], int b, float* red, float* Rs) {
+__device__ void cgs2_block(float (&v)[kRPT][B], int b, float* red, float* Rs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int parity = 0;
-    cgs2_all<B>(v, b, red, parity, Rs, std::make_integer_sequence<int, B>{});
+#pragma unroll 1
+    for (int k = 0; k < b; ++k) {
+        const int qs = B - k;              // first position holding a finished q
+        float hacc = 0.f;                  // lane p (p >= qs): R[p - qs][k]
+        if (k > 0) {
+            float p1[B];
+            p1[0] = 0.f;
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                float s = 0.f;
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][0], s);
+                p1[j] = j >= qs ? s : 0.f;
+            }
+            const float h = block_reduce_vec<B>(p1, red, parity);
+            hacc = h;
+            float acc[kRPT];
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) acc[r] = v[r][0];
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const float hj = j >= qs ? __shfl_sync(kFullMask, h, j) : 0.f;
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) v[r][0] = acc[r];
+        }
+        // second pass together with ||a_k||^2 at index 0
+        float p2[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) s = fmaf(v[r][j], v[r][0], s);
+            p2[j] = (j == 0 || j >= qs) ? s : 0.f;
+        }
+        const float h2 = block_reduce_vec<B>(p2, red, parity);
+        const float nn = __shfl_sync(kFullMask, h2, 0);
+        float normsq = nn;
+        if (k > 0) {
+            float acc[kRPT];
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) acc[r] = v[r][0];
+            float hh = 0.f;
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const float hj = j >= qs ? __shfl_sync(kFullMask, h2, j) : 0.f;
+                hh = fmaf(hj, hj, hh);
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) acc[r] = fmaf(-v[r][j], hj, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kRPT; ++r) v[r][0] = acc[r];
+            hacc += h2;
+            normsq = nn - hh;
+            if (!(normsq >= 0.25f * nn)) {     // the second pass removed a large part: reduce directly
+                float d[1];
+                d[0] = 0.f;
+#pragma unroll
+                for (int r = 0; r < kRPT; ++r) d[0] = fmaf(v[r][0], v[r][0], d[0]);
+                normsq = block_reduce_vec<1>(d, red, parity);
+            }
+        }
+        const float nrm = sqrtf(fmaxf(normsq, 0.f));
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        if (warp == 0) {
+            if (lane < B && lane >= qs) Rs[(lane - qs) * 33 + k] = hacc;
+            if (lane == 0) Rs[k * 33 + k] = nrm;
+        }
+#pragma unroll
+        for (int r = 0; r < kRPT; ++r) {
+            const float q = v[r][0] * inv;
+#pragma unroll
+            for (int j = 0; j < B - 1; ++j) v[r][j] = v[r][j + 1];
+            v[r][B - 1] = q;
+        }
+    }
     __syncthreads();   // Rs complete
 }
 
@@ -213,21 +211,11 @@ __device__ __forceinline__ void write_rblock(float* dst, const float* Rs) {
     for (int i = threadIdx.x; i < 1024; i += kPanelThreads) dst[i] = Rs[(i >> 5) * 33 + (i & 31)];
 }
 
+// Load the CTA's leaf block (rows t + 256 r of [s, s + rows)) and factor it.
 template <int B>
-__global__ void __launch_bounds__(kPanelThreads, 1)
-panel_leaf_tree_kernel(PanelArgs a) {
-    __shared__ float red[2 * kPanelWarps * 32];
-    __shared__ float Rs[32 * 33];
-    __shared__ int s_last;
-    const int t = threadIdx.x;
-    const int b = a.b;
-    for (int i = t; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
-
-    // ---- step 1: factor this CTA's row block (rows t + 256 r) ----
-    int s, e;
-    leaf_range(a.m, a.P0, blockIdx.x, s, e);
-    const int rows = e - s;
-    float v[kRPT][B];
+__device__ __forceinline__ void leaf_factor(const PanelArgs& a, float (&v)[kRPT][B], float* red, float* Rs,
+                                            int s, int rows) {
+    const int t = threadIdx.x, b = a.b;
 #pragma unroll
     for (int r = 0; r < kRPT; ++r) {
         const int lr = t + r * kPanelThreads;
@@ -237,31 +225,35 @@ panel_leaf_tree_kernel(PanelArgs a) {
     }
     __syncthreads();
     cgs2_block<B>(v, b, red, Rs);
+}
 
-    if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
-#pragma unroll
-        for (int r = 0; r < kRPT; ++r) {
-            const int lr = t + r * kPanelThreads;
-            if (lr < rows)
-#pragma unroll
-                for (int j = 0; j < B; ++j)
-                    if (j < b) store_q(a, s + lr, j, v[r][j]);
-        }
-        write_r11(a, Rs);
-        return;
-    }
+// Store the factored block's Q (q_j at register position B - b + j): to W and Wh when
+// `final`, to W only otherwise.
+template <int B>
+__device__ __forceinline__ void store_leaf_q(const PanelArgs& a, const float (&v)[kRPT][B], int s, int rows,
+                                             bool final) {
+    const int t = threadIdx.x, off = B - a.b;
 #pragma unroll
     for (int r = 0; r < kRPT; ++r) {
         const int lr = t + r * kPanelThreads;
-        if (lr < rows)
+        if (lr >= rows) continue;
 #pragma unroll
-            for (int j = 0; j < B; ++j)
-                if (j < b) a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] = v[r][j];
+        for (int p = 0; p < B; ++p) {
+            const int j = p - off;
+            if (j < 0) continue;
+            if (final) store_q(a, s + lr, j, v[r][p]);
+            else a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] = v[r][p];
+        }
     }
-    write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[0] + blockIdx.x) * 1024, Rs);
+}
 
-    // ---- steps 2-3: combine stacked R factors up the tree (last arriver does the work) ----
-    int node = blockIdx.x;
+// Steps 2-3: climb the tree from leaf `node`; at each level the CTA that arrives last in its
+// group factors the group's stacked R factors. Returns true for the CTA that factored the
+// root (R11 written), false for a CTA that stopped because it was not last.
+template <int B>
+__device__ bool climb_tree(const PanelArgs& a, float (&v)[kRPT][B], float* red, float* Rs, int node,
+                           int* s_last) {
+    const int t = threadIdx.x, b = a.b, off = B - b;
     for (int l = 0; l < a.lv.nlev; ++l) {
         const int parent = node / a.fanin;
         const int nch = min(a.fanin, a.lv.nodes[l] - parent * a.fanin);
@@ -270,11 +262,11 @@ panel_leaf_tree_kernel(PanelArgs a) {
         if (t == 0) {
             unsigned* c = a.cnt + a.lv.cnt_off[l + 1] + parent;
             const unsigned old = atomicAdd(c, 1u);
-            s_last = (old == (unsigned)(nch - 1));
-            if (s_last) atomicExch(c, 0u);   // self-reset for the next panel
+            *s_last = (old == (unsigned)(nch - 1));
+            if (*s_last) atomicExch(c, 0u);   // self-reset for the next panel
         }
         __syncthreads();
-        if (!s_last) return;
+        if (!*s_last) return false;
         __threadfence();
         const float* src0 = a.rbuf + (size_t)(a.lv.rbuf_off[l] + parent * a.fanin) * 1024;
 #pragma unroll
@@ -294,29 +286,27 @@ panel_leaf_tree_kernel(PanelArgs a) {
             const int rho = t + r * kPanelThreads;
             if (rho < nch * b)
 #pragma unroll
-                for (int j = 0; j < B; ++j) qdst[rho * 32 + j] = v[r][j];
+                for (int p = 0; p < B; ++p)
+                    if (p >= off) qdst[rho * 32 + (p - off)] = v[r][p];
         }
         if (a.lv.nodes[l + 1] == 1) {
             write_r11(a, Rs);
-            return;
+            return true;
         }
         write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[l + 1] + parent) * 1024, Rs);
         node = parent;
     }
+    return false;
 }
 
-// Steps 4-5: Q_i <- Q_i (S_1 S_2 ... S_top), S_l the b x b slice of the level-l tree Q on the
-// block's path; writes the FP32 Q and its low-precision copy.
+// Steps 4-5 for leaf block `leaf`: Q_i <- Q_i (S_1 S_2 ... S_top), S_l the b x b slice of the
+// level-l tree Q on the block's path; reads the leaf Q from W, writes Q to W and Wh.
 template <int B>
-__global__ void __launch_bounds__(kPanelThreads)
-panel_reconstruct_kernel(PanelArgs a) {
-    __shared__ float T[32 * 33];
-    __shared__ float U[32 * 33];
-    const int t = threadIdx.x;
-    const int b = a.b;
+__device__ void reconstruct(const PanelArgs& a, int leaf, float* T, float* U) {
+    const int t = threadIdx.x, b = a.b;
     for (int i = t; i < 32 * 33; i += kPanelThreads) T[i] = (i / 33 == i % 33) ? 1.f : 0.f;
     __syncthreads();
-    int node = blockIdx.x;
+    int node = leaf;
     for (int l = 0; l < a.lv.nlev; ++l) {
         const int parent = node / a.fanin, child = node % a.fanin;
         const float* q = a.qbuf + (size_t)(a.lv.qbuf_off[l + 1] + parent) * (kNodeRows * 32) + (size_t)child * b * 32;
@@ -332,7 +322,7 @@ panel_reconstruct_kernel(PanelArgs a) {
         node = parent;
     }
     int s, e;
-    leaf_range(a.m, a.P0, blockIdx.x, s, e);
+    leaf_range(a.m, a.P0, leaf, s, e);
     const int rows = e - s;
 #pragma unroll 1
     for (int r = 0; r < kRPT; ++r) {
@@ -341,7 +331,7 @@ panel_reconstruct_kernel(PanelArgs a) {
         const size_t row = (size_t)(s + lr);
         float q[B];
 #pragma unroll
-        for (int j = 0; j < B; ++j) q[j] = j < b ? a.W[row + (size_t)(a.c0 + j) * a.ldw] : 0.f;
+        for (int j = 0; j < B; ++j) q[j] = j < b ? __ldcg(a.W + row + (size_t)(a.c0 + j) * a.ldw) : 0.f;
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if (j >= b) break;
@@ -353,10 +343,94 @@ panel_reconstruct_kernel(PanelArgs a) {
     }
 }
 
+// Two-launch path, step 1-3 (any number of leaf blocks).
+template <int B>
+__global__ void __launch_bounds__(kPanelThreads, 1)
+panel_leaf_tree_kernel(PanelArgs a) {
+    __shared__ float red[2 * kPanelWarps * 32];
+    __shared__ float Rs[32 * 33];
+    __shared__ int s_last;
+    for (int i = threadIdx.x; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
+    int s, e;
+    leaf_range(a.m, a.P0, blockIdx.x, s, e);
+    float v[kRPT][B];
+    leaf_factor<B>(a, v, red, Rs, s, e - s);
+    if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
+        store_leaf_q<B>(a, v, s, e - s, true);
+        write_r11(a, Rs);
+        return;
+    }
+    store_leaf_q<B>(a, v, s, e - s, false);
+    write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[0] + blockIdx.x) * 1024, Rs);
+    climb_tree<B>(a, v, red, Rs, blockIdx.x, &s_last);
+}
+
+// Two-launch path, steps 4-5.
+template <int B>
+__global__ void __launch_bounds__(kPanelThreads)
+panel_reconstruct_kernel(PanelArgs a) {
+    __shared__ float T[32 * 33];
+    __shared__ float U[32 * 33];
+    reconstruct<B>(a, blockIdx.x, T, U);
+}
+
+// One-launch path (cooperative launch, all leaf CTAs resident): after the tree, every CTA
+// waits (bounded) for the root CTA's completion flag, then rebuilds its own block. The last
+// CTA to finish resets the flag words for the next panel.
+template <int B>
+__global__ void __launch_bounds__(kPanelThreads, 1)
+panel_coop_kernel(PanelArgs a) {
+    __shared__ float red[2 * kPanelWarps * 32];
+    __shared__ float Rs[32 * 33];
+    __shared__ float U[32 * 33];
+    __shared__ int s_last, s_ok;
+    for (int i = threadIdx.x; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
+    int s, e;
+    leaf_range(a.m, a.P0, blockIdx.x, s, e);
+    {
+        float v[kRPT][B];
+        leaf_factor<B>(a, v, red, Rs, s, e - s);
+        store_leaf_q<B>(a, v, s, e - s, false);
+        write_rblock(a.rbuf + (size_t)(a.lv.rbuf_off[0] + blockIdx.x) * 1024, Rs);
+        const bool root = climb_tree<B>(a, v, red, Rs, blockIdx.x, &s_last);
+        if (root) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicExch(a.sync, 1u);
+        }
+    }
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = globaltimer_ns();
+        while (atomicAdd(a.sync, 0u) == 0u) {
+            if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(200);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) reconstruct<B>(a, blockIdx.x, Rs, U);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.sync + 1, 1u) == (unsigned)(a.P0 - 1)) {
+            atomicExch(a.sync + 1, 0u);
+            atomicExch(a.sync, 0u);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
 static int bucket(int b) { return b <= 8 ? 8 : (b <= 16 ? 16 : 32); }
+
+constexpr int kSyncWords = 2;   // cnt[0..1]: root-done flag and exit count of the one-launch path
 
 static void panel_levels(int m, int b, PanelLevels& lv, int& P0, int& fanin) {
     P0 = ceil_div(m, kNodeRows);
@@ -367,7 +441,7 @@ static void panel_levels(int m, int b, PanelLevels& lv, int& P0, int& fanin) {
         lv.nodes[lv.nlev + 1] = ceil_div(lv.nodes[lv.nlev], fanin);
         lv.nlev++;
     }
-    int ro = 0, qo = 0, co = 0;
+    int ro = 0, qo = 0, co = kSyncWords;
     for (int l = 0; l <= lv.nlev; ++l) {
         lv.rbuf_off[l] = ro;
         ro += lv.nodes[l];
@@ -385,11 +459,32 @@ void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t
     for (int l = 0; l <= lv.nlev; ++l) { nodes += lv.nodes[l]; if (l > 0) upper += lv.nodes[l]; }
     rbuf_floats = nodes * 1024;
     qbuf_floats = (upper + 1) * (size_t)kNodeRows * 32;
-    cnt_words = upper + 1;
+    cnt_words = upper + kSyncWords + 1;
 }
 
 template <int B>
-static int launch_panel(const PanelArgs& a, cudaStream_t st) {
+static int coop_capacity() {
+    static int cap = -1;
+    if (cap < 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_coop_kernel<B>, kPanelThreads, 0) != cudaSuccess)
+            cap = 0;
+        else
+            cap = sms * per;
+    }
+    return cap;
+}
+
+template <int B>
+static int launch_panel(PanelArgs& a, cudaStream_t st) {
+    if (a.P0 > 1 && a.P0 <= coop_capacity<B>()) {
+        void* args[] = {&a};
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_coop_kernel<B>, dim3(a.P0), dim3(kPanelThreads), args, 0, st));
+        LLS_LAUNCH_CHECK("panel_coop", st);
+        return LLS_OK;
+    }
     panel_leaf_tree_kernel<B><<<a.P0, kPanelThreads, 0, st>>>(a);
     LLS_LAUNCH_CHECK("panel_leaf_tree", st);
     if (a.P0 > 1) {
@@ -404,7 +499,7 @@ int panel_qr(const PanelCall& c, cudaStream_t st) {
     PanelArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
-    a.rbuf = c.rbuf; a.qbuf = c.qbuf; a.cnt = c.cnt;
+    a.rbuf = c.rbuf; a.qbuf = c.qbuf; a.cnt = c.cnt; a.sync = c.cnt; a.err = c.err;
     panel_levels(c.m, c.b, a.lv, a.P0, a.fanin);
     if (a.lv.nodes[a.lv.nlev] != 1) return LLS_ERR_UNSUPPORTED;
     const int bk = bucket(c.b);

@@ -21,7 +21,8 @@ STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_S
 
 EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
            "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve",
-           "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update")
+           "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update",
+           "lls_backward_workspace_size", "lls_backward")
 
 
 class lls_options(C.Structure):
@@ -79,6 +80,13 @@ def load(path: str = LIB_PATH):
     lib.lls_lowp_projection.restype = i
     lib.lls_lowp_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, vp, i, vp, sz, vp]
     lib.lls_lowp_update.restype = i
+    ip = C.POINTER(C.c_int)
+    pp = C.POINTER(C.c_void_p)
+    lib.lls_backward_workspace_size.argtypes = [i, ip, ip, C.POINTER(lls_options)]
+    lib.lls_backward_workspace_size.restype = sz
+    lib.lls_backward.argtypes = [i, ip, ip, pp, ip, pp, pp, pp, ip, pp, pp, ip, pp, vp, sz,
+                                 C.POINTER(lls_options), vp]
+    lib.lls_backward.restype = i
     _lib = lib
     return lib
 
@@ -145,6 +153,28 @@ def lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl,
 def lls_lowp_update(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes, stream) -> int:
     return load().lls_lowp_update(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes,
                                   stream)
+
+
+def _ints(v):
+    return (C.c_int * len(v))(*[int(t) for t in v])
+
+
+def _ptrs(v):
+    return (C.c_void_p * len(v))(*[int(t) if t else None for t in v])
+
+
+def lls_backward_workspace_size(batch, m, n, opts=None) -> int:
+    return load().lls_backward_workspace_size(batch, _ints(m), _ints(n),
+                                              C.byref(opts) if opts is not None else None)
+
+
+def lls_backward(batch, m, n, A, lda, b, x, R, ldr, grad_x, grad_A, ldga, grad_b, ws, ws_bytes,
+                 opts, stream) -> int:
+    """m, n, lda, ldr, ldga: int sequences; A ... grad_b: sequences of device pointers."""
+    return load().lls_backward(batch, _ints(m), _ints(n), _ptrs(A), _ints(lda), _ptrs(b), _ptrs(x),
+                               _ptrs(R), _ints(ldr), _ptrs(grad_x), _ptrs(grad_A), _ints(ldga),
+                               _ptrs(grad_b), ws, ws_bytes, C.byref(opts) if opts is not None else None,
+                               stream)
 
 
 # ---- torch helpers (allocation and pointer passing only) -----------------------------------
@@ -224,3 +254,96 @@ def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=3
     d = info.as_dict()
     d["status_code"] = st
     return (x, d, R) if want_r else (x, d)
+
+
+def backward(As, bs, xs, Rs, gxs, prec="fp16", target="fp64", max_iter=200, stream=None):
+    """Adjoint for a list of problems: returns (grad_As, grad_bs) as column-major FP32 and FP64
+    device tensors. As: column-major FP32 (m, n); bs, xs, gxs: FP64 vectors; Rs: (n, n) FP32."""
+    torch = _torch()
+    batch = len(As)
+    ms = [A.shape[0] for A in As]
+    ns = [A.shape[1] for A in As]
+    o = make_options(prec=prec, target=target, max_iter=max_iter)
+    nb = lls_backward_workspace_size(batch, ms, ns, o)
+    if nb == 0:
+        raise LLSError(-1, "lls_backward_workspace_size")
+    dev = As[0].device
+    ws = workspace(nb, dev)
+    gAs = [torch.empty((n_, m_), dtype=torch.float32, device=dev).t() for m_, n_ in zip(ms, ns)]
+    gbs = [torch.empty(m_, dtype=torch.float64, device=dev) for m_ in ms]
+    bs = [b.to(device=dev, dtype=torch.float64).contiguous() for b in bs]
+    xs = [x.to(device=dev, dtype=torch.float64).contiguous() for x in xs]
+    gxs = [g.to(device=dev, dtype=torch.float64).contiguous() for g in gxs]
+    for A in As:
+        _check_colmajor(A)
+    for R in Rs:
+        _check_colmajor(R)
+    st = lls_backward(batch, ms, ns, [A.data_ptr() for A in As], [A.stride(1) for A in As],
+                      [b.data_ptr() for b in bs], [x.data_ptr() for x in xs],
+                      [R.data_ptr() for R in Rs], [R.stride(1) for R in Rs],
+                      [g.data_ptr() for g in gxs], [g.data_ptr() for g in gAs],
+                      [g.stride(1) for g in gAs], [g.data_ptr() for g in gbs],
+                      ws.data_ptr(), ws.numel(), o, _stream(stream))
+    if st != 0:
+        raise LLSError(st, "lls_backward")
+    return gAs, gbs
+
+
+class _LstsqFunction:
+    """Namespace holder; the autograd Function is created lazily so importing this module
+    does not import torch."""
+    fn = None
+
+
+def _make_function():
+    torch = _torch()
+
+    class LLSFunction(torch.autograd.Function):
+        """x = argmin ||A x - b||_2 for A (m, n) or a batch (B, m, n); differentiable in A and b.
+
+        Forward: lls_solve (RGSQRF + preconditioned CGLS). Backward: lls_backward (the
+        textbook adjoint, with z = (A^T A)^{-1} g from CG preconditioned by the forward R)."""
+
+        @staticmethod
+        def forward(ctx, A, b, opts):
+            batched = A.dim() == 3
+            As = list(A) if batched else [A]
+            bs = list(b) if batched else [b]
+            Acm = [colmajor(a.detach(), device=a.device) for a in As]
+            xs, Rs = [], []
+            for a_cm, bv in zip(Acm, bs):
+                x, info, R = solve(a_cm, bv.detach(), want_r=True, **opts)
+                if info["status_code"] < 0:
+                    raise LLSError(info["status_code"], "lls_solve")
+                xs.append(x)
+                Rs.append(R)
+            ctx.batched = batched
+            ctx.opts = opts
+            ctx.bdtype = b.dtype
+            ctx.Adtype = A.dtype
+            ctx.Acm, ctx.Rs = Acm, Rs
+            ctx.save_for_backward(b, *xs)
+            x = torch.stack(xs) if batched else xs[0]
+            return x.to(b.dtype)
+
+        @staticmethod
+        def backward(ctx, gx):
+            b = ctx.saved_tensors[0]
+            xs = list(ctx.saved_tensors[1:])
+            bs = list(b) if ctx.batched else [b]
+            gxs = list(gx) if ctx.batched else [gx]
+            gAs, gbs = backward(ctx.Acm, bs, xs, ctx.Rs, gxs, prec=ctx.opts.get("prec", "fp16"),
+                                target=ctx.opts.get("target", "fp64"),
+                                max_iter=ctx.opts.get("max_iter", 200))
+            gA = torch.stack(gAs) if ctx.batched else gAs[0]
+            gb = torch.stack(gbs) if ctx.batched else gbs[0]
+            return gA.to(ctx.Adtype), gb.to(ctx.bdtype), None
+
+    return LLSFunction
+
+
+def lstsq(A, b, **opts):
+    """Differentiable least-squares solve on the GPU (see LLSFunction)."""
+    if _LstsqFunction.fn is None:
+        _LstsqFunction.fn = _make_function()
+    return _LstsqFunction.fn.apply(A, b, opts)
