@@ -127,6 +127,29 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
               lls_info* info, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched solve: `batch` independent problems min ||A_i x_i - b_i||, uneven sizes, in one
+ * persistent launch (each SM takes whole problems from a device work queue, largest first,
+ * and runs factorization, preconditioner and CGLS on its own; 16-column panels).
+ *  m, n, lda, ldr: HOST arrays of `batch` ints; n_i <= m_i <= 8192, n_i <= 1024.
+ *  A, b, x, R_out: HOST arrays of `batch` DEVICE pointers (A_i m_i x n_i FP32, b_i m_i FP64,
+ *     x_i n_i FP64 output, R_out_i n_i x n_i FP32 output or NULL; R_out itself may be NULL).
+ *  ws: lls_solve_batched_workspace_size(batch, m, n, opts) bytes, 256-byte aligned.
+ *  infos: HOST array of `batch` lls_info, or NULL. When non-NULL the call synchronizes the
+ *     stream and fills one record per problem (krylov_ms holds the whole batch's time);
+ *     the return value is then the worst per-problem status.
+ *  opts: gemm_prec FP16 or BF16; panel_width is fixed at 16 in this path.
+ * The problem table is copied into the workspace first; the launch itself is replayed as
+ * a CUDA graph on non-default streams.
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED (sizes, FP32 products, LSQR),
+ *         LLS_ERR_CUDA; per-problem LLS_ERR_SINGULAR / LLS_NOT_CONVERGED through infos.
+ * -------------------------------------------------------------------------- */
+size_t lls_solve_batched_workspace_size(int batch, const int* m, const int* n, const lls_options* opts);
+int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                      const double* const* b, double* const* x, float* const* R_out, const int* ldr,
+                      void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
+                      cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint of the least-squares solution map (the paper has none; this is the textbook
  * sensitivity of x* = (A^T A)^{-1} A^T b, used by the differentiable solve).
  * For each problem i of the batch, given x_i = x*(A_i, b_i), the R factor R_i returned by

@@ -9,6 +9,8 @@
 // asynchronous on the caller's stream; nothing is allocated.
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -465,6 +467,92 @@ int lls_backward(int batch, const int* m, const int* n, const float* const* A, c
     }
     trace_flush();
     return LLS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched solve: many independent problems, one persistent launch (batched.cu).
+// ---------------------------------------------------------------------------------------
+struct BatchExec {
+    int batch; const int* m; const int* n; void* ws; lls_options o;
+};
+
+static int enqueue_batched(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+    BatchExec& c = *(BatchExec*)p;
+    if (ev) record_phase(ev[0], st, capturing);
+    LLS_TRY(batched_execute(c.batch, c.m, c.n, c.ws, c.o, st));
+    if (ev) { record_phase(ev[1], st, capturing); record_phase(ev[2], st, capturing); }
+    return LLS_OK;
+}
+
+size_t lls_solve_batched_workspace_size(int batch, const int* m, const int* n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    int mmax, nmax;
+    if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return 0;
+    for (int i = 0; i < batch; ++i)
+        if (!batched_supported(m[i], n[i])) return 0;
+    return batched_workspace_bytes(batch, m, n);
+}
+
+int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                      const double* const* b, double* const* x, float* const* R_out, const int* ldr,
+                      void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
+                      cudaStream_t stream) {
+    lls_options o;
+    resolve(opts, o);
+    int mmax, nmax;
+    if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
+    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32) return LLS_ERR_UNSUPPORTED;
+    if (!A || !lda || !b || !x || !ws) return LLS_ERR_ARG;
+    for (int i = 0; i < batch; ++i) {
+        if (!batched_supported(m[i], n[i])) return LLS_ERR_UNSUPPORTED;
+        if (!A[i] || !b[i] || !x[i] || lda[i] < m[i]) return LLS_ERR_ARG;
+        if (R_out && R_out[i] && (!ldr || ldr[i] < n[i])) return LLS_ERR_ARG;
+    }
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    if (infos) memset(infos, 0, sizeof(lls_info) * (size_t)batch);
+    trace_mark(stream);
+    LLS_TRY(batched_upload(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, stream));
+    BatchExec c;
+    c.batch = batch; c.m = m; c.n = n; c.ws = ws; c.o = o;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.op = 3; key.device = current_device();
+    key.ints[0] = batch;
+    key.ptrs[0] = ws;
+    key.ws_bytes = ws_bytes; key.opts = o;
+    cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (infos) {
+        for (int i = 0; i < 3; ++i) LLS_CUDA_TRY(cudaEventCreate(&own[i]));
+        for (int i = 0; i < 3; ++i) ev[i] = own[i];
+    }
+    int rc = run_graphed(key, stream, enqueue_batched, &c, infos ? ev : nullptr);
+    trace_flush();
+    if (rc != LLS_OK || !infos) {
+        for (auto& e : own) if (e) cudaEventDestroy(e);
+        return rc;
+    }
+    std::vector<double> h((size_t)16 * batch);
+    LLS_CUDA_TRY(cudaMemcpyAsync(h.data(), batched_info_ptr(ws, batch, m, n), sizeof(double) * h.size(),
+                                 cudaMemcpyDeviceToHost, stream));
+    LLS_CUDA_TRY(cudaStreamSynchronize(stream));
+    float total_ms = 0.f;
+    cudaEventElapsedTime(&total_ms, ev[0], ev[1]);
+    for (auto& e : own) cudaEventDestroy(e);
+    int worst = LLS_OK;
+    for (int i = 0; i < batch; ++i) {
+        const double* d = &h[(size_t)16 * i];
+        lls_info& f = infos[i];
+        f.iters = (int)d[0]; f.eta = d[1]; f.fwd_est = d[2]; f.res_norm = d[3]; f.atr_norm = d[4];
+        f.anorm_f = d[5]; f.xnorm = d[6]; f.a_passes = (int)d[10]; f.m_passes = (int)d[11];
+        f.krylov_ms = total_ms;
+        const int s = (int)d[7];
+        f.status = s == 0 ? LLS_OK : (s == -2 ? LLS_ERR_SINGULAR : LLS_NOT_CONVERGED);
+        if (f.status < 0) worst = f.status;
+        else if (f.status > 0 && worst == LLS_OK) worst = f.status;
+    }
+    return worst;
 }
 
 }  // extern "C"

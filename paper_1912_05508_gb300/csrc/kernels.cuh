@@ -99,6 +99,15 @@ struct AdjointCall {
 };
 int adjoint_solve(const AdjointCall& c, cudaStream_t st);
 
+// ---- batched solver (batched.cu) -----------------------------------------------------------
+bool batched_supported(int m, int n);
+size_t batched_workspace_bytes(int batch, const int* m, const int* n);
+double* batched_info_ptr(void* ws, int batch, const int* m, const int* n);
+int batched_upload(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                   const double* const* b, double* const* x, float* const* Rout, const int* ldr,
+                   void* ws, size_t ws_bytes, cudaStream_t st);
+int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, cudaStream_t st);
+
 // ---- graph replay (graph.cu) -----------------------------------------------------------------
 // Identity of one call: plain-old-data, compared bytewise (zero-initialize before filling).
 struct GraphKey {

@@ -22,7 +22,8 @@ STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_S
 EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
            "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve",
            "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update",
-           "lls_backward_workspace_size", "lls_backward")
+           "lls_backward_workspace_size", "lls_backward",
+           "lls_solve_batched_workspace_size", "lls_solve_batched")
 
 
 class lls_options(C.Structure):
@@ -87,6 +88,11 @@ def load(path: str = LIB_PATH):
     lib.lls_backward.argtypes = [i, ip, ip, pp, ip, pp, pp, pp, ip, pp, pp, ip, pp, vp, sz,
                                  C.POINTER(lls_options), vp]
     lib.lls_backward.restype = i
+    lib.lls_solve_batched_workspace_size.argtypes = [i, ip, ip, C.POINTER(lls_options)]
+    lib.lls_solve_batched_workspace_size.restype = sz
+    lib.lls_solve_batched.argtypes = [i, ip, ip, pp, ip, pp, pp, pp, ip, vp, sz, C.POINTER(lls_options),
+                                      C.POINTER(lls_info), vp]
+    lib.lls_solve_batched.restype = i
     _lib = lib
     return lib
 
@@ -175,6 +181,20 @@ def lls_backward(batch, m, n, A, lda, b, x, R, ldr, grad_x, grad_A, ldga, grad_b
                                _ptrs(R), _ints(ldr), _ptrs(grad_x), _ptrs(grad_A), _ints(ldga),
                                _ptrs(grad_b), ws, ws_bytes, C.byref(opts) if opts is not None else None,
                                stream)
+
+
+def lls_solve_batched_workspace_size(batch, m, n, opts=None) -> int:
+    return load().lls_solve_batched_workspace_size(batch, _ints(m), _ints(n),
+                                                   C.byref(opts) if opts is not None else None)
+
+
+def lls_solve_batched(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, infos, stream) -> int:
+    """m, n, lda, ldr: int sequences; A, b, x, R_out: sequences of device pointers (R_out may be
+    None); infos: a ctypes array of lls_info or None."""
+    return load().lls_solve_batched(batch, _ints(m), _ints(n), _ptrs(A), _ints(lda), _ptrs(b), _ptrs(x),
+                                    _ptrs(R_out) if R_out is not None else None,
+                                    _ints(ldr) if ldr is not None else None, ws, ws_bytes,
+                                    C.byref(opts) if opts is not None else None, infos, stream)
 
 
 # ---- torch helpers (allocation and pointer passing only) -----------------------------------
@@ -347,3 +367,35 @@ def lstsq(A, b, **opts):
     if _LstsqFunction.fn is None:
         _LstsqFunction.fn = _make_function()
     return _LstsqFunction.fn.apply(A, b, opts)
+
+
+def solve_batched(As, bs, prec="fp16", target="fp32", tol=0.0, max_iter=200, want_r=False, ws=None,
+                  stream=None, check=True):
+    """Solve a list of independent problems in one persistent launch.
+
+    As: column-major FP32 device matrices (m_i, n_i); bs: FP64 device vectors.
+    Returns (xs, infos[, Rs]) with infos a list of dicts."""
+    torch = _torch()
+    batch = len(As)
+    for A in As:
+        _check_colmajor(A)
+    ms = [A.shape[0] for A in As]
+    ns = [A.shape[1] for A in As]
+    o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter, panel_width=16)
+    nb = lls_solve_batched_workspace_size(batch, ms, ns, o)
+    if nb == 0:
+        raise LLSError(-6, "lls_solve_batched_workspace_size")
+    dev = As[0].device
+    ws = ws if ws is not None and ws.numel() >= nb else workspace(nb, dev)
+    bs = [b.to(device=dev, dtype=torch.float64).contiguous() for b in bs]
+    xs = [torch.empty(n_, dtype=torch.float64, device=dev) for n_ in ns]
+    Rs = [torch.empty((n_, n_), dtype=torch.float32, device=dev).t() for n_ in ns] if want_r else None
+    infos = (lls_info * batch)()
+    st = lls_solve_batched(batch, ms, ns, [A.data_ptr() for A in As], [A.stride(1) for A in As],
+                           [b.data_ptr() for b in bs], [x.data_ptr() for x in xs],
+                           [R.data_ptr() for R in Rs] if want_r else None,
+                           ns if want_r else None, ws.data_ptr(), ws.numel(), o, infos, _stream(stream))
+    if check and st < 0:
+        raise LLSError(st, "lls_solve_batched")
+    out = [infos[i].as_dict() for i in range(batch)]
+    return (xs, out, Rs) if want_r else (xs, out)
