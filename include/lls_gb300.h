@@ -39,7 +39,8 @@ typedef enum {
     LLS_ERR_CUDA = -3,         /* a CUDA runtime or driver call failed */
     LLS_ERR_WORKSPACE = -4,    /* workspace too small or misaligned */
     LLS_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired (the kernel returned early) */
-    LLS_ERR_UNSUPPORTED = -6   /* valid but unimplemented option combination */
+    LLS_ERR_UNSUPPORTED = -6,  /* valid but unimplemented option combination */
+    LLS_ERR_TOO_LARGE = -7     /* sizes need more scratch than a fixed-scratch entry point holds */
 } lls_status;
 
 /* Precision of the two tensor-core products of each recursion step (Alg. 2 lines 8-9).
@@ -200,6 +201,37 @@ int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const 
 int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
                     int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
                     cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * lls_lowp_projection_noalloc: lls_lowp_projection without a workspace argument. The paper
+ * has no counterpart; this entry point exists for callers that cannot allocate device memory
+ * when they need the product, e.g. code inside a framework's op or plugin hook whose memory
+ * pool forbids allocation during execution, latency-bound paths that cannot afford the
+ * implicit device synchronisation of cudaMalloc/cudaFree, or host code that only holds
+ * borrowed device pointers. It allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine. Its scratch (split-K partial sums and a device error word) is one
+ * file-scope device array of LLS_NOALLOC_SCRATCH_BYTES (4 MiB) inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ * Arguments, layouts, outputs and the order of summation are those of lls_lowp_projection;
+ * Q1l, A2l, e, R12, R12l and f are caller-owned device memory, as there.
+ * Limit: accepted when lls_lowp_projection_workspace_size(m, w1, w2) <= LLS_NOALLOC_SCRATCH_BYTES,
+ *   otherwise LLS_ERR_TOO_LARGE is returned before any work (for example m = 8192 with
+ *   w1 = w2 = 128 fits; m = 32768 with w1 = w2 = 256 does not).
+ * Set-up: the first call on each device, with that device current, looks up the array's
+ *   device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture begins.
+ * Sharing: all calls in the process use the same array, which keeps the last call's
+ *   contents; each call clears the error word itself on the given stream. Calls whose work
+ *   overlaps on the GPU (different streams without ordering, several host threads) race on
+ *   the array and give wrong results: order them on one stream or with events.
+ * Errors: LLS_ERR_ARG, LLS_ERR_TOO_LARGE, LLS_ERR_UNSUPPORTED (alignment, device index >= 64),
+ *   LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+#define LLS_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+int lls_lowp_projection_noalloc(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l,
+                                int ldh, const int* e, float* R12, int ldr, void* R12l, int ldrl,
+                                int* f, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

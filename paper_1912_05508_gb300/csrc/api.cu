@@ -181,6 +181,7 @@ const char* lls_status_string(int s) {
         case LLS_ERR_WORKSPACE: return "workspace too small or misaligned";
         case LLS_ERR_TIMEOUT: return "device wait timed out";
         case LLS_ERR_UNSUPPORTED: return "unsupported option combination";
+        case LLS_ERR_TOO_LARGE: return "sizes exceed the fixed scratch of this entry point";
         default: return "unknown status";
     }
 }

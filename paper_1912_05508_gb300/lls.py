@@ -17,13 +17,15 @@ PREC = {"fp16": 0, "bf16": 1, "fp32": 3}
 TARGET = {"fp32": 0, "fp64": 1}
 KRYLOV = {"cgls": 0, "lsqr": 1}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
-          -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED"}
+          -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED",
+          -7: "LLS_ERR_TOO_LARGE"}
 
 EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
            "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve",
            "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update",
            "lls_backward_workspace_size", "lls_backward",
-           "lls_solve_batched_workspace_size", "lls_solve_batched")
+           "lls_solve_batched_workspace_size", "lls_solve_batched",
+           "lls_lowp_projection_noalloc")
 
 
 class lls_options(C.Structure):
@@ -79,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.lls_lowp_projection_workspace_size.restype = sz
     lib.lls_lowp_projection.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp, sz, vp]
     lib.lls_lowp_projection.restype = i
+    lib.lls_lowp_projection_noalloc.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp]
+    lib.lls_lowp_projection_noalloc.restype = i
     lib.lls_lowp_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, vp, i, vp, sz, vp]
     lib.lls_lowp_update.restype = i
     ip = C.POINTER(C.c_int)
@@ -154,6 +158,12 @@ def lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl,
                         stream) -> int:
     return load().lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f,
                                       ws, ws_bytes, stream)
+
+
+def lls_lowp_projection_noalloc(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f, stream) -> int:
+    """lls_lowp_projection with the library's fixed device scratch instead of a workspace."""
+    return load().lls_lowp_projection_noalloc(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f,
+                                              stream)
 
 
 def lls_lowp_update(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes, stream) -> int:
