@@ -156,6 +156,99 @@ def run_reference(args):
                               "d2h_bytes_per_step": 0}}))
 
 
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
+# it stands, from the captures summarised under profiles/; None once a kernel changes.
+NCU_TRAFFIC = {"panel": None, "tc_projection": None, "tc_update": None, "cgls": None}
+
+
+def split_point(w, pw):
+    return pw * (-(-w // (2 * pw)))
+
+
+def time_launches(launch, count, stream):
+    """Mean device time (ms) of `count` back-to-back calls, CUDA events on the launching stream."""
+    import torch
+    for i in range(3):
+        launch(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(count):
+        launch(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / count
+
+
+def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
+    """The panel and the two top-level tensor-core products of the bench shape, each timed
+    alone through its kernel-level C entry point. Inputs rotate over more than L2 holds."""
+    import torch
+    from paper_1912_05508_gb300 import lls
+    sh = stream.cuda_stream
+    pcode = lls.PREC[prec]
+    tdt = torch.float16 if prec == "fp16" else torch.bfloat16
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(7)
+
+    # panel: m x pw, algorithmic bytes = read m*pw FP32 + write Q (FP32) + write Q (2-byte copy)
+    nbuf = max(2, -(-(160 << 20) // (m * pw * 4)))
+    W = torch.randn((nbuf * pw, m), device=dev, generator=g).t()
+    Wh = torch.empty((nbuf * pw, m), dtype=tdt, device=dev).t()
+    R = torch.empty((pw, pw), device=dev)
+    pws = lls.workspace(lls.lls_panel_qr_workspace_size(m, pw), dev).zero_()
+
+    def panel(i):
+        k = i % nbuf
+        st = lls.lls_panel_qr(m, pw, pcode, W[:, k * pw:].data_ptr(), m, Wh[:, k * pw:].data_ptr(), m,
+                              R.data_ptr(), pw, pws.data_ptr(), pws.numel(), sh)
+        assert st == 0, st
+    ms = time_launches(panel, 200, stream)
+    by = 10.0 * m * pw
+    out["panel"] = {"kernel": f"panel_coop_kernel (CAQR panel {m}x{pw}, CGS2 leaves)", "bound": "hbm",
+                    "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "us_per_launch": ms * 1e3, "algorithmic_bytes_per_launch": by}
+    del W, Wh
+
+    # top recursion node: R12 = Q1^T A2 (projection) and A2 -= Q1 R12 (update)
+    w1 = split_point(n, pw)
+    w2 = n - w1
+    Q1l = (torch.randn((w1, m), device=dev, generator=g) / m ** 0.5).to(tdt).t()
+    A2l = torch.randn((w2, m), device=dev, generator=g).to(tdt).t()
+    A2 = torch.randn((w2, m), device=dev, generator=g).t()
+    e = torch.zeros(w2, dtype=torch.int32, device=dev)
+    R12 = torch.empty((w2, w1), device=dev)
+    ldrl = -(-w1 // 8) * 8
+    R12l = torch.empty((w2, ldrl), dtype=tdt, device=dev)
+    f = torch.zeros(w2, dtype=torch.int32, device=dev)
+    gws = lls.workspace(lls.lls_lowp_projection_workspace_size(m, w1, w2), dev)
+
+    def proj(i):
+        st = lls.lls_lowp_projection(m, w1, w2, pcode, Q1l.data_ptr(), A2l.data_ptr(), m, e.data_ptr(),
+                                     R12.data_ptr(), w1, R12l.data_ptr(), ldrl, f.data_ptr(), gws.data_ptr(),
+                                     gws.numel(), sh)
+        assert st == 0, st
+    ms_p = time_launches(proj, 10, stream)
+    R12l.zero_()     # the update then subtracts zero products: same work, A2 stays finite
+    f.zero_()
+
+    def upd(i):
+        st = lls.lls_lowp_update(m, w1, w2, pcode, Q1l.data_ptr(), m, R12l.data_ptr(), ldrl, f.data_ptr(),
+                                 A2.data_ptr(), m, gws.data_ptr(), gws.numel(), sh)
+        assert st == 0, st
+    ms_u = time_launches(upd, 10, stream)
+    fl = 2.0 * m * w1 * w2
+    for key, t, name in (("tc_projection", ms_p, f"tc_gemm_kernel projection R12 = Q1^T A2 ({w1}x{w2}x{m}, "
+                                                   f"split-K + fixed-order reduce)"),
+                         ("tc_update", ms_u, f"tc_gemm_kernel update A2 -= Q1 R12 ({m}x{w2}x{w1})")):
+        out[key] = {"kernel": name, "bound": "tensor", "achieved": fl / (t * 1e-3) / 1e12, "peak": tc_peak,
+                    "unit": "TFLOP/s", "us_per_launch": t * 1e3, "algorithmic_flops_per_launch": fl}
+    for k, v in out.items():
+        v["frac"] = v["achieved"] / v["peak"]
+        v["traffic"] = NCU_TRAFFIC.get(k)
+    return out
+
+
 def make_inputs(args, m, n, rank, dev):
     """Generate the problem on the device; keep a host copy in /tmp so a rerun of the same
     command (e.g. under a profiler, where torch's linear-algebra plugin may not load) reuses it."""
@@ -192,6 +285,7 @@ def main():
     m, n = args.m, args.n
     A, b = make_inputs(args, m, n, rank, dev)
     o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw)
+    pw = args.pw if args.pw > 0 else lls.default_options().panel_width
     nb = lls.lls_solve_workspace_size(m, n, o)
     wsbuf = lls.workspace(nb, dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
@@ -289,12 +383,16 @@ def main():
         hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
         hbm_peak, peak_src = 6800.0, "fallback"
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))   # FP16 and BF16 have the same dense rate
     achieved = kry_bytes / (kry_ms * 1e-3) / 1e9
-    roofline = {"kernel": "cgls_kernel (persistent CGLS iteration)", "bound": "hbm",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-                "traffic": None,
-                "algorithmic_bytes_per_launch": kry_bytes}
+    kernels = kernel_rooflines(m, n, pw, args.prec, stream, dev, hbm_peak, tc_peak)
+    kernels["cgls"] = {"kernel": "cgls_kernel (persistent CGLS iteration, whole Krylov phase)", "bound": "hbm",
+                       "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                       "traffic": NCU_TRAFFIC["cgls"], "algorithmic_bytes_per_launch": kry_bytes}
+    # the panel has the largest share of the solve in the ncu launch list
+    roofline = dict(kernels["panel"])
+    roofline["peak_source"] = ("measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peak_src == "measured"
+                               else "fallback 6800 GB/s")
     out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "fp16 products / f32 panel / double-float Krylov",
@@ -302,13 +400,14 @@ def main():
            "config": {"workload": f"single LLS {m}x{n} FP32, {args.kind} spectrum kappa={args.kappa:g}, "
                                   f"{args.prec.upper()} products, {args.target.upper()} target",
                       "m": m, "n": n, "prec": args.prec, "target": args.target,
-                      "panel_width": o.panel_width,
+                      "panel_width": pw,
                       "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
                       "parallelism": f"replicas x{ws}"},
            "qr_ms": qr_ms, "qr_tflops": qr_flops(m, n) / (qr_ms * 1e-3) / 1e12,
            "krylov_ms": kry_ms, "iters": last["iters"], "eta": last["eta"],
            "status": last["status"], "problems_per_s": ws * 1e3 / ms,
            "roofline": roofline,
+           "kernels": kernels,
            "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms",
                    "h2d_bytes_per_step": m * n * 4 + m * 8, "d2h_bytes_per_step": n * 8},
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,

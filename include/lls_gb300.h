@@ -61,7 +61,7 @@ typedef struct {
                           FP64: eta_est = ||R^-T A^T r|| / (||A||_F ||x||) <= 1e-12
                           FP32: fwd_est = ||R^-1||_F ||R^-T A^T r|| / ||x|| <= 1e-6 */
     int max_iter;      /* iteration cap, default 200 (the paper's cap, Sec. 4.2.3) */
-    int panel_width;   /* recursion leaf width b (columns per panel), 0 = default 32 (Sec. 3.1.3); 1..32 */
+    int panel_width;   /* recursion leaf width b (columns per panel), 0 = default 16 (the paper uses 32, Sec. 3.1.3); 1..32 */
     int krylov;        /* lls_krylov, default CGLS */
     int leaf_rows;     /* rows per CAQR leaf block, 0 = default 256 (Sec. 3.1.3); 64..256, multiple of 32 */
 } lls_options;
@@ -201,6 +201,31 @@ int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const 
 int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
                     int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
                     cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * lls_panel_qr: the tall-skinny panel factorization of one recursion leaf (Eq. caqr,
+ * Sec. 3.1.3): communication-avoiding QR over row blocks of <= 1024 rows with CGS2 leaves
+ * (classical Gram-Schmidt with one reorthogonalization; the paper's leaf is MGS, Alg. 4),
+ * the b x b R factors combined up a reduction tree, and each block's Q multiplied by its
+ * path of tree Q factors. Exposed for testing and for callers that run their own recursion.
+ *   m >= b, 1 <= b <= 32.
+ *   W   [in/out] m x b FP32, column-major (ldw >= m): the panel in, Q (orthonormal columns) out.
+ *   Wh  [out]    m x b copy of Q rounded to nearest even to FP16/BF16 (ldh >= m); ignored and
+ *                may be NULL when prec = LLS_PREC_FP32.
+ *   R   [out]    b x b upper triangular FP32 (ldr >= b) with a nonnegative diagonal; the
+ *                strict lower triangle is written with zeros. A = Q R.
+ *   ws           lls_panel_qr_workspace_size(m, b) bytes, 256-B aligned (tree buffers,
+ *                arrival counters, device error word). Zero-fill it once before its first
+ *                use: every call leaves the counters at zero again, so back-to-back calls on
+ *                one stream reuse it without clearing (calls that overlap on the GPU race).
+ * Asynchronous on `stream`; no host synchronisation. The one-launch path waits (bounded,
+ * about 2 s) for co-resident CTAs; if such a wait gives up, Q and R are undefined and the
+ * error word stays set, so the workspace must be zero-filled again before the next call.
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+size_t lls_panel_qr_workspace_size(int m, int b);
+int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr,
+                 void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * lls_lowp_projection_noalloc: lls_lowp_projection without a workspace argument. The paper

@@ -29,7 +29,7 @@ static void resolve(const lls_options* o, lls_options& r) {
     lls_default_options(&r);
     if (!o) return;
     r = *o;
-    if (r.panel_width <= 0) r.panel_width = 32;
+    if (r.panel_width <= 0) r.panel_width = 16;
     if (r.leaf_rows <= 0) r.leaf_rows = 256;
     if (r.max_iter <= 0) r.max_iter = 200;
     if (r.tol <= 0.0) r.tol = r.target == LLS_TARGET_FP32 ? 1e-6 : 1e-12;
@@ -166,7 +166,7 @@ void lls_default_options(lls_options* o) {
     o->target = LLS_TARGET_FP64;
     o->tol = 0.0;
     o->max_iter = 200;
-    o->panel_width = 32;
+    o->panel_width = 16;
     o->krylov = LLS_KRYLOV_CGLS;
     o->leaf_rows = 256;
 }
@@ -278,6 +278,46 @@ int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, c
     uc.Q1l = Q1l; uc.ldh = ldh; uc.R12l = R12l; uc.ldrl = ldrl; uc.f = f; uc.A2 = A2; uc.ldw = lda;
     uc.m = m; uc.w1 = w1; uc.w2 = w2; uc.lowp = lowp_code(prec);
     return gemm_update(uc, stream);
+}
+
+struct PanelWs {
+    float* rbuf; float* qbuf; unsigned* cnt; size_t cnt_words; int* err;
+};
+
+static void panel_layout(WsArena& ar, int m, PanelWs& w) {
+    size_t rb, qb, cw;
+    panel_scratch_sizes(m, rb, qb, cw);
+    w.rbuf = ar.take<float>(rb);
+    w.qbuf = ar.take<float>(qb);
+    w.cnt = ar.take<unsigned>(cw);
+    w.cnt_words = cw;
+    w.err = ar.take<int>(16);
+}
+
+size_t lls_panel_qr_workspace_size(int m, int b) {
+    if (m < 1 || b < 1 || b > 32 || m < b) return 0;
+    WsArena ar(nullptr, ~(size_t)0);
+    PanelWs w;
+    panel_layout(ar, m, w);
+    return ar.off;
+}
+
+int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr, void* ws,
+                 size_t ws_bytes, cudaStream_t stream) {
+    if (m < 1 || b < 1 || b > 32 || m < b || ldw < m || ldr < b || !W || !R || !ws) return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP16 && prec != LLS_PREC_BF16 && prec != LLS_PREC_FP32) return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP32 && (!Wh || ldh < m)) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, ws_bytes);
+    PanelWs w;
+    panel_layout(ar, m, w);
+    if (!ar.ok) return LLS_ERR_WORKSPACE;
+    // counters and error word are zero on entry (caller's zero fill, then self-resetting)
+    PanelCall p;
+    p.W = W; p.ldw = ldw; p.Wh = prec == LLS_PREC_FP32 ? nullptr : Wh; p.ldh = ldh; p.R = R; p.ldr = ldr;
+    p.m = m; p.c0 = 0; p.b = b; p.lowp = lowp_code(prec);
+    p.rbuf = w.rbuf; p.qbuf = w.qbuf; p.cnt = w.cnt; p.err = w.err;
+    return panel_qr(p, stream);
 }
 
 static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w, float*& R,

@@ -180,6 +180,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
+    if (EPI == TC_EPI_UPDATE && nk > 0) {
+        // Pull this CTA's FP32 tile of A2 into L2 while the main loop runs, so that the
+        // epilogue's read-modify-write finds it there: one 128-byte line per 32 rows of a column.
+        for (int l = threadIdx.x; l < 4 * BN; l += kTcThreads) {
+            const int j = n0 + (l >> 2), i = m0 + (l & 3) * 32;
+            if (j < a.N && i < a.M)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.out + (size_t)i + (size_t)j * a.ldo));
+        }
+    }
+
     if (nk > 0) {
         if (warp == 0 && lane == 0) {
             // ---- TMA producer ----
@@ -224,10 +234,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const bool ready = mbar_wait(accb, 0, a.err);
         __syncwarp();
         tc_fence_after();
-        if (ready) {
+        if (ready && EPI == TC_EPI_PARTIAL) {
             const int i = m0 + warp * 32 + lane;
-            float fs[BN / 16];
-            (void)fs;
 #pragma unroll 1
             for (int c = 0; c < BN / 16; ++c) {
                 float v[16];
@@ -236,15 +244,44 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                     for (int r = 0; r < 16; ++r) {
                         const int j = n0 + c * 16 + r;
-                        if (j < a.N) {
-                            if (EPI == TC_EPI_PARTIAL) {
-                                a.out[(size_t)blockIdx.z * a.M * a.N + (size_t)i + (size_t)j * a.M] = v[r];
-                            } else {
-                                const size_t idx = (size_t)i + (size_t)j * a.ldo;
-                                a.out[idx] = a.out[idx] - v[r] * pow2f(-a.fexp[j]);
-                            }
-                        }
+                        if (j < a.N) a.out[(size_t)blockIdx.z * a.M * a.N + (size_t)i + (size_t)j * a.M] = v[r];
                     }
+                }
+            }
+        } else if (ready) {
+            // A2 -= acc * 2^-f, 16 columns at a time. The 16 old values (and scales) of the
+            // next chunk are loaded before the current chunk is stored, so each chunk costs
+            // one overlapped round trip instead of one per element.
+            const int i = m0 + warp * 32 + lane;
+            const bool row_ok = i < a.M;
+            float* orow = a.out + (size_t)(row_ok ? i : 0);
+            float nxt[16], nsc[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int j = n0 + r;
+                const bool in = row_ok && j < a.N;
+                nxt[r] = in ? orow[(size_t)j * a.ldo] : 0.f;
+                nsc[r] = in ? pow2f(-__ldg(a.fexp + j)) : 0.f;
+            }
+#pragma unroll 1
+            for (int c = 0; c < BN / 16; ++c) {
+                float cur[16], sc[16], v[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) { cur[r] = nxt[r]; sc[r] = nsc[r]; }
+                if (c + 1 < BN / 16) {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const int j = n0 + (c + 1) * 16 + r;
+                        const bool in = row_ok && j < a.N;
+                        nxt[r] = in ? orow[(size_t)j * a.ldo] : 0.f;
+                        nsc[r] = in ? pow2f(-__ldg(a.fexp + j)) : 0.f;
+                    }
+                }
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int j = n0 + c * 16 + r;
+                    if (row_ok && j < a.N) orow[(size_t)j * a.ldo] = fmaf(-v[r], sc[r], cur[r]);
                 }
             }
         } else {

@@ -25,7 +25,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update",
            "lls_backward_workspace_size", "lls_backward",
            "lls_solve_batched_workspace_size", "lls_solve_batched",
-           "lls_lowp_projection_noalloc")
+           "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr")
 
 
 class lls_options(C.Structure):
@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH):
     lib.lls_lowp_projection.restype = i
     lib.lls_lowp_projection_noalloc.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp]
     lib.lls_lowp_projection_noalloc.restype = i
+    lib.lls_panel_qr_workspace_size.argtypes = [i, i]
+    lib.lls_panel_qr_workspace_size.restype = sz
+    lib.lls_panel_qr.argtypes = [i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]
+    lib.lls_panel_qr.restype = i
     lib.lls_lowp_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, vp, i, vp, sz, vp]
     lib.lls_lowp_update.restype = i
     ip = C.POINTER(C.c_int)
@@ -101,7 +105,14 @@ def load(path: str = LIB_PATH):
     return lib
 
 
-def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=32,
+def default_options() -> lls_options:
+    """The library's defaults (lls_default_options)."""
+    o = lls_options()
+    load().lls_default_options(C.byref(o))
+    return o
+
+
+def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
                  krylov="cgls", leaf_rows=256) -> lls_options:
     o = lls_options()
     load().lls_default_options(C.byref(o))
@@ -158,6 +169,14 @@ def lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl,
                         stream) -> int:
     return load().lls_lowp_projection(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f,
                                       ws, ws_bytes, stream)
+
+
+def lls_panel_qr_workspace_size(m, b) -> int:
+    return load().lls_panel_qr_workspace_size(m, b)
+
+
+def lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream) -> int:
+    return load().lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream)
 
 
 def lls_lowp_projection_noalloc(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f, stream) -> int:
@@ -239,7 +258,7 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def qr(A, prec="fp16", panel_width=32, want_q=True, ws=None, stream=None):
+def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None):
     """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False."""
     torch = _torch()
     _check_colmajor(A)
@@ -258,7 +277,7 @@ def qr(A, prec="fp16", panel_width=32, want_q=True, ws=None, stream=None):
     return Q, R
 
 
-def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=32,
+def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
           krylov="cgls", want_r=False, ws=None, stream=None, check=True):
     """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
 

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_defaults_and_status_strings(lib):
     o = lls.lls_default_options()
-    assert (o.gemm_prec, o.target, o.max_iter, o.panel_width, o.krylov) == (0, 1, 200, 32, 0)
+    assert (o.gemm_prec, o.target, o.max_iter, o.panel_width, o.krylov) == (0, 1, 200, 16, 0)
     assert lls.lls_status_string(0) == "ok"
     assert "singular" in lls.lls_status_string(-2)
 
