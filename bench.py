@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--prec", default="fp16")
     ap.add_argument("--target", default="fp64")
+    ap.add_argument("--krylov", default="cgls", choices=["cgls", "lsqr"])
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=1024)
@@ -158,7 +159,8 @@ def run_reference(args):
 
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
 # it stands, from the captures summarised under profiles/; None once a kernel changes.
-NCU_TRAFFIC = {"panel": None, "tc_projection": None, "tc_update": None, "cgls": None}
+NCU_TRAFFIC = {"panel": 2.191616e6, "tc_projection": 0.362066e9 + 40.856064e6,
+               "tc_update": 1.496239e9 + 243.421952e6, "cgls": 24.633982e9 + 205.846784e6}
 
 
 def split_point(w, pw):
@@ -284,7 +286,7 @@ def main():
     dev = torch.device("cuda", local)
     m, n = args.m, args.n
     A, b = make_inputs(args, m, n, rank, dev)
-    o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw)
+    o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw, krylov=args.krylov)
     pw = args.pw if args.pw > 0 else lls.default_options().panel_width
     nb = lls.lls_solve_workspace_size(m, n, o)
     wsbuf = lls.workspace(nb, dev)
@@ -386,7 +388,7 @@ def main():
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))   # FP16 and BF16 have the same dense rate
     achieved = kry_bytes / (kry_ms * 1e-3) / 1e9
     kernels = kernel_rooflines(m, n, pw, args.prec, stream, dev, hbm_peak, tc_peak)
-    kernels["cgls"] = {"kernel": "cgls_kernel (persistent CGLS iteration, whole Krylov phase)", "bound": "hbm",
+    kernels["cgls"] = {"kernel": f"{args.krylov}_kernel (persistent {args.krylov.upper()} iteration, whole Krylov phase)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                        "traffic": NCU_TRAFFIC["cgls"], "algorithmic_bytes_per_launch": kry_bytes}
     # the panel has the largest share of the solve in the ncu launch list
@@ -398,8 +400,9 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "fp16 products / f32 panel / double-float Krylov",
            "data": "synthetic",
            "config": {"workload": f"single LLS {m}x{n} FP32, {args.kind} spectrum kappa={args.kappa:g}, "
-                                  f"{args.prec.upper()} products, {args.target.upper()} target",
-                      "m": m, "n": n, "prec": args.prec, "target": args.target,
+                                  f"{args.prec.upper()} products, {args.krylov.upper()} to the "
+                                  f"{args.target.upper()} target",
+                      "m": m, "n": n, "prec": args.prec, "target": args.target, "krylov": args.krylov,
                       "panel_width": pw,
                       "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
                       "parallelism": f"replicas x{ws}"},

@@ -110,6 +110,9 @@ int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R
 
 /* ---------------------------------------------------------------------------
  * Least-squares solve (Alg. 5 with the QR above as right preconditioner).
+ * opts->krylov selects the iteration on the preconditioned operator A R^{-1}: CGLS
+ * (Alg. 5, default) or LSQR (Golub-Kahan bidiagonalization, Paige-Saunders; Sec. 5).
+ * Both stop on the same tests (lls_options.tol) and confirm them on a fresh residual.
  *
  *  A     [in]  m x n FP32, lda >= m; the problem is defined for these FP32 values.
  *  b     [in]  m FP64.

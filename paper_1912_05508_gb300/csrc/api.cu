@@ -380,7 +380,7 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     if (n < 1 || m < n || lda < m || !A || !b || !x || !ws) return LLS_ERR_ARG;
     if (R_out && ldr < n) return LLS_ERR_ARG;
     if (!valid_opts(o)) return LLS_ERR_ARG;
-    if (o.krylov != LLS_KRYLOV_CGLS) return LLS_ERR_UNSUPPORTED;
+    // CGLS and LSQR share the workspace layout and the stop tests
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
     WsArena ar(ws, ws_bytes);
     SolveCall c;

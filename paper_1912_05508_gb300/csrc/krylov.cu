@@ -51,7 +51,7 @@ struct KArgs {
     double* x;
     const float* M;
     const float* Mt;
-    double *r, *q, *t, *p, *s, *u, *qpart, *upart, *bpart;
+    double *r, *q, *t, *p, *s, *u, *d, *qpart, *upart, *bpart;
     unsigned* bar;
     int* err;
     double* info;
@@ -568,6 +568,202 @@ cgls_kernel(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// LSQR (Paige and Saunders; Sec. 5 names it as the stable equivalent of CGLS) on the same
+// right-preconditioned operator B = A M, M = R^{-1}, with x = M y kept directly.
+// Golub-Kahan bidiagonalization started from the current residual r = b - A x:
+//   beta u = r,  alpha v = M^T A^T u,  t = M v,  d = t,  phibar = beta,  rhobar = alpha
+//   loop: w = A t - alpha u;  beta = ||w||;  u = w / beta
+//         s = M^T A^T u - beta v;  alpha = ||s||;  v = s / alpha
+//         rho = hypot(rhobar, beta);  c = rhobar / rho;  sn = beta / rho
+//         theta = sn alpha;  rhobar = -c alpha;  phi = c phibar;  phibar = sn phibar
+//         x += (phi / rho) d;  t = M v;  d = t - (theta / rho) d
+// ||B^T r|| = phibar alpha |c| is the same quantity as CGLS's ||s||, so the stop tests and
+// the fresh-residual confirmation (with restarts from the current x) are those of CGLS.
+// Per iteration: one pass over A for A t, one for A^T u, one product each with M and M^T.
+// Vector roles: u -> r (m), w -> q (m), v -> p, A^T u -> u, s -> s, t -> t, d -> d (n).
+__global__ void __launch_bounds__(kKThreads, 2)
+lsqr_kernel(KArgs a) {
+    const int gtid = blockIdx.x * kKThreads + threadIdx.x, gthreads = gridDim.x * kKThreads;
+    const double anorm = sqrt(*a.anorm2);
+    const double mnorm = sqrt(*a.mnorm2);
+    int iters = 0, status = 1, apasses = 0, mpasses = 0;
+    double eta = 0.0, fwd = 0.0, rn2 = 0.0, un2 = 0.0, xn2 = 0.0;
+    bool xzero = a.x_zero != 0;
+
+    for (int restart = 0; restart <= kMaxRestarts; ++restart) {
+        // ---- r = b - A x, beta = ||r|| ----
+        if (xzero) {
+            double sq = 0.0;
+            for (int i = gtid; i < a.m; i += gthreads) { double bi = a.b[i]; a.r[i] = bi; sq += bi * bi; }
+            block_partial(sq, a.bpart, 0);
+            for (int j = gtid; j < a.n; j += gthreads) a.x[j] = 0.0;
+        } else {
+            stage_vec(a.x, a.n);
+            a_times_partials(a);
+            ++apasses;
+            KB_SYNC();
+            double sq = 0.0;
+            for (int i = gtid; i < a.m; i += gthreads) {
+                double ax = 0.0;
+                for (int cc = 0; cc < a.nck; ++cc) ax += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                double ri = a.b[i] - ax;
+                a.r[i] = ri;
+                sq += ri * ri;
+            }
+            block_partial(sq, a.bpart, 0);
+        }
+        xzero = false;
+        KB_SYNC();
+        rn2 = grid_total(a.bpart, 0);
+        double beta = sqrt(rn2);
+        // ---- A^T r (scaled to A^T u below), ||x||^2 ----
+        at_times_partials(a, a.r);
+        ++apasses;
+        {
+            double xs = 0.0;
+            for (int j = gtid; j < a.n; j += gthreads) { double xv = __ldcg(a.x + j); xs += xv * xv; }
+            block_partial(xs, a.bpart, 3);
+        }
+        KB_SYNC();
+        xn2 = grid_total(a.bpart, 3);
+        {
+            const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+            double sq = 0.0;
+            for (int j = gtid; j < a.n; j += gthreads) {
+                double v = 0.0;
+                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                sq += v * v;
+                a.u[j] = v * ib;
+            }
+            block_partial(sq, a.bpart, 1);
+            for (int i = gtid; i < a.m; i += gthreads) a.r[i] *= ib;
+        }
+        KB_SYNC();
+        un2 = grid_total(a.bpart, 1);
+        // ---- alpha v = M^T A^T u ----
+        stage_vec(a.u, a.n);
+        block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
+        ++mpasses;
+        KB_SYNC();
+        double alpha = sqrt(grid_total(a.bpart, 2));
+        {
+            const double xn = sqrt(xn2), sn = alpha * beta;
+            eta = xn > 0.0 ? sn / (anorm * xn) : (sn == 0.0 ? 0.0 : INFINITY);
+            fwd = xn > 0.0 ? mnorm * sn / xn : (sn == 0.0 ? 0.0 : INFINITY);
+        }
+        const double crit = a.target == LLS_TARGET_FP64 ? eta : fwd;
+        if (crit <= a.tol) { status = 0; break; }
+        if (iters >= a.max_iter || restart == kMaxRestarts || !(alpha > 0.0)) { status = 1; break; }
+        {
+            const double ia = 1.0 / alpha;
+            for (int j = gtid; j < a.n; j += gthreads) a.p[j] = __ldcg(a.s + j) * ia;
+        }
+        KB_SYNC();
+        stage_vec(a.p, a.n);
+        tri_gemv(a.Mt, a.n, false, a.t);
+        ++mpasses;
+        KB_SYNC();
+        for (int j = gtid; j < a.n; j += gthreads) a.d[j] = __ldcg(a.t + j);
+        double phibar = beta, rhobar = alpha;
+
+        // ---- iterate ----
+        while (iters < a.max_iter) {
+            // w = A t - alpha u, beta = ||w||
+            stage_vec(a.t, a.n);
+            a_times_partials(a);
+            ++apasses;
+            KB_SYNC();
+            {
+                double sq = 0.0;
+                for (int i = gtid; i < a.m; i += gthreads) {
+                    double v = 0.0;
+                    for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                    v -= alpha * a.r[i];
+                    a.q[i] = v;
+                    sq += v * v;
+                }
+                block_partial(sq, a.bpart, 0);
+            }
+            KB_SYNC();
+            beta = sqrt(grid_total(a.bpart, 0));
+            const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+            // u = w / beta;  A^T u = (A^T w) / beta
+            at_times_partials(a, a.q);
+            ++apasses;
+            for (int i = gtid; i < a.m; i += gthreads) a.r[i] = __ldcg(a.q + i) * ib;
+            KB_SYNC();
+            for (int j = gtid; j < a.n; j += gthreads) {
+                double v = 0.0;
+                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                a.u[j] = v * ib;
+            }
+            KB_SYNC();
+            // s = M^T A^T u - beta v, alpha = ||s||
+            stage_vec(a.u, a.n);
+            tri_gemv(a.M, a.n, true, a.s);
+            ++mpasses;
+            KB_SYNC();
+            {
+                double sq = 0.0;
+                for (int j = gtid; j < a.n; j += gthreads) {
+                    const double v = __ldcg(a.s + j) - beta * a.p[j];
+                    a.s[j] = v;
+                    sq += v * v;
+                }
+                block_partial(sq, a.bpart, 1);
+            }
+            KB_SYNC();
+            alpha = sqrt(grid_total(a.bpart, 1));
+            ++iters;
+            // plane rotation of the bidiagonal (every CTA computes the same scalars)
+            const double rho = hypot(rhobar, beta);
+            const double c = rho > 0.0 ? rhobar / rho : 1.0, sn = rho > 0.0 ? beta / rho : 0.0;
+            const double theta = sn * alpha;
+            rhobar = -c * alpha;
+            const double phi = c * phibar;
+            phibar = sn * phibar;
+            const double step = rho > 0.0 ? phi / rho : 0.0, dcoef = rho > 0.0 ? theta / rho : 0.0;
+            const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+            {
+                double xs = 0.0;
+                for (int j = gtid; j < a.n; j += gthreads) {
+                    const double xv = a.x[j] + step * a.d[j];
+                    a.x[j] = xv;
+                    xs += xv * xv;
+                    a.p[j] = __ldcg(a.s + j) * ia;
+                }
+                block_partial(xs, a.bpart, 3);
+            }
+            KB_SYNC();
+            const double xn = sqrt(grid_total(a.bpart, 3));
+            const double atr = phibar * alpha * fabs(c);
+            const double e1 = xn > 0.0 ? atr / (anorm * xn) : INFINITY;
+            const double f1 = xn > 0.0 ? mnorm * atr / xn : INFINITY;
+            if ((a.target == LLS_TARGET_FP64 ? e1 : f1) <= a.tol || !(alpha > 0.0) || !(beta > 0.0)) break;
+            // t = M v, d = t - (theta / rho) d
+            stage_vec(a.p, a.n);
+            tri_gemv(a.Mt, a.n, false, a.t);
+            ++mpasses;
+            KB_SYNC();
+            for (int j = gtid; j < a.n; j += gthreads) a.d[j] = __ldcg(a.t + j) - dcoef * a.d[j];
+        }
+        // loop back: the top of the restart loop recomputes b - A x and re-tests
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.info[0] = iters;
+        a.info[1] = eta;
+        a.info[2] = fwd;
+        a.info[3] = sqrt(rn2);
+        a.info[4] = sqrt(un2);
+        a.info[5] = anorm;
+        a.info[6] = sqrt(xn2);
+        a.info[7] = status;
+        a.info[10] = apasses;
+        a.info[11] = mpasses;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Adjoint of the least-squares solution map (for the differentiable solve).
 //
 // For a loss L(x*) with g = dL/dx, z = (A^T A)^{-1} g; then dL/db = A z and
@@ -708,7 +904,7 @@ adjoint_kernel(AdjArgs aa) {
 // ---------------------------------------------------------------------------------------
 struct KLayout {
     int nrt, nck, nrc, ncg;
-    size_t off_r, off_q, off_t, off_p, off_s, off_u, off_qpart, off_upart, off_v1, off_v2, off_bpart,
+    size_t off_r, off_q, off_t, off_p, off_s, off_u, off_d, off_qpart, off_upart, off_v1, off_v2, off_bpart,
         off_bar, total;
 };
 
@@ -726,6 +922,7 @@ static KLayout k_layout(int m, int n, int grid) {
     L.off_p = take(8ull * n);
     L.off_s = take(8ull * n);
     L.off_u = take(8ull * n);
+    L.off_d = take(8ull * n);
     L.off_qpart = take(8ull * m * L.nck);
     L.off_upart = take(8ull * n * L.nrc);
     L.off_v1 = take(8ull * n * grid);
@@ -764,8 +961,9 @@ static int fused_nc(int n) {
 }
 
 template <int NC>
-static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, int sms, cudaStream_t st) {
-    auto kern = cgls_kernel<NC>;
+static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, int sms, cudaStream_t st,
+                       bool lsqr = false) {
+    void (*kern)(KArgs) = lsqr ? lsqr_kernel : cgls_kernel<NC>;
     LLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKThreads, smem));
@@ -785,7 +983,7 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     if (L.total > c.scratch_bytes) return LLS_ERR_WORKSPACE;
     a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
     a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);
-    a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u);
+    a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u); a.d = (double*)(base + L.off_d);
     a.qpart = (double*)(base + L.off_qpart); a.upart = (double*)(base + L.off_upart);
     a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
     a.bpart = (double*)(base + L.off_bpart);
@@ -794,16 +992,17 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kKThreads), args, smem, st));
-    note_launch("cgls", st);
+    note_launch(lsqr ? "lsqr" : "cgls", st);
     return LLS_OK;
 }
 
 int krylov_solve(const KrylovCall& c, cudaStream_t st) {
-    if (c.method != LLS_KRYLOV_CGLS) return LLS_ERR_UNSUPPORTED;
+    if (c.method != LLS_KRYLOV_CGLS && c.method != LLS_KRYLOV_LSQR) return LLS_ERR_UNSUPPORTED;
+    const bool lsqr = c.method == LLS_KRYLOV_LSQR;
     const int sms = sm_count();
     if (sms <= 0) return LLS_ERR_CUDA;
     static const bool want_fused = getenv("LLS_KRYLOV_FUSED") != nullptr;
-    const int nc = want_fused ? fused_nc(c.n) : 0;
+    const int nc = (want_fused && !lsqr) ? fused_nc(c.n) : 0;
     KArgs a;
     a.m = c.m; a.n = c.n; a.lda = c.lda; a.A = c.A; a.b = c.b; a.x = c.x;
     a.M = c.Minv; a.Mt = c.Mt;
@@ -829,7 +1028,7 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;
     if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
-    return launch_cgls<0>(a, c, base, smem, sms, st);
+    return launch_cgls<0>(a, c, base, smem, sms, st, lsqr);
 }
 
 int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
@@ -860,7 +1059,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     char* base = (char*)c.scratch;
     a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
     a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);
-    a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u);
+    a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u); a.d = (double*)(base + L.off_d);
     a.qpart = (double*)(base + L.off_qpart); a.upart = (double*)(base + L.off_upart);
     a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
     a.bpart = (double*)(base + L.off_bpart);

@@ -131,3 +131,47 @@ def test_default_engine_two_passes_per_iteration():
     x, info = run(p, prec="fp16", target="fp64")
     # init (A^T b) + two passes per iteration + final check (A x, A^T r)
     assert info["a_passes"] == 2 * info["iters"] + 3
+
+
+# ---- LSQR (opts.krylov = LLS_KRYLOV_LSQR) on the same preconditioned operator ----
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("kind", ["geometric", "arithmetic", "cluster"])
+def test_lsqr_fp64_target(prec, kind):
+    p = synth.svd_lls(1024, 128, kind, 1e3, seed=5)
+    x, info = run(p, prec=prec, target="fp64", krylov="lsqr")
+    xs = direct.lls(p.A, p.b)
+    assert info["status"] == 0, info
+    assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
+    assert metrics.forward_error(x, xs) <= 10 * p.kappa * 1e-12
+
+
+def test_lsqr_fp32_target_config_small():
+    # the small configuration: 1024 x 128, geometric spectrum 1 .. 1e-3, FP16 products, LSQR
+    p = synth.svd_lls(1024, 128, "geometric", 1e3, seed=1)
+    x, info = run(p, prec="fp16", target="fp32", krylov="lsqr")
+    xs = direct.lls(p.A, p.b)
+    assert info["status"] == 0, info
+    assert metrics.forward_error(x, xs) <= 1e-5
+
+
+@pytest.mark.parametrize("m,n", [(3000, 200), (700, 45), (96, 96), (40, 1), (5000, 1100)])
+def test_lsqr_ragged_shapes_match_cgls(m, n):
+    p = synth.svd_lls(m, n, "geometric", 1e2, seed=m + 7 * n, noise=1e-3 if m > n else 0.0)
+    xl, il = run(p, prec="fp16", target="fp64", krylov="lsqr")
+    xc, ic = run(p, prec="fp16", target="fp64", krylov="cgls")
+    xs = direct.lls(p.A, p.b)
+    assert il["status"] == 0 and ic["status"] == 0, (il, ic)
+    assert metrics.forward_error(xl, xs) <= 10 * p.kappa * 1e-12
+    # in exact arithmetic LSQR and CGLS generate the same iterates
+    assert abs(il["iters"] - ic["iters"]) <= 2 + ic["iters"] // 5
+
+
+def test_lsqr_counts_two_passes_per_iteration():
+    p = synth.svd_lls(4096, 256, "geometric", 1e3, seed=9)
+    x, info = run(p, prec="fp16", target="fp64", krylov="lsqr")
+    assert info["status"] == 0, info
+    # two passes over A per iteration, plus A^T r at the start and b - A x plus A^T r at the
+    # confirmation of each (re)start
+    assert info["a_passes"] >= 2 * info["iters"] + 1
+    assert info["a_passes"] <= 2 * info["iters"] + 3 * 4
