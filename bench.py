@@ -159,7 +159,7 @@ def run_reference(args):
 
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
 # it stands, from the captures summarised under profiles/; None once a kernel changes.
-NCU_TRAFFIC = {"panel": 2.191616e6, "tc_projection": 0.362066e9 + 40.856064e6,
+NCU_TRAFFIC = {"panel": None, "tc_projection": 0.362066e9 + 40.856064e6,
                "tc_update": 1.496239e9 + 243.421952e6, "cgls": 24.633982e9 + 205.846784e6}
 
 
@@ -167,19 +167,27 @@ def split_point(w, pw):
     return pw * (-(-w // (2 * pw)))
 
 
-def time_launches(launch, count, stream):
-    """Mean device time (ms) of `count` back-to-back calls, CUDA events on the launching stream."""
+def time_launches(launch, count, stream, reps=3):
+    """Mean device time (ms) per call: `count` calls captured in one CUDA graph (as inside the
+    solve, where the library replays its own graph), replayed `reps` times between CUDA events
+    on the launching stream, so host submission cost is not in the number."""
     import torch
     for i in range(3):
         launch(i)
     torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        for i in range(count):
+            launch(i)
+    g.replay()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(count):
-        launch(i)
+    for _ in range(reps):
+        g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / count
+    return e0.elapsed_time(e1) / (reps * count)
 
 
 def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
@@ -205,7 +213,7 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
         st = lls.lls_panel_qr(m, pw, pcode, W[:, k * pw:].data_ptr(), m, Wh[:, k * pw:].data_ptr(), m,
                               R.data_ptr(), pw, pws.data_ptr(), pws.numel(), sh)
         assert st == 0, st
-    ms = time_launches(panel, 200, stream)
+    ms = time_launches(panel, 100, stream)
     by = 10.0 * m * pw
     out["panel"] = {"kernel": f"panel_coop_kernel (CAQR panel {m}x{pw}, CGS2 leaves)", "bound": "hbm",
                     "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",

@@ -54,7 +54,7 @@ struct BArgs {
 };
 
 struct BSmem {
-    float red[2 * kPanelWarps * 32];
+    float red[kRedFloats];
     float Rs[32 * 33];
     float Rstk[kBMaxBlocks * 16 * 16];
     float Qt[kBMaxBlocks * 16 * 16];

@@ -211,7 +211,7 @@ __device__ void reconstruct(const PanelArgs& a, int leaf, float* T, float* U) {
 template <int B>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_leaf_tree_kernel(PanelArgs a) {
-    __shared__ float red[2 * kPanelWarps * 32];
+    __shared__ float red[kRedFloats];
     __shared__ float Rs[32 * 33];
     __shared__ int s_last;
     for (int i = threadIdx.x; i < 32 * 33; i += kPanelThreads) Rs[i] = 0.f;
@@ -244,7 +244,7 @@ panel_reconstruct_kernel(PanelArgs a) {
 template <int B>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_coop_kernel(PanelArgs a) {
-    __shared__ float red[2 * kPanelWarps * 32];
+    __shared__ float red[kRedFloats];
     __shared__ float Rs[32 * 33];
     __shared__ float U[32 * 33];
     __shared__ int s_last, s_ok;
