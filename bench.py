@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--krylov", default="cgls", choices=["cgls", "lsqr"])
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-householder", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=1024)
     return ap.parse_args()
 
@@ -259,6 +260,38 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
     return out
 
 
+def householder_baseline(A, b, x_ref, stream, dev, reps=2):
+    """The plain Householder solve (Alg. 1) in FP64 and FP32 on the same GPU and inputs:
+    device time per solve (CUDA events, after one warm-up) and its distance from our x."""
+    import torch
+    from paper_1912_05508_gb300 import lls
+    m, n = A.shape
+    out = {}
+    for prec in ("fp64", "fp32"):
+        nb = lls.lls_householder_workspace_size(m, n, lls.PREC[prec])
+        ws = lls.workspace(nb, dev)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+
+        def run():
+            st = lls.lls_householder_solve(m, n, lls.PREC[prec], A.data_ptr(), A.stride(1), b.data_ptr(),
+                                           x.data_ptr(), ws.data_ptr(), ws.numel(), stream.cuda_stream)
+            assert st == 0, st
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        rel = float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))
+        out[prec] = {"ms": ms, "rel_diff_vs_mixed_precision_x": rel,
+                     "qr_tflops_equiv": qr_flops(m, n) / (ms * 1e-3) / 1e12}
+        del ws
+    return out
+
+
 def make_inputs(args, m, n, rank, dev):
     """Generate the problem on the device; keep a host copy in /tmp so a rerun of the same
     command (e.g. under a profiler, where torch's linear-algebra plugin may not load) reuses it."""
@@ -381,6 +414,9 @@ def main():
         if it > 0:
             e2e_ms.append(s0.elapsed_time(s1))
 
+    x_ref = x.clone()
+    hh = householder_baseline(A, b, x_ref, stream, dev) if not args.no_householder else None
+
     last = infos[-1]
     kry_ms = statistics.mean(i["krylov_ms"] for i in infos)
     a_passes = statistics.mean(i["a_passes"] for i in infos)
@@ -421,6 +457,8 @@ def main():
            "kernels": kernels,
            "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms",
                    "h2d_bytes_per_step": m * n * 4 + m * 8, "d2h_bytes_per_step": n * 8},
+           "householder": hh,
+           "speedup_vs_householder_fp64": (hh["fp64"]["ms"] / ms) if hh else None,
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
            "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

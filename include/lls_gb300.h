@@ -45,8 +45,9 @@ typedef enum {
 
 /* Precision of the two tensor-core products of each recursion step (Alg. 2 lines 8-9).
  * FP16 is the paper's choice (Sec. 2.1); BF16 trades resolution for range; FP32 runs the
- * products on the FP32 units (no rounding of the inputs), a reference mode. */
-typedef enum { LLS_PREC_FP16 = 0, LLS_PREC_BF16 = 1, LLS_PREC_FP32 = 3 } lls_gemm_prec;
+ * products on the FP32 units (no rounding of the inputs), a reference mode. FP64 is used
+ * only by the plain Householder solver below. */
+typedef enum { LLS_PREC_FP16 = 0, LLS_PREC_BF16 = 1, LLS_PREC_FP32 = 3, LLS_PREC_FP64 = 4 } lls_gemm_prec;
 
 /* Accuracy target of the Krylov refinement (Sec. 3.2.3). */
 typedef enum { LLS_TARGET_FP32 = 0, LLS_TARGET_FP64 = 1 } lls_target;
@@ -229,6 +230,22 @@ int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, c
 size_t lls_panel_qr_workspace_size(int m, int b);
 int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr,
                  void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Plain Householder least squares (Alg. 1, Sec. 3.2.2): the comparison solver the
+ * mixed-precision method is measured against, in FP64 (prec = LLS_PREC_FP64) or FP32
+ * (LLS_PREC_FP32) arithmetic throughout. Blocked Householder QR of [A, b] in compact-WY
+ * form (32-column panels factored by a cooperative kernel; the trailing update
+ * C -= V T^T V^T C and the final triangular solve through cuBLAS), then x = R^{-1} (Q^T b).
+ *  A [in] m x n FP32 (lda >= m), b [in] m FP64, x [out] n FP64 (rounded from the working
+ *  precision); ws: lls_householder_workspace_size(m, n, prec) bytes, 256-B aligned.
+ * Asynchronous on `stream`. No rank check: a zero pivot gives inf/nan in x.
+ * Errors: LLS_ERR_ARG (n < 1, m < n, lda < m, null pointers, prec), LLS_ERR_WORKSPACE,
+ *         LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+size_t lls_householder_workspace_size(int m, int n, int prec);
+int lls_householder_solve(int m, int n, int prec, const float* A, int lda, const double* b, double* x,
+                          void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * lls_lowp_projection_noalloc: lls_lowp_projection without a workspace argument. The paper

@@ -13,7 +13,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblls_gb300.so")
 
-PREC = {"fp16": 0, "bf16": 1, "fp32": 3}
+PREC = {"fp16": 0, "bf16": 1, "fp32": 3, "fp64": 4}
 TARGET = {"fp32": 0, "fp64": 1}
 KRYLOV = {"cgls": 0, "lsqr": 1}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
@@ -25,7 +25,8 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_lowp_projection_workspace_size", "lls_lowp_projection", "lls_lowp_update",
            "lls_backward_workspace_size", "lls_backward",
            "lls_solve_batched_workspace_size", "lls_solve_batched",
-           "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr")
+           "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr",
+           "lls_householder_workspace_size", "lls_householder_solve")
 
 
 class lls_options(C.Structure):
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
     lib.lls_panel_qr_workspace_size.restype = sz
     lib.lls_panel_qr.argtypes = [i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]
     lib.lls_panel_qr.restype = i
+    lib.lls_householder_workspace_size.argtypes = [i, i, i]
+    lib.lls_householder_workspace_size.restype = sz
+    lib.lls_householder_solve.argtypes = [i, i, i, vp, i, vp, vp, vp, sz, vp]
+    lib.lls_householder_solve.restype = i
     lib.lls_lowp_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, vp, i, vp, sz, vp]
     lib.lls_lowp_update.restype = i
     ip = C.POINTER(C.c_int)
@@ -177,6 +182,32 @@ def lls_panel_qr_workspace_size(m, b) -> int:
 
 def lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream) -> int:
     return load().lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream)
+
+
+def lls_householder_workspace_size(m, n, prec) -> int:
+    return load().lls_householder_workspace_size(m, n, prec)
+
+
+def lls_householder_solve(m, n, prec, A, lda, b, x, ws, ws_bytes, stream) -> int:
+    return load().lls_householder_solve(m, n, prec, A, lda, b, x, ws, ws_bytes, stream)
+
+
+def householder_solve(A, b, prec="fp64", stream=None):
+    """x of min ||A x - b|| by the plain Householder solver (FP64 or FP32 arithmetic)."""
+    torch = _torch()
+    _check_colmajor(A)
+    m, n = A.shape
+    nb = lls_householder_workspace_size(m, n, PREC[prec])
+    if nb == 0:
+        raise LLSError(-1, "lls_householder_workspace_size")
+    ws = workspace(nb, A.device)
+    x = torch.empty(n, dtype=torch.float64, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream(A.device).cuda_stream
+    st = lls_householder_solve(m, n, PREC[prec], A.data_ptr(), A.stride(1), b.data_ptr(), x.data_ptr(),
+                               ws.data_ptr(), ws.numel(), s)
+    if st < 0:
+        raise LLSError(st, "lls_householder_solve")
+    return x
 
 
 def lls_lowp_projection_noalloc(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f, stream) -> int:
