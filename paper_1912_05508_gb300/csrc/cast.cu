@@ -10,47 +10,95 @@
 
 namespace lls {
 
-constexpr int kCastThreads = 256;
+constexpr int kCastThreads = 512;
 
+template <typename TL> struct Pack4;
+template <> struct Pack4<__half> {
+    static __device__ __forceinline__ uint2 make(float4 v) {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
+    }
+};
+template <> struct Pack4<__nv_bfloat16> {
+    static __device__ __forceinline__ uint2 make(float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
+    }
+};
+
+// One CTA per column: the column maximum (FP16 only), then the scaled cast. With 16-byte
+// aligned columns both passes move 16-byte vectors, four independent loads per thread per
+// trip, so each CTA keeps enough loads in flight; the second pass re-reads the column from L2.
 template <typename TL>
 __global__ void __launch_bounds__(kCastThreads)
 scale_cast_kernel(const float* __restrict__ X, int ldx, int m, int c0, TL* __restrict__ Xh,
-                  int ldh, int want_scale, int* __restrict__ exps) {
+                  int ldh, int want_scale, int* __restrict__ exps, int vec) {
     const int j = c0 + blockIdx.x;
     const float* col = X + (size_t)j * ldx;
+    TL* out = Xh + (size_t)j * ldh;
     __shared__ float s_red[kCastThreads / 32];
     __shared__ int s_e;
+    const int t = threadIdx.x;
+    const int m4 = vec ? m / 4 : 0;                 // float4 part; the tail goes element-wise
+    const float4* col4 = reinterpret_cast<const float4*>(col);
     int e = 0;
     if (want_scale) {
         float mx = 0.f;
-        for (int i = threadIdx.x; i < m; i += kCastThreads) mx = fmaxf(mx, fabsf(col[i]));
+        int q = t;
+        for (; q + 3 * kCastThreads < m4; q += 4 * kCastThreads) {
+            const float4 a = __ldg(col4 + q), b = __ldg(col4 + q + kCastThreads);
+            const float4 c = __ldg(col4 + q + 2 * kCastThreads), d = __ldg(col4 + q + 3 * kCastThreads);
+            mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
+                                 fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w)))));
+            mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fmaxf(fabsf(c.z), fabsf(c.w))),
+                                 fmaxf(fmaxf(fabsf(d.x), fabsf(d.y)), fmaxf(fabsf(d.z), fabsf(d.w)))));
+        }
+        for (; q < m4; q += kCastThreads) {
+            const float4 a = __ldg(col4 + q);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+        }
+        for (int i = 4 * m4 + t; i < m; i += kCastThreads) mx = fmaxf(mx, fabsf(col[i]));
         mx = warp_max_f(mx);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+        if ((t & 31) == 0) s_red[t >> 5] = mx;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float t = 0.f;
-            for (int w = 0; w < kCastThreads / 32; ++w) t = fmaxf(t, s_red[w]);
-            s_e = fp16_scale_exponent(t);
+        if (t == 0) {
+            float tm = 0.f;
+            for (int w = 0; w < kCastThreads / 32; ++w) tm = fmaxf(tm, s_red[w]);
+            s_e = fp16_scale_exponent(tm);
             exps[blockIdx.x] = s_e;
         }
         __syncthreads();
         e = s_e;
-    } else if (threadIdx.x == 0) {
+    } else if (t == 0) {
         exps[blockIdx.x] = 0;
     }
     const float sc = pow2f(e);
-    TL* out = Xh + (size_t)j * ldh;
-    for (int i = threadIdx.x; i < m; i += kCastThreads)
-        out[i] = LowPrec<TL>::from_float(col[i] * sc);
+    uint2* out2 = reinterpret_cast<uint2*>(out);
+    int q = t;
+    for (; q + kCastThreads < m4; q += 2 * kCastThreads) {
+        float4 a = __ldg(col4 + q), b = __ldg(col4 + q + kCastThreads);
+        a.x *= sc; a.y *= sc; a.z *= sc; a.w *= sc;
+        b.x *= sc; b.y *= sc; b.z *= sc; b.w *= sc;
+        out2[q] = Pack4<TL>::make(a);
+        out2[q + kCastThreads] = Pack4<TL>::make(b);
+    }
+    for (; q < m4; q += kCastThreads) {
+        float4 a = __ldg(col4 + q);
+        a.x *= sc; a.y *= sc; a.z *= sc; a.w *= sc;
+        out2[q] = Pack4<TL>::make(a);
+    }
+    for (int i = 4 * m4 + t; i < m; i += kCastThreads) out[i] = LowPrec<TL>::from_float(col[i] * sc);
 }
 
 int scale_cast_columns(const float* X, int ldx, int m, int c0, int w, void* Xh, int ldh,
                        int lowp, int* exps, cudaStream_t st) {
     if (w <= 0) return LLS_OK;
+    // 16-byte vectors need 16-byte aligned columns in X and 8-byte aligned ones in Xh
+    const int vec = (((uintptr_t)X & 15) == 0) && (ldx % 4 == 0) && (((uintptr_t)Xh & 7) == 0) && (ldh % 4 == 0);
     if (lowp == 0)
-        scale_cast_kernel<__half><<<w, kCastThreads, 0, st>>>(X, ldx, m, c0, (__half*)Xh, ldh, 1, exps);
+        scale_cast_kernel<__half><<<w, kCastThreads, 0, st>>>(X, ldx, m, c0, (__half*)Xh, ldh, 1, exps, vec);
     else if (lowp == 1)
-        scale_cast_kernel<__nv_bfloat16><<<w, kCastThreads, 0, st>>>(X, ldx, m, c0, (__nv_bfloat16*)Xh, ldh, 0, exps);
+        scale_cast_kernel<__nv_bfloat16><<<w, kCastThreads, 0, st>>>(X, ldx, m, c0, (__nv_bfloat16*)Xh, ldh, 0, exps, vec);
     else
         return LLS_ERR_UNSUPPORTED;
     LLS_LAUNCH_CHECK("scale_cast", st);

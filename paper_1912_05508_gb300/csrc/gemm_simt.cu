@@ -108,32 +108,60 @@ __global__ void __launch_bounds__(256)
 proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
                    const int* __restrict__ e, float* __restrict__ R12, int ldr,
                    TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int want_scale) {
+    // Threads split as (row slot i0 < rp) x (split group g < G): group g sums splits
+    // g, g + G, ... (four independent loads per trip); the groups are then added in order
+    // g = 0, 1, ..., so the result does not depend on timing.
+    __shared__ float s_part[256];
+    __shared__ float s_red[8];
+    __shared__ int s_f;
     const int j = blockIdx.x;
     const float se = e ? pow2f(-e[j]) : 1.f;
     const size_t plane = (size_t)w1 * w2;
+    int rp = 1;
+    while (rp < w1 && rp < 256) rp <<= 1;
+    const int G = 256 / rp;
+    const int t = threadIdx.x, i0 = t % rp, g = t / rp;
     float mx = 0.f;
-    for (int i = threadIdx.x; i < w1; i += 256) {
+    for (int ib = 0; ib < w1; ib += rp) {
+        const int i = ib + i0;
         float s = 0.f;
-        for (int z = 0; z < splits; ++z) s += part[(size_t)z * plane + (size_t)i + (size_t)j * w1];
-        s *= se;
-        R12[(size_t)i + (size_t)j * ldr] = s;
-        mx = fmaxf(mx, fabsf(s));
+        if (i < w1) {
+            const float* p = part + (size_t)i + (size_t)j * w1;
+            int z = g;
+            for (; z + 3 * G < splits; z += 4 * G) {
+                const float a = __ldg(p + (size_t)z * plane), b = __ldg(p + (size_t)(z + G) * plane);
+                const float c = __ldg(p + (size_t)(z + 2 * G) * plane), d = __ldg(p + (size_t)(z + 3 * G) * plane);
+                s += a; s += b; s += c; s += d;
+            }
+            for (; z < splits; z += G) s += __ldg(p + (size_t)z * plane);
+        }
+        if (G > 1) {
+            __syncthreads();
+            s_part[t] = s;
+            __syncthreads();
+            if (g == 0) {
+                for (int q = 1; q < G; ++q) s += s_part[q * rp + i0];
+            }
+        }
+        if (g == 0 && i < w1) {
+            s *= se;
+            R12[(size_t)i + (size_t)j * ldr] = s;
+            mx = fmaxf(mx, fabsf(s));
+        }
     }
     if (!R12l) return;
-    __shared__ float s_red[8];
-    __shared__ int s_f;
     mx = warp_max_f(mx);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    if ((t & 31) == 0) s_red[t >> 5] = mx;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < 8; ++w) t = fmaxf(t, s_red[w]);
-        s_f = want_scale ? fp16_scale_exponent(t) : 0;
+    if (t == 0) {
+        float tm = 0.f;
+        for (int w = 0; w < 8; ++w) tm = fmaxf(tm, s_red[w]);
+        s_f = want_scale ? fp16_scale_exponent(tm) : 0;
         f[j] = s_f;
     }
     __syncthreads();
     const float sc = pow2f(s_f);
-    for (int i = threadIdx.x; i < w1; i += 256)
+    for (int i = t; i < w1; i += 256)
         R12l[(size_t)i + (size_t)j * ldrl] = LowPrec<TL>::from_float(R12[(size_t)i + (size_t)j * ldr] * sc);
 }
 
