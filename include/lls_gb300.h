@@ -44,10 +44,11 @@ typedef enum {
 } lls_status;
 
 /* Precision of the two tensor-core products of each recursion step (Alg. 2 lines 8-9).
- * FP16 is the paper's choice (Sec. 2.1); BF16 trades resolution for range; FP32 runs the
- * products on the FP32 units (no rounding of the inputs), a reference mode. FP64 is used
- * only by the plain Householder solver below. */
-typedef enum { LLS_PREC_FP16 = 0, LLS_PREC_BF16 = 1, LLS_PREC_FP32 = 3, LLS_PREC_FP64 = 4 } lls_gemm_prec;
+ * FP16 is the paper's choice (Sec. 2.1); BF16 trades resolution for range; FP8 is E4M3 with a
+ * power-of-two scale per column of both operands (max in [2^7, 2^8)), 3 significand bits
+ * (requires panel_width 16 or 32); FP32 runs the products on the FP32 units (no rounding of
+ * the inputs), a reference mode. FP64 is used only by the plain Householder solver below. */
+typedef enum { LLS_PREC_FP16 = 0, LLS_PREC_BF16 = 1, LLS_PREC_FP8 = 2, LLS_PREC_FP32 = 3, LLS_PREC_FP64 = 4 } lls_gemm_prec;
 
 /* Accuracy target of the Krylov refinement (Sec. 3.2.3). */
 typedef enum { LLS_TARGET_FP32 = 0, LLS_TARGET_FP64 = 1 } lls_target;

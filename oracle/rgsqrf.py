@@ -114,7 +114,10 @@ def rgsqrf(A: np.ndarray, panel_width: int = 32, prec: str = "fp16",
 
     R12 = (round(Q1)^T round(A2 * 2^e)) * 2^-e           (line 8, A2 columns scaled)
     A2  = A2 - (round(Q1) round(R12 * 2^f)) * 2^-f        (line 9, R12 columns scaled)
-    Q1 is not scaled (|q| <= 1). Returns (Q, R) in FP64.
+    Q1 is not scaled for FP16/BF16 (|q| <= 1). For 'fp8' (E4M3, whose normal range starts at
+    2^-6, above the ~m^-1/2 entries of Q) Q1's columns are scaled too, Q1l = round(Q1 2^s):
+    R12 = 2^-s (Q1l^T A2l) 2^-e, and the update uses Q1 R12 = Q1l (2^-s R12), so R12's rows
+    are divided by 2^s before its own column scaling. Returns (Q, R) in FP64.
     """
     W = np.array(A, dtype=np.float64, copy=True)
     m, n = W.shape
@@ -128,11 +131,14 @@ def rgsqrf(A: np.ndarray, panel_width: int = 32, prec: str = "fp16",
             return
         w1 = split_point(w, panel_width)
         rec(c0, w1)
-        Q1l = round_to(prec, W[:, c0:c0 + w1])
+        if prec == "fp8":
+            Q1l, s = scaled_round(W[:, c0:c0 + w1], prec)
+        else:
+            Q1l, s = round_to(prec, W[:, c0:c0 + w1]), np.zeros(w1, dtype=np.int64)
         A2l, e = scaled_round(W[:, c0 + w1:c0 + w], prec)
-        R12 = np.ldexp(Q1l.T @ A2l, -e[None, :])
+        R12 = np.ldexp(np.ldexp(Q1l.T @ A2l, -e[None, :]), -s[:, None])
         R[c0:c0 + w1, c0 + w1:c0 + w] = R12
-        R12l, f = scaled_round(R12, prec)
+        R12l, f = scaled_round(np.ldexp(R12, -s[:, None]), prec)
         W[:, c0 + w1:c0 + w] -= np.ldexp(Q1l @ R12l, -f[None, :])
         rec(c0 + w1, w - w1)
 

@@ -36,10 +36,13 @@ static void resolve(const lls_options* o, lls_options& r) {
 }
 
 static bool valid_opts(const lls_options& o) {
-    if (o.gemm_prec != LLS_PREC_FP16 && o.gemm_prec != LLS_PREC_BF16 && o.gemm_prec != LLS_PREC_FP32) return false;
+    if (o.gemm_prec != LLS_PREC_FP16 && o.gemm_prec != LLS_PREC_BF16 && o.gemm_prec != LLS_PREC_FP8 &&
+        o.gemm_prec != LLS_PREC_FP32)
+        return false;
     if (o.target != LLS_TARGET_FP32 && o.target != LLS_TARGET_FP64) return false;
     if (o.krylov != LLS_KRYLOV_CGLS && o.krylov != LLS_KRYLOV_LSQR) return false;
     if (o.panel_width < 1 || o.panel_width > 32) return false;
+    if (o.gemm_prec == LLS_PREC_FP8 && o.panel_width % 16 != 0) return false;   // 16-byte aligned FP8 slices
     if (o.leaf_rows != 256) return false;
     return true;
 }
@@ -59,13 +62,16 @@ struct QrWs {
     void* Wh; int ldh;
     float* part; size_t part_floats;
     void* R12l; int* eA; int* f;
+    uint8_t* QT; int ldq; int* sQ;   // FP8 only: row-major copy of Q and its column exponents
     float* rbuf; float* qbuf; unsigned* cnt; size_t cnt_words;
     int* err;
     double* dinfo;     // 16 doubles of device-side results
     double* red;       // 8192 doubles of reduction partials
 };
 
-static int lowp_code(int prec) { return prec == LLS_PREC_FP16 ? 0 : (prec == LLS_PREC_BF16 ? 1 : 3); }
+static int lowp_code(int prec) {
+    return prec == LLS_PREC_FP16 ? 0 : (prec == LLS_PREC_BF16 ? 1 : (prec == LLS_PREC_FP8 ? 2 : 3));
+}
 
 static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) {
     const bool lowp = o.gemm_prec != LLS_PREC_FP32;
@@ -80,6 +86,10 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.R12l = lowp ? (void*)ar.take<uint16_t>(r12) : nullptr;
     w.eA = ar.take<int>(n);
     w.f = ar.take<int>(n);
+    const bool f8 = o.gemm_prec == LLS_PREC_FP8;
+    w.ldq = (int)align_up((size_t)n, 16);
+    w.QT = f8 ? ar.take<uint8_t>((size_t)m * w.ldq) : nullptr;
+    w.sQ = f8 ? ar.take<int>(n) : nullptr;
     size_t rb, qb, cw;
     panel_scratch_sizes(m, rb, qb, cw);
     w.rbuf = ar.take<float>(rb);
@@ -102,9 +112,17 @@ static int qr_rec(QrCtx& c, int c0, int w) {
     if (w <= c.pw) {
         PanelCall p;
         p.W = c.w.W; p.ldw = c.w.ldw; p.Wh = c.w.Wh; p.ldh = c.w.ldh; p.R = c.R; p.ldr = c.ldr;
-        p.m = c.m; p.c0 = c0; p.b = w; p.lowp = c.lowp;
+        p.m = c.m; p.c0 = c0; p.b = w; p.lowp = c.lowp == 2 ? 3 : c.lowp;
         p.rbuf = c.w.rbuf; p.qbuf = c.w.qbuf; p.cnt = c.w.cnt; p.err = c.w.err;
-        return panel_qr(p, c.st);
+        LLS_TRY(panel_qr(p, c.st));
+        if (c.lowp == 2) {
+            // FP8: the copy of Q needs per-column scales (|q| ~ m^-1/2 is below E4M3's normal
+            // range), so it is cast after the panel, column-major for the projection and
+            // row-major for the update
+            LLS_TRY(scale_cast_columns(c.w.W, c.w.ldw, c.m, c0, w, c.w.Wh, c.w.ldh, 2, c.w.sQ + c0, c.st));
+            LLS_TRY(rowmajor_copy8(c.w.Wh, c.w.ldh, c.m, c0, w, c.w.QT, c.w.ldq, c.st));
+        }
+        return LLS_OK;
     }
     const int w1 = split_point(w, c.pw), w2 = w - w1;
     LLS_TRY(qr_rec(c, c0, w1));
@@ -115,19 +133,22 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         LLS_TRY(simt_projection_f32(Q1, A2, c.w.ldw, c.m, w1, w2, R12, c.ldr, c.w.part, c.st));
         LLS_TRY(simt_update_f32(Q1, c.w.ldw, R12, c.ldr, A2, c.m, w1, w2, c.st));
     } else {
-        const size_t esz = 2;
+        const size_t esz = c.lowp == 2 ? 1 : 2;
         const char* Whb = (const char*)c.w.Wh;
         LLS_TRY(scale_cast_columns(c.w.W, c.w.ldw, c.m, c0 + w1, w2, c.w.Wh, c.w.ldh, c.lowp, c.w.eA, c.st));
         ProjCall pc;
         pc.Q1l = Whb + esz * (size_t)c0 * c.w.ldh;
         pc.A2l = Whb + esz * (size_t)(c0 + w1) * c.w.ldh;
         pc.ldh = c.w.ldh; pc.m = c.m; pc.w1 = w1; pc.w2 = w2; pc.e = c.w.eA;
-        pc.R12 = R12; pc.ldr = c.ldr; pc.R12l = c.w.R12l; pc.ldrl = (int)align_up((size_t)w1, 8); pc.f = c.w.f;
+        pc.R12 = R12; pc.ldr = c.ldr; pc.R12l = c.w.R12l; pc.f = c.w.f;
+        pc.ldrl = (int)align_up((size_t)w1, c.lowp == 2 ? 16 : 8);      // 16-byte rows for TMA
+        pc.sq = c.lowp == 2 ? c.w.sQ + c0 : nullptr;
         pc.part = c.w.part; pc.part_floats = c.w.part_floats; pc.lowp = c.lowp; pc.err = c.w.err;
         LLS_TRY(gemm_projection(pc, c.st));
         UpdCall uc;
         uc.Q1l = pc.Q1l; uc.ldh = c.w.ldh; uc.R12l = c.w.R12l; uc.ldrl = pc.ldrl; uc.f = c.w.f; uc.err = c.w.err;
         uc.A2 = A2; uc.ldw = c.w.ldw; uc.m = c.m; uc.w1 = w1; uc.w2 = w2; uc.lowp = c.lowp;
+        if (c.lowp == 2) { uc.QT = c.w.QT + c0; uc.ldq = c.w.ldq; }
         LLS_TRY(gemm_update(uc, c.st));
     }
     return qr_rec(c, c0 + w1, w2);
@@ -543,7 +564,8 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
     resolve(opts, o);
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
-    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32) return LLS_ERR_UNSUPPORTED;
+    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8)
+        return LLS_ERR_UNSUPPORTED;
     if (!A || !lda || !b || !x || !ws) return LLS_ERR_ARG;
     for (int i = 0; i < batch; ++i) {
         if (!batched_supported(m[i], n[i])) return LLS_ERR_UNSUPPORTED;

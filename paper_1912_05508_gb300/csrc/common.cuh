@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -109,6 +110,10 @@ template <> struct LowPrec<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from_float(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 };
+template <> struct LowPrec<__nv_fp8_e4m3> {   // round to nearest even, saturating to +-448
+    static __device__ __forceinline__ __nv_fp8_e4m3 from_float(float x) { return __nv_fp8_e4m3(x); }
+    static __device__ __forceinline__ float to_float(__nv_fp8_e4m3 x) { return float(x); }
+};
 template <> struct LowPrec<float> {
     static __device__ __forceinline__ float from_float(float x) { return x; }
     static __device__ __forceinline__ float to_float(float x) { return x; }
@@ -122,6 +127,21 @@ __device__ __forceinline__ int fp16_scale_exponent(float mx) {
     frexpf(mx, &ex);                      // mx = f * 2^ex, f in [0.5, 1)
     int e = 15 - ex;
     return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// Column scale exponent e with max|x| * 2^e in [2^7, 2^8) (FP8 E4M3 target range, largest
+// finite E4M3 is 448). Zero (or non-finite) maximum gives 0; clamped to [-100, 100].
+__device__ __forceinline__ int fp8_scale_exponent(float mx) {
+    if (!(mx > 0.0f) || !isfinite(mx)) return 0;
+    int ex;
+    frexpf(mx, &ex);
+    int e = 8 - ex;
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// Scale kinds of the low-precision copies: 0 none (BF16, FP32), 1 FP16 range, 2 FP8 range.
+__device__ __forceinline__ int scale_exponent(int kind, float mx) {
+    return kind == 1 ? fp16_scale_exponent(mx) : (kind == 2 ? fp8_scale_exponent(mx) : 0);
 }
 
 // 2^e as an FP32 number for e in [-126, 127] (exponent field only): multiplying by it is exact

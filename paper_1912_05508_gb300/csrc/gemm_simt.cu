@@ -106,8 +106,8 @@ int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, in
 template <typename TL>
 __global__ void __launch_bounds__(256)
 proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
-                   const int* __restrict__ e, float* __restrict__ R12, int ldr,
-                   TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int want_scale) {
+                   const int* __restrict__ e, const int* __restrict__ sq, float* __restrict__ R12, int ldr,
+                   TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int kind) {
     // Threads split as (row slot i0 < rp) x (split group g < G): group g sums splits
     // g, g + G, ... (four independent loads per trip); the groups are then added in order
     // g = 0, 1, ..., so the result does not depend on timing.
@@ -144,9 +144,12 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
             }
         }
         if (g == 0 && i < w1) {
-            s *= se;
+            // FP8: Q1 column i was scaled by 2^sq_i, so R12 row i is unscaled by it, and the
+            // update operand carries it once more (Q1 R12 = (Q1 2^sq) (2^-sq R12))
+            const float rs = sq ? pow2f(-sq[i]) : 1.f;
+            s *= se * rs;
             R12[(size_t)i + (size_t)j * ldr] = s;
-            mx = fmaxf(mx, fabsf(s));
+            mx = fmaxf(mx, fabsf(s * rs));
         }
     }
     if (!R12l) return;
@@ -156,23 +159,30 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
     if (t == 0) {
         float tm = 0.f;
         for (int w = 0; w < 8; ++w) tm = fmaxf(tm, s_red[w]);
-        s_f = want_scale ? fp16_scale_exponent(tm) : 0;
+        s_f = scale_exponent(kind, tm);
         f[j] = s_f;
     }
     __syncthreads();
     const float sc = pow2f(s_f);
-    for (int i = t; i < w1; i += 256)
-        R12l[(size_t)i + (size_t)j * ldrl] = LowPrec<TL>::from_float(R12[(size_t)i + (size_t)j * ldr] * sc);
+    for (int i = t; i < w1; i += 256) {
+        const float rs = sq ? pow2f(-sq[i]) : 1.f;
+        R12l[(size_t)i + (size_t)j * ldrl] = LowPrec<TL>::from_float(R12[(size_t)i + (size_t)j * ldr] * rs * sc);
+    }
 }
 
-int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, float* R12, int ldr,
+int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, const int* sq, float* R12, int ldr,
                 void* R12l, int ldrl, int* f, int lowp, cudaStream_t st) {
     if (lowp == 0)
-        proj_reduce_kernel<__half><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, R12, ldr, (__half*)R12l, ldrl, f, 1);
+        proj_reduce_kernel<__half><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, nullptr, R12, ldr, (__half*)R12l, ldrl, f, 1);
     else if (lowp == 1)
-        proj_reduce_kernel<__nv_bfloat16><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, R12, ldr, (__nv_bfloat16*)R12l, ldrl, f, 0);
+        proj_reduce_kernel<__nv_bfloat16><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, nullptr, R12, ldr,
+                                                              (__nv_bfloat16*)R12l, ldrl, f, 0);
+    else if (lowp == 2)
+        proj_reduce_kernel<__nv_fp8_e4m3><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, sq, R12, ldr,
+                                                              (__nv_fp8_e4m3*)R12l, ldrl, f, 2);
     else
-        proj_reduce_kernel<float><<<w2, 256, 0, st>>>(part, splits, w1, w2, nullptr, R12, ldr, (float*)nullptr, 0, f, 0);
+        proj_reduce_kernel<float><<<w2, 256, 0, st>>>(part, splits, w1, w2, nullptr, nullptr, R12, ldr, (float*)nullptr,
+                                                      0, f, 0);
     LLS_LAUNCH_CHECK("proj_reduce", st);
     return LLS_OK;
 }
@@ -196,7 +206,7 @@ int simt_projection_f32(const float* Q1, const float* A2, int ldw, int m, int w1
     gemm_simt_kernel<float, float, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         w1, w2, m, kc, Q1, ldw, A2, ldw, part, 0, 1.f, 0.f, nullptr);
     LLS_LAUNCH_CHECK("simt_proj_f32", st);
-    return proj_reduce(part, splits, w1, w2, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st);
+    return proj_reduce(part, splits, w1, w2, nullptr, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st);
 }
 
 int simt_update_f32(const float* Q1, int ldw, const float* R12, int ldr, float* A2, int m, int w1,
@@ -220,7 +230,7 @@ static int simt_lowp_projection(const ProjCall& c, cudaStream_t st) {
     gemm_simt_kernel<TL, TL, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         c.w1, c.w2, c.m, kc, (const TL*)c.Q1l, c.ldh, (const TL*)c.A2l, c.ldh, c.part, 0, 1.f, 0.f, nullptr);
     LLS_LAUNCH_CHECK("simt_upd_f32", st);
-    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
 }
 
 template <typename TL>

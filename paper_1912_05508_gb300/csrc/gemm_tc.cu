@@ -27,7 +27,7 @@
 
 namespace lls {
 
-int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, float* R12, int ldr,
+int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, const int* sq, float* R12, int ldr,
                 void* R12l, int ldrl, int* f, int lowp, cudaStream_t st);
 
 constexpr int kTcThreads = 128;
@@ -116,6 +116,17 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+// kind::f8f6f4 with E4M3 operands (format code 0 for A and B in the instruction descriptor):
+// K = 32 elements = 32 bytes per instruction, the same byte footprint as 16 FP16 elements.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -146,9 +157,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-template <int BN, bool A_MN, int EPI>
+template <int BN, bool A_MN, int EPI, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    static_assert(!(F8 && A_MN), "8-bit operands are used K-major only");
+    constexpr int kKe = F8 ? 2 * kTcBK : kTcBK;   // K elements per 128-byte k-tile row
     constexpr int kBBytes = BN * kTcBK * 2;
     constexpr int kStageBytes = kTcABytes + kBBytes;
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
@@ -160,7 +173,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
-    const int kt_total = (a.K + kTcBK - 1) / kTcBK;
+    const int kt_total = (a.K + kKe - 1) / kKe;
     const int kt0 = blockIdx.z * a.k_tiles_per_split;
     const int kt1 = min(kt_total, kt0 + a.k_tiles_per_split);
     const int nk = kt1 - kt0;
@@ -200,7 +213,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const uint32_t sa = smem_u32(smem + s * kStageBytes);
                 const uint32_t sb = sa + kTcABytes;
                 mbar_expect_tx(full0 + 8 * s, kStageBytes);
-                const int k0 = (kt0 + i) * kTcBK;
+                const int k0 = (kt0 + i) * kKe;
                 if (A_MN) {
                     tma_load_2d(sa, &tmA, m0, k0, full0 + 8 * s);
                     tma_load_2d(sa + kTcABytes / 2, &tmA, m0 + 64, k0, full0 + 8 * s);
@@ -223,7 +236,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const uint64_t ad = A_MN ? smem_desc(sa + kk * 2048, 8192, 1024)
                                              : smem_desc(sa + kk * 32, 16, 1024);
                     const uint64_t bd = smem_desc(sb + kk * 32, 16, 1024);
-                    mma_f16(tmem, ad, bd, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    if constexpr (F8) mma_f8(tmem, ad, bd, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    else mma_f16(tmem, ad, bd, a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
                 }
                 mma_commit(empty0 + 8 * s);
             }
@@ -329,19 +343,22 @@ static int make_tmap(CUtensorMap* tm, const void* base, int lowp, uint64_t inner
                      uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return LLS_ERR_CUDA;
-    if (((uintptr_t)base & 15) != 0 || ((ld * 2) & 15) != 0) return LLS_ERR_UNSUPPORTED;
+    const uint64_t esz = lowp == 2 ? 1 : 2;
+    if (((uintptr_t)base & 15) != 0 || ((ld * esz) & 15) != 0) return LLS_ERR_UNSUPPORTED;
     cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {ld * 2};
+    cuuint64_t strides[1] = {ld * esz};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUtensorMapDataType dt = lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : (lowp == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    CUresult r = fn(tm, dt, 2,
                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? LLS_OK : LLS_ERR_CUDA;
 }
 
 static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
-    const uint32_t fmt = lowp == 0 ? 0u : 1u;       // 0 = F16, 1 = BF16
+    const uint32_t fmt = lowp == 1 ? 1u : 0u;       // kind::f16: 0 = F16, 1 = BF16; kind::f8f6f4: 0 = E4M3
     uint32_t d = 0;
     d |= 1u << 4;                                    // D = F32
     d |= fmt << 7;                                   // A type
@@ -354,10 +371,10 @@ static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
 
 static int pick_bn(int n) { return n <= 64 ? 64 : (n <= 128 ? 128 : 256); }
 
-template <int BN, bool A_MN, int EPI>
+template <int BN, bool A_MN, int EPI, bool F8>
 static int launch_tc(const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
     constexpr int smem = kTcStages * (kTcABytes + BN * kTcBK * 2) + 1024 + 256;
-    auto k = tc_gemm_kernel<BN, A_MN, EPI>;
+    auto k = tc_gemm_kernel<BN, A_MN, EPI, F8>;
     static bool attr = false;
     if (!attr) {
         LLS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -368,11 +385,11 @@ static int launch_tc(const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs&
     return LLS_OK;
 }
 
-template <bool A_MN, int EPI>
+template <bool A_MN, int EPI, bool F8 = false>
 static int launch_bn(int bn, const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
-    if (bn == 64) return launch_tc<64, A_MN, EPI>(tA, tB, a, grid, st);
-    if (bn == 128) return launch_tc<128, A_MN, EPI>(tA, tB, a, grid, st);
-    return launch_tc<256, A_MN, EPI>(tA, tB, a, grid, st);
+    if (bn == 64) return launch_tc<64, A_MN, EPI, F8>(tA, tB, a, grid, st);
+    if (bn == 128) return launch_tc<128, A_MN, EPI, F8>(tA, tB, a, grid, st);
+    return launch_tc<256, A_MN, EPI, F8>(tA, tB, a, grid, st);
 }
 
 static int sm_count() {
@@ -385,10 +402,10 @@ static int sm_count() {
     return sms;
 }
 
-static void proj_split(int m, int w1, int w2, int& splits, int& ktps) {
+static void proj_split(int m, int w1, int w2, int& splits, int& ktps, int lowp = 0) {
     const int bn = pick_bn(w2);
     const int tiles = ceil_div(w1, kTcBM) * ceil_div(w2, bn);
-    const int kt = ceil_div(m, kTcBK);
+    const int kt = ceil_div(m, lowp == 2 ? 2 * kTcBK : kTcBK);
     int want = ceil_div(2 * sm_count(), tiles);             // about two waves of CTAs
     int maxs = kt / 8 > 0 ? kt / 8 : 1;                      // at least 8 K tiles per CTA
     splits = want < maxs ? want : maxs;
@@ -405,23 +422,38 @@ size_t proj_partial_floats(int m, int w1, int w2) {
 
 int gemm_projection(const ProjCall& c, cudaStream_t st) {
     int splits, ktps;
-    proj_split(c.m, c.w1, c.w2, splits, ktps);
+    proj_split(c.m, c.w1, c.w2, splits, ktps, c.lowp);
     if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
     const int bn = pick_bn(c.w2);
+    const uint32_t bk = c.lowp == 2 ? 2 * kTcBK : kTcBK;     // 128-byte rows
     CUtensorMap tA, tB;
-    LLS_TRY(make_tmap(&tA, c.Q1l, c.lowp, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, kTcBK, kTcBM));
-    LLS_TRY(make_tmap(&tB, c.A2l, c.lowp, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldh, kTcBK, (uint32_t)bn));
+    LLS_TRY(make_tmap(&tA, c.Q1l, c.lowp, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, bk, kTcBM));
+    LLS_TRY(make_tmap(&tB, c.A2l, c.lowp, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldh, bk, (uint32_t)bn));
     TcArgs a;
     a.M = c.w1; a.N = c.w2; a.K = c.m; a.k_tiles_per_split = ktps;
     a.idesc = make_idesc(c.lowp, bn, false);
     a.out = c.part; a.ldo = c.w1; a.fexp = nullptr; a.err = c.err;
     dim3 grid(ceil_div(c.w1, kTcBM), ceil_div(c.w2, bn), splits);
-    LLS_TRY((launch_bn<false, TC_EPI_PARTIAL>(bn, tA, tB, a, grid, st)));
-    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+    if (c.lowp == 2) LLS_TRY((launch_bn<false, TC_EPI_PARTIAL, true>(bn, tA, tB, a, grid, st)));
+    else LLS_TRY((launch_bn<false, TC_EPI_PARTIAL>(bn, tA, tB, a, grid, st)));
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
 }
 
 int gemm_update(const UpdCall& c, cudaStream_t st) {
     const int bn = pick_bn(c.w2);
+    if (c.lowp == 2) {
+        // FP8: A = Q1 row-major (K-major, rows of ldq bytes), B = R12l (K-major)
+        if (!c.QT) return LLS_ERR_UNSUPPORTED;
+        CUtensorMap tA, tB;
+        LLS_TRY(make_tmap(&tA, c.QT, 2, (uint64_t)c.w1, (uint64_t)c.m, (uint64_t)c.ldq, 2 * kTcBK, kTcBM));
+        LLS_TRY(make_tmap(&tB, c.R12l, 2, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, 2 * kTcBK, (uint32_t)bn));
+        TcArgs a;
+        a.M = c.m; a.N = c.w2; a.K = c.w1; a.k_tiles_per_split = ceil_div(c.w1, 2 * kTcBK);
+        a.idesc = make_idesc(2, bn, false);
+        a.out = c.A2; a.ldo = c.ldw; a.fexp = c.f; a.err = c.err;
+        dim3 grid(ceil_div(c.m, kTcBM), ceil_div(c.w2, bn), 1);
+        return launch_bn<false, TC_EPI_UPDATE, true>(bn, tA, tB, a, grid, st);
+    }
     CUtensorMap tA, tB;
     LLS_TRY(make_tmap(&tA, c.Q1l, c.lowp, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, 64, kTcBK));
     LLS_TRY(make_tmap(&tB, c.R12l, c.lowp, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, kTcBK, (uint32_t)bn));

@@ -24,6 +24,8 @@ int panel_qr(const PanelCall& c, cudaStream_t st);
 // (FP16 rule; 0 for BF16), Xh[:, j] = round(X[:, j] * 2^e_j). Writes exps[j - c0].
 int scale_cast_columns(const float* X, int ldx, int m, int c0, int w, void* Xh, int ldh,
                        int lowp, int* exps, cudaStream_t st);
+// row-major copy of columns [c0, c0 + w) of a column-major 8-bit matrix (lowp 2 only)
+int rowmajor_copy8(const void* X, int ldx, int m, int c0, int w, void* T, int ldt, cudaStream_t st);
 
 // ---- tensor-core products (gemm_tc.cu) ----------------------------------------------------
 // G1 (Alg. 2 line 8): part[s] = Q1l^T A2l over K-split s; then R12 = sum_s part[s] * 2^-e_j
@@ -33,6 +35,7 @@ struct ProjCall {
     const void* Q1l; const void* A2l; int ldh;   // low-precision operands (column-major, ld ldh)
     int m, w1, w2;                                // M = w1, N = w2, K = m
     const int* e;                                 // A2 column exponents (w2)
+    const int* sq = nullptr;                      // FP8: Q1 column exponents (w1), else null
     float* R12; int ldr;                          // FP32 output block of R
     void* R12l; int ldrl;                         // low-precision scaled copy for G2 (w1 x w2)
     int* f;                                       // R12 column exponents (w2)
@@ -41,7 +44,8 @@ struct ProjCall {
     int* err;                                     // device error word (bounded waits)
 };
 struct UpdCall {
-    const void* Q1l; int ldh;                     // m x w1 low precision
+    const void* Q1l; int ldh;                     // m x w1 low precision (M-major A operand)
+    const void* QT = nullptr; int ldq = 0;        // FP8: Q1 row-major (K-major A operand), ldq bytes
     const void* R12l; int ldrl;                   // w1 x w2 low precision (scaled by 2^f)
     const int* f;
     float* A2; int ldw;                           // m x w2 FP32, updated in place

@@ -13,7 +13,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblls_gb300.so")
 
-PREC = {"fp16": 0, "bf16": 1, "fp32": 3, "fp64": 4}
+PREC = {"fp16": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp64": 4}
 TARGET = {"fp32": 0, "fp64": 1}
 KRYLOV = {"cgls": 0, "lsqr": 1}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",

@@ -175,3 +175,25 @@ def test_lsqr_counts_two_passes_per_iteration():
     # confirmation of each (re)start
     assert info["a_passes"] >= 2 * info["iters"] + 1
     assert info["a_passes"] <= 2 * info["iters"] + 3 * 4
+
+
+# ---- scaled FP8 (E4M3) products ----
+
+@pytest.mark.parametrize("kappa", [1e1, 1e2])
+@pytest.mark.parametrize("kind", ["geometric", "cluster"])
+def test_fp8_products_reach_fp64_target(kappa, kind):
+    # E4M3 keeps 3 significand bits, so R is a coarser preconditioner (kappa(A R^-1) grows like
+    # 1 + c kappa 2^-4); at these condition numbers the iteration still reaches 1e-12
+    p = synth.svd_lls(2000, 160, kind, kappa, seed=int(kappa) + 3)
+    x, info = run(p, prec="fp8", target="fp64", panel_width=16)
+    xs = direct.lls(p.A, p.b)
+    assert info["status"] == 0, info
+    assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
+    assert metrics.forward_error(x, xs) <= 10 * p.kappa * 1e-12
+
+
+def test_fp8_requires_16_column_panels():
+    p = synth.svd_lls(300, 40, "geometric", 10.0, seed=1)
+    with pytest.raises(lls.LLSError) as ei:
+        lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda(), prec="fp8", panel_width=8)
+    assert ei.value.status == -1

@@ -5,10 +5,11 @@ Tolerances
 * FP32 products: the factorization is a recursive Gram-Schmidt QR in FP32, so R matches
   the unique (positive-diagonal) FP64 R to c * kappa * u32 normwise, ||A - QR|| / ||A|| <=
   c * u32 and ||I - Q^T Q|| <= c * kappa * u32 (Sec. 3.2.1), with c ~ sqrt(n).
-* FP16 / BF16 products: the oracle runs the same recursion with the same rounding points
-  in FP64. Rounding decisions can differ where the GPU's FP32 operand and the oracle's
-  FP64 operand straddle a rounding boundary, so R agrees to c * u_low normwise (u16 = 2^-11,
-  ubf16 = 2^-8); backward error <= 4 u_low; orthogonality <= c * kappa * u_low.
+* FP16 / BF16 / FP8 products: the oracle runs the same recursion with the same rounding
+  points in FP64. Rounding decisions can differ where the GPU's FP32 operand and the
+  oracle's FP64 operand straddle a rounding boundary, so R agrees to c * u_low normwise
+  (u16 = 2^-11, ubf16 = 2^-8, u8 = 2^-4 for E4M3); backward error <= 4 u_low;
+  orthogonality <= c * kappa * u_low.
 """
 import numpy as np
 import pytest
@@ -20,7 +21,7 @@ from paper_1912_05508_gb300 import lls, synth
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-ULOW = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+ULOW = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "fp8": 2.0 ** -4}
 
 
 def svd_matrix(m, n, kappa, seed, kind="geometric"):
@@ -48,7 +49,7 @@ def test_fp32_products_match_householder(m, n):
     assert metrics.orthogonality(Q, "2") <= 10 * kappa * U32 * n ** 0.5
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
 @pytest.mark.parametrize("m,n,pw", [(1000, 100, 32), (2048, 256, 32), (777, 96, 16)])
 def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
     kappa = 1e3

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from oracle import direct, metrics, rgsqrf
-from oracle.lowprec import column_scale_exponents, round_bf16, round_fp16, scaled_round
+from oracle.lowprec import column_scale_exponents, round_bf16, round_fp8_e4m3, round_fp16, scaled_round
 from paper_1912_05508_gb300 import synth
 
 
@@ -38,6 +38,31 @@ def test_round_bf16_matches_torch_cast():
     assert np.array_equal(round_bf16(x.astype(np.float64)), ref)
     assert round_bf16(np.array([1 + 2 ** -8]))[0] == 1.0           # tie to even (down)
     assert round_bf16(np.array([1 + 3 * 2 ** -8]))[0] == 1 + 2 ** -6  # tie to even (up)
+
+
+def test_round_fp8_e4m3_matches_torch_cast():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(20000) * 10.0 ** rng.uniform(-4, 2.5, 20000)
+    x = x[np.abs(x) < 440.0]
+    x = np.concatenate([x, [448.0, -448.0, 2.0 ** -9, 2.0 ** -10, 3 * 2.0 ** -10, 2.0 ** -6, 0.0]])
+    x32 = x.astype(np.float32)
+    ref = torch.from_numpy(x32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(round_fp8_e4m3(x32.astype(np.float64)), ref)
+    # ties to even: 1 + 2^-4 lies halfway between 1 and 1 + 2^-3
+    assert round_fp8_e4m3(np.array([1 + 2 ** -4]))[0] == 1.0
+    assert round_fp8_e4m3(np.array([1 + 3 * 2 ** -4]))[0] == 1 + 2 ** -2
+    # saturation (the GPU conversion's satfinite mode) instead of NaN
+    assert np.array_equal(round_fp8_e4m3(np.array([500.0, -1e9])), np.array([448.0, -448.0]))
+
+
+def test_column_scale_fp8_range():
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((64, 30)) * 10.0 ** rng.uniform(-10, 10, 30)
+    e = column_scale_exponents(X, "fp8")
+    mx = np.abs(np.ldexp(X, e[None, :])).max(axis=0)
+    assert ((mx >= 2.0 ** 7) & (mx < 2.0 ** 8)).all()
+    Xl, _ = scaled_round(X, "fp8")
+    np.testing.assert_allclose(np.ldexp(Xl, -e[None, :]), X, rtol=2.0 ** -4, atol=0)
 
 
 def test_column_scale_is_exact_power_of_two_in_range():
@@ -129,7 +154,7 @@ def test_rgsqrf_exact_products_is_the_qr(n, pw):
     assert np.allclose(np.tril(R, -1), 0.0) and (np.diag(R) > 0).all()
 
 
-@pytest.mark.parametrize("prec,u", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("prec,u", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8), ("fp8", 2.0 ** -4)])
 def test_rgsqrf_low_precision_error_scales_with_unit_roundoff(prec, u):
     # Backward error stays at the GEMM precision independent of kappa, orthogonality
     # loss grows with kappa (Sec. 3.2.1, Fig. qr_accu discussion).
