@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--prec", default="fp16")
     ap.add_argument("--target", default="fp64")
     ap.add_argument("--krylov", default="cgls", choices=["cgls", "lsqr"])
+    ap.add_argument("--reorth", type=int, default=0, choices=[0, 1])
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-householder", action="store_true")
@@ -333,7 +334,8 @@ def main():
     dev = torch.device("cuda", local)
     m, n = args.m, args.n
     A, b = make_inputs(args, m, n, rank, dev)
-    o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw, krylov=args.krylov)
+    o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw, krylov=args.krylov,
+                         reorth=args.reorth)
     pw = args.pw if args.pw > 0 else lls.default_options().panel_width
     nb = lls.lls_solve_workspace_size(m, n, o)
     wsbuf = lls.workspace(nb, dev)
@@ -381,7 +383,7 @@ def main():
         ms = float(t.item())
 
     # QR alone (for the QR TFLOP/s half of the metric)
-    qo = lls.make_options(prec=args.prec, panel_width=args.pw)
+    qo = lls.make_options(prec=args.prec, panel_width=args.pw, reorth=args.reorth)
     qnb = lls.qr_factor_workspace_size(m, n, qo)
     qws = wsbuf if qnb <= wsbuf.numel() else lls.workspace(qnb, dev)
     R = torch.empty((n, n), dtype=torch.float32, device=dev).t()
@@ -453,6 +455,7 @@ def main():
                                   f"{args.prec.upper()} products, {args.krylov.upper()} to the "
                                   f"{args.target.upper()} target",
                       "m": m, "n": n, "prec": args.prec, "target": args.target, "krylov": args.krylov,
+                      "reorth": args.reorth,
                       "panel_width": pw,
                       "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
                       "parallelism": f"replicas x{ws}"},

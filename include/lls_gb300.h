@@ -65,7 +65,9 @@ typedef struct {
     int max_iter;      /* iteration cap, default 200 (the paper's cap, Sec. 4.2.3) */
     int panel_width;   /* recursion leaf width b (columns per panel), 0 = default 16 (the paper uses 32, Sec. 3.1.3); 1..32 */
     int krylov;        /* lls_krylov, default CGLS */
-    int leaf_rows;     /* rows per CAQR leaf block, 0 = default 256 (Sec. 3.1.3); 64..256, multiple of 32 */
+    int leaf_rows;     /* reserved, 0 or 256 (the GPU panel's CAQR row blocks are 1024 rows, Sec. 3.1.3) */
+    int reorth;        /* 1: re-orthogonalize (Sec. 4.2.1): factor Q once more, Q1 = Q2 R2, and return
+                          Q2 and R = R2 R1 (twice the QR cost); 0 (default): one pass */
 } lls_options;
 
 typedef struct {

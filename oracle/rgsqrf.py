@@ -144,3 +144,13 @@ def rgsqrf(A: np.ndarray, panel_width: int = 32, prec: str = "fp16",
 
     rec(0, n)
     return W, R
+
+
+def rgsqrf_reorth(A: np.ndarray, panel_width: int = 32, prec: str = "fp16", leaf_rows: int = 256,
+                  leaf: str = "cgs2"):
+    """Re-orthogonalized RGSQRF: A = Q1 R1, then Q1 = Q2 R2 by the same recursion, returning
+    (Q2, R2 R1). The second pass restores the orthogonality the recursion loses with growing
+    condition number (the paper's remedy for ill-conditioned inputs, Sec. 4.2.1)."""
+    Q1, R1 = rgsqrf(A, panel_width, prec, leaf_rows, leaf)
+    Q2, R2 = rgsqrf(Q1, panel_width, prec, leaf_rows, leaf)
+    return Q2, R2 @ R1

@@ -44,6 +44,7 @@ static bool valid_opts(const lls_options& o) {
     if (o.panel_width < 1 || o.panel_width > 32) return false;
     if (o.gemm_prec == LLS_PREC_FP8 && o.panel_width % 16 != 0) return false;   // 16-byte aligned FP8 slices
     if (o.leaf_rows != 256) return false;
+    if (o.reorth != 0 && o.reorth != 1) return false;
     return true;
 }
 
@@ -63,6 +64,7 @@ struct QrWs {
     float* part; size_t part_floats;
     void* R12l; int* eA; int* f;
     uint8_t* QT; int ldq; int* sQ;   // FP8 only: row-major copy of Q and its column exponents
+    float* R1; float* Rt;            // re-orthogonalization: the first pass's R, and R2 R1 (n x n)
     float* rbuf; float* qbuf; unsigned* cnt; size_t cnt_words;
     int* err;
     double* dinfo;     // 16 doubles of device-side results
@@ -90,6 +92,8 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.ldq = (int)align_up((size_t)n, 16);
     w.QT = f8 ? ar.take<uint8_t>((size_t)m * w.ldq) : nullptr;
     w.sQ = f8 ? ar.take<int>(n) : nullptr;
+    w.R1 = o.reorth ? ar.take<float>((size_t)n * n) : nullptr;
+    w.Rt = o.reorth ? ar.take<float>((size_t)n * n) : nullptr;
     size_t rb, qb, cw;
     panel_scratch_sizes(m, rb, qb, cw);
     w.rbuf = ar.take<float>(rb);
@@ -163,7 +167,18 @@ static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, cons
     QrCtx c;
     c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec);
     c.w = w; c.R = R; c.ldr = ldr; c.st = st;
-    return qr_rec(c, 0, n);
+    LLS_TRY(qr_rec(c, 0, n));
+    if (o.reorth) {
+        // A = Q1 R1 with Q1 in W; factor Q1 = Q2 R2 by the same recursion, so A = Q2 (R2 R1)
+        LLS_CUDA_TRY(cudaMemcpy2DAsync(w.R1, sizeof(float) * (size_t)n, R, sizeof(float) * (size_t)ldr,
+                                       sizeof(float) * (size_t)n, (size_t)n, cudaMemcpyDeviceToDevice, st));
+        LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
+        LLS_TRY(qr_rec(c, 0, n));
+        LLS_TRY(triu_product(R, ldr, w.R1, n, w.Rt, n, n, st));     // R2 R1
+        LLS_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(float) * (size_t)ldr, w.Rt, sizeof(float) * (size_t)n,
+                                       sizeof(float) * (size_t)n, (size_t)n, cudaMemcpyDeviceToDevice, st));
+    }
+    return LLS_OK;
 }
 
 }  // namespace lls
@@ -564,7 +579,7 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
     resolve(opts, o);
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
-    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8)
+    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8 || o.reorth)
         return LLS_ERR_UNSUPPORTED;
     if (!A || !lda || !b || !x || !ws) return LLS_ERR_ARG;
     for (int i = 0; i < batch; ++i) {

@@ -65,6 +65,9 @@ int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, in
 // ---- triangular inverse (trinv.cu) ----------------------------------------------------------
 // Minv = R^{-1} (upper triangular, n x n, ld n) via diagonal-block inverses and the recursion
 // M12 = -M11 R12 M22 over the same column split as the QR; Mt = Minv^T. tmp: n*n floats.
+// C = U V for upper-triangular n x n U, V (column-major); C (distinct from U and V) is
+// upper triangular with zeros written below the diagonal. FP32.
+int triu_product(const float* U, int ldu, const float* V, int ldv, float* C, int ldc, int n, cudaStream_t st);
 int tri_inverse(const float* R, int ldr, int n, int pw, float* Minv, float* Mt, float* tmp,
                 int* dev_err, cudaStream_t st);
 

@@ -138,6 +138,63 @@ __global__ void transpose_kernel(const float* __restrict__ X, int ldx, float* __
     }
 }
 
+// C = U V for upper-triangular U, V: C(i, j) = sum_{k = i..j} U(i, k) V(k, j). 64 x 64 tiles,
+// the K loop restricted to [i0, j0 + 64); tiles entirely below the diagonal are written zero.
+__global__ void __launch_bounds__(256)
+triu_product_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
+                    float* __restrict__ C, int ldc, int n) {
+    const int i0 = blockIdx.x * kTB, j0 = blockIdx.y * kTB;
+    __shared__ float As[kTK][kTB + 4];
+    __shared__ float Bs[kTK][kTB + 4];
+    const int t = threadIdx.x;
+    const int ti = (t % 16) * 4, tj = (t / 16) * 4;
+    float acc[4][4] = {};
+    if (i0 < j0 + kTB) {
+        const int kbeg = (i0 / kTK) * kTK, kend = min(n, j0 + kTB);
+        for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int idx = t + r * 256;
+                const int ii = idx % kTB, kk = idx / kTB;
+                const int gi = i0 + ii, gk = k0 + kk;
+                As[kk][ii] = (gi < n && gk < n && gk >= gi) ? U[(size_t)gi + (size_t)gk * ldu] : 0.f;
+                const int kk2 = idx % kTK, jj = idx / kTK;
+                const int gj = j0 + jj, gk2 = k0 + kk2;
+                Bs[kk2][jj] = (gj < n && gk2 < n && gk2 <= gj) ? V[(size_t)gk2 + (size_t)gj * ldv] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < kTK; ++kk) {
+                float av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { av[u] = As[kk][ti + u]; bv[u] = Bs[kk][tj + u]; }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int j = j0 + tj + v;
+        if (j >= n) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + ti + u;
+            if (i < n) C[(size_t)i + (size_t)j * ldc] = i <= j ? acc[u][v] : 0.f;
+        }
+    }
+}
+
+int triu_product(const float* U, int ldu, const float* V, int ldv, float* C, int ldc, int n, cudaStream_t st) {
+    dim3 grid(ceil_div(n, kTB), ceil_div(n, kTB));
+    triu_product_kernel<<<grid, 256, 0, st>>>(U, ldu, V, ldv, C, ldc, n);
+    LLS_LAUNCH_CHECK("triu_product", st);
+    return LLS_OK;
+}
+
 namespace {
 struct TreeNode { int c0, w1, w2, depth; };
 

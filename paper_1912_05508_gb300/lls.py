@@ -32,7 +32,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
 class lls_options(C.Structure):
     _fields_ = [("gemm_prec", C.c_int), ("target", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("panel_width", C.c_int), ("krylov", C.c_int),
-                ("leaf_rows", C.c_int)]
+                ("leaf_rows", C.c_int), ("reorth", C.c_int)]
 
 
 class lls_info(C.Structure):
@@ -118,7 +118,7 @@ def default_options() -> lls_options:
 
 
 def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-                 krylov="cgls", leaf_rows=256) -> lls_options:
+                 krylov="cgls", leaf_rows=256, reorth=0) -> lls_options:
     o = lls_options()
     load().lls_default_options(C.byref(o))
     o.gemm_prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -128,6 +128,7 @@ def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=
     o.panel_width = int(panel_width)
     o.krylov = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
     o.leaf_rows = int(leaf_rows)
+    o.reorth = int(reorth)
     return o
 
 
@@ -289,12 +290,12 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None):
+def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=0):
     """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False."""
     torch = _torch()
     _check_colmajor(A)
     m, n = A.shape
-    o = make_options(prec=prec, panel_width=panel_width)
+    o = make_options(prec=prec, panel_width=panel_width, reorth=reorth)
     nb = qr_factor_workspace_size(m, n, o)
     if nb == 0:
         raise LLSError(-1, "qr_factor_workspace_size")
@@ -309,7 +310,7 @@ def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None):
 
 
 def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-          krylov="cgls", want_r=False, ws=None, stream=None, check=True):
+          krylov="cgls", want_r=False, ws=None, stream=None, check=True, reorth=0):
     """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
 
     Returns (x, info_dict[, R]). Synchronizes the stream (to fill info)."""
@@ -317,7 +318,7 @@ def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0
     _check_colmajor(A)
     m, n = A.shape
     o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter,
-                     panel_width=panel_width, krylov=krylov)
+                     panel_width=panel_width, krylov=krylov, reorth=reorth)
     nb = lls_solve_workspace_size(m, n, o)
     if nb == 0:
         raise LLSError(-1, "lls_solve_workspace_size")

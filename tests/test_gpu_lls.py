@@ -197,3 +197,15 @@ def test_fp8_requires_16_column_panels():
     with pytest.raises(lls.LLSError) as ei:
         lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda(), prec="fp8", panel_width=8)
     assert ei.value.status == -1
+
+
+def test_reorth_fp32_products_converge_at_kappa_1e6():
+    # kappa = 1e6: one pass loses orthogonality (and preconditioning quality) like kappa^2 u;
+    # with the second pass the FP32-product factorization preconditions to 1e-12 quickly
+    p = synth.svd_lls(3000, 200, "geometric", 1e6, seed=61)
+    x, info = run(p, prec="fp32", target="fp64", reorth=1)
+    xs = direct.lls(p.A, p.b)
+    assert info["status"] == 0, info
+    assert info["iters"] <= 30
+    assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
+    assert metrics.forward_error(x, xs) <= 10 * p.kappa * 1e-12

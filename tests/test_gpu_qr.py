@@ -92,3 +92,21 @@ def test_q_optional_and_repeatable():
     _, R2 = lls.qr(Ad, prec="fp16", want_q=False)
     torch.cuda.synchronize()
     assert torch.equal(R1, R2)     # fixed reduction order: bitwise repeatable
+
+
+@pytest.mark.parametrize("prec,u", [("fp32", U32), ("fp16", 2.0 ** -11)])
+def test_reorth_restores_orthogonality(prec, u):
+    # with the recursion's single projection per node, orthogonality decays with kappa; the
+    # second pass brings it back to the product precision (oracle: oracle.rgsqrf.rgsqrf_reorth)
+    kappa = 1e5 if prec == "fp32" else 1e3
+    A = svd_matrix(2000, 128, kappa, seed=44)
+    Q1, R1 = lls.qr(lls.colmajor(A), prec=prec, panel_width=16)
+    Q2, R2 = lls.qr(lls.colmajor(A), prec=prec, panel_width=16, reorth=1)
+    torch.cuda.synchronize()
+    Q1, Q2 = Q1.cpu().numpy().astype(np.float64), Q2.cpu().numpy().astype(np.float64)
+    R2 = R2.cpu().numpy().astype(np.float64)
+    o1, o2 = metrics.orthogonality(Q1, "2"), metrics.orthogonality(Q2, "2")
+    assert o2 < o1 / 10
+    assert o2 <= 16 * u * 128 ** 0.5
+    assert metrics.qr_factorization_error(A, Q2, R2) <= 16 * u * 128 ** 0.5
+    assert np.allclose(np.tril(R2, -1), 0.0)

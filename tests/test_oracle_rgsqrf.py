@@ -169,3 +169,21 @@ def test_rgsqrf_low_precision_error_scales_with_unit_roundoff(prec, u):
         if e_prev is not None:
             assert orth > e_prev           # loses orthogonality as kappa grows
         e_prev = orth
+
+
+def test_reorth_exact_products_is_the_qr():
+    A = ill_conditioned(600, 80, 1e6, seed=21)
+    Q, R = rgsqrf.rgsqrf_reorth(A, 16, "fp64", leaf_rows=128)
+    Qh, Rh = direct.householder_qr(A)
+    assert np.linalg.norm(R - Rh) <= 1e-9 * np.linalg.norm(Rh)
+    assert metrics.orthogonality(Q) < 1e-14
+
+
+def test_reorth_restores_orthogonality_of_low_precision_factors():
+    A = ill_conditioned(1024, 96, 1e3, seed=22)
+    Q1, R1 = rgsqrf.rgsqrf(A, 32, "fp16", leaf_rows=256)
+    Q2, R2 = rgsqrf.rgsqrf_reorth(A, 32, "fp16", leaf_rows=256)
+    o1, o2 = metrics.orthogonality(Q1, "2"), metrics.orthogonality(Q2, "2")
+    assert o2 < o1 / 20
+    assert o2 < 8 * 2.0 ** -11 * 96 ** 0.5
+    assert metrics.qr_factorization_error(A, Q2, R2) < 8 * 2.0 ** -11
