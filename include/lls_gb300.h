@@ -81,7 +81,8 @@ typedef struct {
     double xnorm;      /* ||x||_2 */
     float qr_ms;       /* device time of the factorization (and preconditioner set-up) */
     float krylov_ms;   /* device time of the Krylov iteration */
-    int a_passes;      /* full passes over A made by the Krylov kernel (A x, A^T r products) */
+    int a_passes;      /* full passes over A made by the Krylov phase (A x, A^T r products; the
+                          one-pass CGLS engine's row-block copy of A counts as 2: read + write) */
     int m_passes;      /* products with the n x n preconditioner R^{-1} or its transpose */
 } lls_info;
 

@@ -7,6 +7,7 @@
 //   update A2 <- A2 - Q1 R12 (Alg. 2 line 9)          -> FP32 in place
 // and for every leaf (<= panel_width columns) the CAQR panel (Eq. caqr). All of it is
 // asynchronous on the caller's stream; nothing is allocated.
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -66,6 +67,7 @@ struct QrWs {
     uint8_t* QT; int ldq; int* sQ;   // FP8 only: row-major copy of Q and its column exponents
     float* R1; float* Rt;            // re-orthogonalization: the first pass's R, and R2 R1 (n x n)
     float* rbuf; float* qbuf; unsigned* cnt; size_t cnt_words;
+    unsigned* colmax; unsigned* nbar;   // fused narrow nodes: column maxima (n), grid barrier (2)
     int* err;
     double* dinfo;     // 16 doubles of device-side results
     double* red;       // 8192 doubles of reduction partials
@@ -82,6 +84,10 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.W = ar.take<float>((size_t)w.ldw * n);
     w.Wh = lowp ? (void*)ar.take<uint16_t>((size_t)w.ldh * n) : nullptr;
     w.part_floats = max_partial(m, 0, n, o.panel_width, lowp);
+    if (o.gemm_prec == LLS_PREC_FP16 || o.gemm_prec == LLS_PREC_BF16) {
+        const size_t nf = node_fused_part_floats(m);
+        if (nf > w.part_floats) w.part_floats = nf;
+    }
     if (w.part_floats == 0) w.part_floats = 1;
     w.part = ar.take<float>(w.part_floats);
     size_t r12 = (size_t)(n / 2 + 32) * (size_t)(n / 2 + 32);
@@ -100,6 +106,8 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.qbuf = ar.take<float>(qb);
     w.cnt = ar.take<unsigned>(cw);
     w.cnt_words = cw;
+    w.colmax = ar.take<unsigned>((size_t)n + 2);
+    w.nbar = w.colmax ? w.colmax + n : nullptr;
     w.err = ar.take<int>(16);
     w.dinfo = ar.take<double>(16);
     w.red = ar.take<double>(8192);
@@ -111,6 +119,15 @@ struct QrCtx {
     float* R; int ldr;
     cudaStream_t st;
 };
+
+// LLS_NODE=split keeps narrow nodes on the four-kernel path (for comparisons).
+static bool use_fused_nodes() {
+    static const bool on = [] {
+        const char* v = getenv("LLS_NODE");
+        return !(v && v[0] == 's');
+    }();
+    return on;
+}
 
 static int qr_rec(QrCtx& c, int c0, int w) {
     if (w <= c.pw) {
@@ -139,6 +156,18 @@ static int qr_rec(QrCtx& c, int c0, int w) {
     } else {
         const size_t esz = c.lowp == 2 ? 1 : 2;
         const char* Whb = (const char*)c.w.Wh;
+        if (use_fused_nodes()) {
+            NodeCall nc;
+            nc.W = c.w.W; nc.ldw = c.w.ldw; nc.Wh = c.w.Wh; nc.ldh = c.w.ldh;
+            nc.m = c.m; nc.c0 = c0; nc.w1 = w1; nc.w2 = w2; nc.lowp = c.lowp;
+            nc.R = c.R; nc.ldr = c.ldr; nc.part = c.w.part; nc.part_floats = c.w.part_floats;
+            nc.R12l = c.w.R12l; nc.f = c.w.f; nc.colmax = c.w.colmax; nc.bar = c.w.nbar; nc.err = c.w.err;
+            const int r = node_fused(nc, c.st);
+            if (r != LLS_ERR_UNSUPPORTED) {
+                LLS_TRY(r);
+                return qr_rec(c, c0 + w1, w2);
+            }
+        }
         LLS_TRY(scale_cast_columns(c.w.W, c.w.ldw, c.m, c0 + w1, w2, c.w.Wh, c.w.ldh, c.lowp, c.w.eA, c.st));
         ProjCall pc;
         pc.Q1l = Whb + esz * (size_t)c0 * c.w.ldh;
@@ -161,6 +190,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
                   QrWs& w, cudaStream_t st) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
+    LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * ((size_t)n + 2), st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
     LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
@@ -363,7 +393,7 @@ static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w,
     Minv = ar.take<float>((size_t)n * n);
     Mt = ar.take<float>((size_t)n * n);
     tmp = ar.take<float>((size_t)n * n);
-    ks_bytes = krylov_scratch_bytes(m, n, 0);
+    ks_bytes = krylov_scratch_bytes(m, n, 0, o.krylov == LLS_KRYLOV_CGLS);
     ks = ar.take<char>(ks_bytes);
 }
 

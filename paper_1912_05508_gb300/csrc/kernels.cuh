@@ -18,6 +18,8 @@ struct PanelCall {
 };
 void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t& cnt_words);
 int panel_qr(const PanelCall& c, cudaStream_t st);
+// One-level-tree variant (panel_flat.cu); LLS_ERR_UNSUPPORTED when the panel needs a deeper tree.
+int panel_flat_qr(const PanelCall& c, cudaStream_t st);
 
 // ---- scale / cast (cast.cu) ---------------------------------------------------------------
 // For columns [c0, c0 + w) of the FP32 matrix X (m rows, ldx): e_j = column scale exponent
@@ -54,6 +56,22 @@ struct UpdCall {
     int* err;
 };
 size_t proj_partial_floats(int m, int w1, int w2);
+// Narrow node (w1 <= 32, FP16/BF16) as one cooperative launch (node_fused.cu): the same
+// products as gemm_projection + gemm_update without the separate cast and reduce passes.
+// LLS_ERR_UNSUPPORTED (nothing launched) when the node does not qualify.
+struct NodeCall {
+    float* W; int ldw;                            // FP32 work matrix (Q1 and A2 columns)
+    const void* Wh; int ldh;                      // product-precision copy holding Q1l
+    int m, c0, w1, w2, lowp;
+    float* R; int ldr;
+    float* part; size_t part_floats;              // >= node_fused_part_floats(m)
+    void* R12l; int* f;                           // >= 32 x 32 low-precision values; w2 ints
+    unsigned* colmax;                             // n words, zero on entry (left zero)
+    unsigned* bar;                                // 2 words, zero on entry (left zero)
+    int* err;
+};
+size_t node_fused_part_floats(int m);
+int node_fused(const NodeCall& c, cudaStream_t st);
 int gemm_projection(const ProjCall& c, cudaStream_t st);
 int gemm_update(const UpdCall& c, cudaStream_t st);
 
@@ -87,7 +105,8 @@ struct KrylovCall {
     int* dev_err;
     double* dev_info;       // [iters, eta, fwd, res, atr, anorm, xnorm, status]
 };
-size_t krylov_scratch_bytes(int m, int n, int grid);
+// one_pass: room for the one-pass CGLS engine's row-block copy of A (used when n <= 4096).
+size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass = false);
 int krylov_solve(const KrylovCall& c, cudaStream_t st);
 
 // Adjoint (krylov.cu): z = (A^T A)^{-1} g by M M^T-preconditioned CG, then

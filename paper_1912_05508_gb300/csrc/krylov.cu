@@ -38,7 +38,7 @@ namespace lls {
 constexpr int kKThreads = 256;
 constexpr int kKWarps = kKThreads / 32;
 constexpr int kRowTile = 1024;    // rows per A t work item (four rows per thread)
-constexpr int kColChunk = 128;    // columns per A t work item
+constexpr int kColChunk = 64;     // columns per A t work item
 constexpr int kRowChunk = 2048;   // rows per A^T r work item (staged in shared memory)
 constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
 constexpr int kMaxRestarts = 3;
@@ -62,6 +62,7 @@ struct KArgs {
     int nrt, nck, nrc, ncg;
     double *v1part, *v2part;     // fused engine: per-CTA partial A^T q and A^T r, [grid][n]
     int aligned16;               // A and lda allow 16-byte copies of 4-row column segments
+    const float4* At;            // row-block copy of A: At[blk * n + j] = A[4 blk .. 4 blk + 3, j], or null
     int vec_floats;              // floats reserved at the start of dynamic smem for vectors
 };
 
@@ -231,10 +232,36 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Two compensated dot-product steps at once (dot2_step on each lane of a float2), with the
+// paired FP32 instructions of sm_100 and later; every operation rounds to nearest, so the
+// error-free transformations hold lane by lane.
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ void dot2_step2(float2& s, float2& c, float2 a, float2 th, float2 tl) {
+    const float2 p = __fmul2_rn(a, th);
+    float2 e = __ffma2_rn(a, th, neg2(p));           // exact: a*th = p + e
+    e = __ffma2_rn(a, tl, e);
+    const float2 s2 = __fadd2_rn(s, p);              // TwoSum(s, p) = s2 + e2
+    const float2 z = __fadd2_rn(s2, neg2(s));
+    const float2 e2 = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(s2, neg2(z)))), __fadd2_rn(p, neg2(z)));
+    s = s2;
+    c = __fadd2_rn(c, __fadd2_rn(e, e2));
+}
+
 // Row block `blk` (rows 4 blk .. 4 blk + 3) of the CTA's own columns into buffer `dst`,
 // stored column by column: dst[j] = (A[i0, j], A[i0+1, j], A[i0+2, j], A[i0+3, j]).
 template <int NC>
 __device__ __forceinline__ void prefetch_rows(const KArgs& a, int blk, float4* dst) {
+    if (a.At) {   // the block is one contiguous run of n 16-byte segments
+        const float4* src = a.At + (size_t)blk * a.n;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int j = threadIdx.x + c * kKThreads;
+            if (j >= a.n) break;
+            cp_async16((uint32_t)__cvta_generic_to_shared(dst + j), src + j);
+        }
+        cp_async_commit();
+        return;
+    }
     const int i0 = blk * kRB;
     const bool full = a.aligned16 && (i0 + kRB <= a.m);
 #pragma unroll
@@ -258,21 +285,28 @@ __device__ __forceinline__ void prefetch_rows(const KArgs& a, int blk, float4* d
 
 // One pass over A. doA: q = A t (written to a.q, ||q||^2 added to dsum by threads 0..3);
 // doB1: per-CTA partial of A^T q into v1part; doB2: per-CTA partial of A^T r into v2part.
+// Thread t owns columns t + 256 c (c < NC); the products of two columns (A^T) or two rows
+// (A t) advance together in the paired FP32 instructions.
 template <int NC>
 __device__ void fused_pass(const KArgs& a, const double* __restrict__ tvec, const double* __restrict__ rvec,
                            bool doA, bool doB1, bool doB2, double& dsum) {
+    constexpr int NP = (NC + 1) / 2;   // column pairs; an odd last pair carries one column
     float4* ring = reinterpret_cast<float4*>(reinterpret_cast<float*>(k_dsm) + a.vec_floats);
     __shared__ float2 s_red[kKWarps][kRB];
-    __shared__ double s_q[kRB];
+    __shared__ float4 s_qr[kRB];   // per row of the block: q and r as double-float (qh, ql, rh, rl)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    float th[NC], tl[NC], v1s[NC], v1c[NC], v2s[NC], v2c[NC];
+    const float2 z2 = make_float2(0.f, 0.f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float th[NC], tl[NC];
+    float2 v1s[NP], v1c[NP], v2s[NP], v2c[NP];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int j = t + c * kKThreads;
         th[c] = tl[c] = 0.f;
         if (doA && j < a.n) split_df(__ldcg(tvec + j), th[c], tl[c]);
-        v1s[c] = v1c[c] = v2s[c] = v2c[c] = 0.f;
     }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) v1s[p] = v1c[p] = v2s[p] = v2c[p] = z2;
     const int nblk = (a.m + kRB - 1) / kRB;
     const int per = (nblk + gridDim.x - 1) / gridDim.x;
     const int b0 = blockIdx.x * per, b1 = min(nblk, b0 + per);
@@ -289,76 +323,75 @@ __device__ void fused_pass(const KArgs& a, const double* __restrict__ tvec, cons
         __syncthreads();
         const float4* rb = ring + buf * a.n;
         const int i0 = blk * kRB;
-        double q[kRB] = {0.0, 0.0, 0.0, 0.0};
         if (doA) {
-            float qs[kRB] = {0.f, 0.f, 0.f, 0.f}, qc[kRB] = {0.f, 0.f, 0.f, 0.f};
+            float2 s01 = z2, c01 = z2, s23 = z2, c23 = z2;   // rows (0, 1) and (2, 3)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int j = t + c * kKThreads;
-                if (j < a.n) {
-                    const float4 av = rb[j];
-                    dot2_step(qs[0], qc[0], av.x, th[c], tl[c]);
-                    dot2_step(qs[1], qc[1], av.y, th[c], tl[c]);
-                    dot2_step(qs[2], qc[2], av.z, th[c], tl[c]);
-                    dot2_step(qs[3], qc[3], av.w, th[c], tl[c]);
-                }
+                const float4 av = j < a.n ? rb[j] : z4;
+                const float2 h2 = make_float2(th[c], th[c]), l2 = make_float2(tl[c], tl[c]);
+                dot2_step2(s01, c01, make_float2(av.x, av.y), h2, l2);
+                dot2_step2(s23, c23, make_float2(av.z, av.w), h2, l2);
             }
+            float qs[kRB] = {s01.x, s01.y, s23.x, s23.y}, qc[kRB] = {c01.x, c01.y, c23.x, c23.y};
 #pragma unroll
             for (int r = 0; r < kRB; ++r) {
                 warp_sum_df(qs[r], qc[r]);
                 if (lane == 0) s_red[warp][r] = make_float2(qs[r], qc[r]);
             }
             __syncthreads();
-            if (t < kRB) {
-                double v = 0.0;
+        }
+        // the block's row scalars q_i and r_i, split once (FP64 work is scarce on this GPU)
+        if (t < kRB) {
+            double v = 0.0;
+            if (doA) {
 #pragma unroll
                 for (int w = 0; w < kKWarps; ++w) v += join_df(s_red[w][t].x, s_red[w][t].y);
-                s_q[t] = v;
                 if (i0 + t < a.m) {
                     a.q[i0 + t] = v;
                     dsum += v * v;
                 }
             }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < kRB; ++r) q[r] = s_q[r];
+            const double rv = (doB2 && i0 + t < a.m) ? __ldcg(rvec + i0 + t) : 0.0;
+            float4 o;
+            split_df(v, o.x, o.y);
+            split_df(rv, o.z, o.w);
+            s_qr[t] = o;
         }
+        __syncthreads();
         if (doB1 || doB2) {
             float qh[kRB], ql[kRB], rh[kRB], rl[kRB];
 #pragma unroll
             for (int r = 0; r < kRB; ++r) {
-                split_df(q[r], qh[r], ql[r]);
-                const double rv = (doB2 && i0 + r < a.m) ? __ldcg(rvec + i0 + r) : 0.0;
-                split_df(rv, rh[r], rl[r]);
+                const float4 o = s_qr[r];
+                qh[r] = o.x; ql[r] = o.y; rh[r] = o.z; rl[r] = o.w;
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int j = t + c * kKThreads;
-                if (j < a.n) {
-                    const float4 av = rb[j];
-                    if (doB1) {
-                        dot2_step(v1s[c], v1c[c], av.x, qh[0], ql[0]);
-                        dot2_step(v1s[c], v1c[c], av.y, qh[1], ql[1]);
-                        dot2_step(v1s[c], v1c[c], av.z, qh[2], ql[2]);
-                        dot2_step(v1s[c], v1c[c], av.w, qh[3], ql[3]);
-                    }
-                    if (doB2) {
-                        dot2_step(v2s[c], v2c[c], av.x, rh[0], rl[0]);
-                        dot2_step(v2s[c], v2c[c], av.y, rh[1], rl[1]);
-                        dot2_step(v2s[c], v2c[c], av.z, rh[2], rl[2]);
-                        dot2_step(v2s[c], v2c[c], av.w, rh[3], rl[3]);
-                    }
+            for (int p = 0; p < NP; ++p) {
+                const int j0 = t + (2 * p) * kKThreads, j1 = j0 + kKThreads;
+                const float4 A0 = j0 < a.n ? rb[j0] : z4;
+                const float4 A1 = (2 * p + 1 < NC && j1 < a.n) ? rb[j1] : z4;
+                const float2 a2[kRB] = {make_float2(A0.x, A1.x), make_float2(A0.y, A1.y),
+                                        make_float2(A0.z, A1.z), make_float2(A0.w, A1.w)};
+#pragma unroll
+                for (int r = 0; r < kRB; ++r) {
+                    if (doB1) dot2_step2(v1s[p], v1c[p], a2[r], make_float2(qh[r], qh[r]), make_float2(ql[r], ql[r]));
+                    if (doB2) dot2_step2(v2s[p], v2c[p], a2[r], make_float2(rh[r], rh[r]), make_float2(rl[r], rl[r]));
                 }
             }
         }
         __syncthreads();   // this buffer is overwritten by the prefetch two blocks ahead
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const int j = t + c * kKThreads;
-        if (j < a.n) {
-            if (doB1) a.v1part[(size_t)blockIdx.x * a.n + j] = join_df(v1s[c], v1c[c]);
-            if (doB2) a.v2part[(size_t)blockIdx.x * a.n + j] = join_df(v2s[c], v2c[c]);
+    for (int p = 0; p < NP; ++p) {
+        const int j0 = t + (2 * p) * kKThreads, j1 = j0 + kKThreads;
+        if (j0 < a.n) {
+            if (doB1) a.v1part[(size_t)blockIdx.x * a.n + j0] = join_df(v1s[p].x, v1c[p].x);
+            if (doB2) a.v2part[(size_t)blockIdx.x * a.n + j0] = join_df(v2s[p].x, v2c[p].x);
+        }
+        if (2 * p + 1 < NC && j1 < a.n) {
+            if (doB1) a.v1part[(size_t)blockIdx.x * a.n + j1] = join_df(v1s[p].y, v1c[p].y);
+            if (doB2) a.v2part[(size_t)blockIdx.x * a.n + j1] = join_df(v2s[p].y, v2c[p].y);
         }
     }
 }
@@ -384,7 +417,7 @@ __device__ double reduce_u(const KArgs& a, double alpha, bool use_v1, int gtid, 
 
 // NC > 0: fused engine with NC columns per thread; NC == 0: two-pass engine.
 template <int NC>
-__global__ void __launch_bounds__(kKThreads, 1)
+__global__ void __launch_bounds__(kKThreads, NC > 0 ? 1 : 3)
 cgls_kernel(KArgs a) {
     const int gtid = blockIdx.x * kKThreads + threadIdx.x, gthreads = gridDim.x * kKThreads;
     const double anorm = sqrt(*a.anorm2);
@@ -562,7 +595,7 @@ cgls_kernel(KArgs a) {
         a.info[5] = anorm;
         a.info[6] = sqrt(xn2);
         a.info[7] = status;
-        a.info[10] = apasses;
+        a.info[10] = apasses + (a.At ? 2 : 0);   // the row-block copy reads and writes A once
         a.info[11] = mpasses;
     }
 }
@@ -905,10 +938,12 @@ adjoint_kernel(AdjArgs aa) {
 struct KLayout {
     int nrt, nck, nrc, ncg;
     size_t off_r, off_q, off_t, off_p, off_s, off_u, off_d, off_qpart, off_upart, off_v1, off_v2, off_bpart,
-        off_bar, total;
+        off_bar, off_tile, total;
 };
 
-static KLayout k_layout(int m, int n, int grid) {
+// The one-pass engine streams A from a copy in 4-row blocks (tiled = true): block blk is the
+// contiguous run At[blk * n .. blk * n + n) of 16-byte segments (A[4 blk .. 4 blk + 3, j]).
+static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     KLayout L;
     L.nrt = ceil_div(m, kRowTile);
     L.nck = ceil_div(n, kColChunk);
@@ -929,8 +964,44 @@ static KLayout k_layout(int m, int n, int grid) {
     L.off_v2 = take(8ull * n * grid);
     L.off_bpart = take(8ull * kNPart * grid);
     L.off_bar = take(64);
+    L.off_tile = tiled ? take(16ull * (size_t)ceil_div(m, kRB) * n) : 0;
     L.total = o;
     return L;
+}
+
+// At[blk * n + j] = (A[4 blk + r, j], r = 0..3), rows beyond m as zero. 64 row blocks x 32
+// columns per CTA through shared memory, so both the column reads and the block writes are
+// contiguous.
+__global__ void __launch_bounds__(256) tile_rows_kernel(const float* __restrict__ A, int lda, int m, int n,
+                                                        float4* __restrict__ At, int aligned16) {
+    __shared__ float4 tile[64][33];
+    const int nblk = (m + kRB - 1) / kRB;
+    const int blk0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int bb = threadIdx.x % 64, jj = threadIdx.x / 64 + 4 * it;
+        const int j = j0 + jj, i = kRB * (blk0 + bb);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < n && i < m) {
+            const float* src = A + (size_t)j * lda + i;
+            if (aligned16 && i + kRB <= m) {
+                v = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+                v.x = src[0];
+                if (i + 1 < m) v.y = src[1];
+                if (i + 2 < m) v.z = src[2];
+                if (i + 3 < m) v.w = src[3];
+            }
+        }
+        tile[bb][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int jj = threadIdx.x % 32, bb = threadIdx.x / 32 + 8 * it;
+        const int j = j0 + jj, blk = blk0 + bb;
+        if (j < n && blk < nblk) At[(size_t)blk * n + j] = tile[bb][jj];
+    }
 }
 
 static int sm_count() {
@@ -940,14 +1011,24 @@ static int sm_count() {
     return sms;
 }
 
-constexpr int kMaxGridPerSm = 2;
+constexpr int kMaxGridPerSm = 3;
 
-size_t krylov_scratch_bytes(int m, int n, int grid) {
+// The one-pass engine (CGLS, n <= 4096) and its copy of A are used when the scratch holds it.
+static int fused_nc(int n);
+static bool tiled_engine_allowed(int n) {
+    static const bool onepass = [] {
+        const char* v = getenv("LLS_KRYLOV");
+        return v && v[0] == 'o';   // LLS_KRYLOV=onepass: the one-pass engine for CGLS, n <= 4096
+    }();
+    return onepass && fused_nc(n) > 0;
+}
+
+size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass) {
     if (grid <= 0) {
         int sms = sm_count();
         grid = kMaxGridPerSm * (sms > 0 ? sms : 160);
     }
-    return k_layout(m, n, grid).total;
+    return k_layout(m, n, grid, one_pass && tiled_engine_allowed(n)).total;
 }
 
 static int fused_nc(int n) {
@@ -979,8 +1060,15 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     }
     if (grid < 1) grid = 1;
     if (grid > maxg) grid = maxg;
-    KLayout L = k_layout(c.m, c.n, grid);
+    KLayout L = k_layout(c.m, c.n, grid, NC > 0);
     if (L.total > c.scratch_bytes) return LLS_ERR_WORKSPACE;
+    a.At = nullptr;
+    if (NC > 0) {
+        a.At = reinterpret_cast<const float4*>(base + L.off_tile);
+        dim3 tg(ceil_div(ceil_div(c.m, kRB), 64), ceil_div(c.n, 32));
+        tile_rows_kernel<<<tg, 256, 0, st>>>(c.A, c.lda, c.m, c.n, const_cast<float4*>(a.At), a.aligned16);
+        LLS_LAUNCH_CHECK("tile_rows", st);
+    }
     a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
     a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);
     a.s = (double*)(base + L.off_s); a.u = (double*)(base + L.off_u); a.d = (double*)(base + L.off_d);
@@ -1001,8 +1089,11 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     const bool lsqr = c.method == LLS_KRYLOV_LSQR;
     const int sms = sm_count();
     if (sms <= 0) return LLS_ERR_CUDA;
-    static const bool want_fused = getenv("LLS_KRYLOV_FUSED") != nullptr;
-    const int nc = (want_fused && !lsqr) ? fused_nc(c.n) : 0;
+    int nc = (!lsqr && tiled_engine_allowed(c.n)) ? fused_nc(c.n) : 0;
+    if (nc > 0) {   // the one-pass engine needs its copy of A in the scratch
+        const int maxg = kMaxGridPerSm * sms;
+        if (k_layout(c.m, c.n, maxg, true).total > c.scratch_bytes) nc = 0;
+    }
     KArgs a;
     a.m = c.m; a.n = c.n; a.lda = c.lda; a.A = c.A; a.b = c.b; a.x = c.x;
     a.M = c.Minv; a.Mt = c.Mt;
@@ -1056,6 +1147,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     if (grid > maxg) grid = maxg;
     KLayout L = k_layout(c.m, c.n, grid);
     if (L.total > c.scratch_bytes) return LLS_ERR_WORKSPACE;
+    a.At = nullptr;
     char* base = (char*)c.scratch;
     a.r = (double*)(base + L.off_r); a.q = (double*)(base + L.off_q);
     a.t = (double*)(base + L.off_t); a.p = (double*)(base + L.off_p);

@@ -360,6 +360,9 @@ static int launch_panel(PanelArgs& a, cudaStream_t st) {
 
 int panel_qr(const PanelCall& c, cudaStream_t st) {
     if (c.b < 1 || c.b > 32) return LLS_ERR_UNSUPPORTED;
+    // one-level tree when the stacked leaf R factors fit one block (panel_flat.cu)
+    const int flat = panel_flat_qr(c, st);
+    if (flat != LLS_ERR_UNSUPPORTED) return flat;
     PanelArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;

@@ -1,0 +1,446 @@
+// Tall-skinny panel QR with a one-level tree: communication-avoiding QR (Eq. caqr,
+// Sec. 3.1.3) with CGS2 leaves, for panels whose stacked leaf R factors fit one 1024-row
+// block (P0 * b <= 1024; at b = 16 every m <= 65536).
+//
+//  1. (Eq. caqr, circled 1) each of P0 CTAs factors a row block of at most RL * 256 rows by
+//     CGS2, RL rows per thread in registers; its Q goes to shared memory and its b x b R to
+//     the workspace.
+//  2. One bounded grid barrier (cooperative launch: all CTAs are resident).
+//  3. (circled 2-3) every CTA loads the P0 stacked R factors and factors the stack with the
+//     same code in the same order, so each CTA holds the tree's Q without a second exchange
+//     through memory. CTA 0 writes R.
+//  4. (circled 4-5) each CTA multiplies its block's Q by its b x b slice of the tree's Q and
+//     stores the result: FP32 to W and, rounded to nearest even, to the product-precision
+//     copy Wh.
+//
+// CGS2 runs in the lagged one-reduction form: one CTA-wide reduction per column gives the
+// second-pass coefficients of column k against q_<k, ||a_k'||^2, the first-pass coefficients
+// of column k+1 against q_<k and a_k'^T a_{k+1}, and the first-pass coefficient of column
+// k+1 against q_k follows as (a_k'^T a_{k+1} - h2^T g) / R_kk. Every column is still
+// orthogonalised twice; in exact arithmetic Q and R are those of CGS2. The column loop is
+// unrolled in groups of four columns, so every register index is a constant and each step
+// forms at most three products it does not need.
+#include "cgs2.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <stdlib.h>
+
+namespace lls {
+namespace {
+
+constexpr int kFT = 256;            // threads per CTA
+constexpr int kFW = kFT / 32;       // warps per CTA
+constexpr int kRootRPT = 4;         // stacked rows per thread in the tree factorization
+constexpr int kStackRows = kRootRPT * kFT;
+
+struct FlatArgs {
+    float* W; int ldw;
+    void* Wh; int ldh;
+    float* R; int ldr;
+    int m, c0, b, P0, lowp;
+    float* rbuf;            // P0 row-major B x B blocks: the leaf R factors
+    unsigned* bar;          // [0] arrivals, [1] departures: zero on entry, reset by the last CTA
+    int* err;
+};
+
+template <int B>
+struct FlatSmem {
+    float red[2][2][kFW][32];            // partial sums: 2 alternating buffers x 2 chunks of 32
+    float tot[kFW][64];                  // per-warp copy of the CTA totals
+    float Rs[B][B + 1];                  // R of the current factorization
+    __align__(16) float S[B][B];         // this block's slice of the tree's Q
+    int ok;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// CTA-wide sums of the N (<= 64) values x[] held by every thread. Returns this warp's row of
+// `tot`, whose entries 0..N-1 hold the CTA totals. One barrier; `red` alternates between
+// two buffers, so the next call may start writing before every warp has read this one.
+template <int N, int B>
+__device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<B>& sm, int& parity) {
+    static_assert(N >= 1 && N <= 64, "block_sum handles at most 64 values");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int N0 = N < 32 ? N : 32;
+    constexpr int S0 = pow2ceil(N0);
+    float c0[S0];
+#pragma unroll
+    for (int i = 0; i < S0; ++i) c0[i] = i < N0 ? x[i] : 0.f;
+    sm.red[parity][0][warp][lane] = warp_transpose_reduce<S0>(c0);
+    if constexpr (N > 32) {
+        constexpr int S1 = pow2ceil(N - 32);
+        float c1[S1];
+#pragma unroll
+        for (int i = 0; i < S1; ++i) c1[i] = 32 + i < N ? x[32 + i] : 0.f;
+        sm.red[parity][1][warp][lane] = warp_transpose_reduce<S1>(c1);
+    }
+    __syncthreads();
+    float t0 = 0.f;
+#pragma unroll
+    for (int q = 0; q < kFW; ++q) t0 += sm.red[parity][0][q][lane];
+    sm.tot[warp][lane] = t0;
+    if constexpr (N > 32) {
+        float t1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < kFW; ++q) t1 += sm.red[parity][1][q][lane];
+        sm.tot[warp][32 + lane] = t1;
+    }
+    parity ^= 1;
+    __syncwarp();
+    return sm.tot[warp];
+}
+
+// Steps K = K0 .. K0 + KG - 1 of the lagged CGS2 on the register block v (R rows per thread,
+// columns 0..B-1; before step K, columns < K hold q_0..q_{K-1}, column K holds a_K after its
+// first projection, the rest are raw). Afterwards column K holds q_K and column K+1 its first
+// projection. Rs row j, column K accumulates R_jK (first-pass part written at step K-1,
+// second-pass part added at step K).
+// The KG steps of a group share one body (a runtime loop): they form the products of the
+// group's widest step, with the columns not yet orthogonalised masked to zero, and pick the
+// current and next columns by register selects. Sharing bodies keeps the kernel's code
+// small enough for the instruction cache at a cost of at most KG - 1 extra products.
+template <int B, int R, int K0, int KG>
+__device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+    constexpr int NQ = K0 + KG - 1;              // q columns any step of the group may use
+    constexpr int N = 2 * NQ + 2;                // h2[NQ], nn, g[NQ], c
+#pragma unroll 1
+    for (int s = 0; s < KG; ++s) {
+        const int K = K0 + s;
+        if (K >= b) return;
+        float cur[R], nx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float c = v[r][K0], d = K0 + 1 < B ? v[r][K0 + 1] : 0.f;
+#pragma unroll
+            for (int u = 1; u < KG; ++u) {
+                c = s == u ? v[r][K0 + u] : c;
+                d = s == u ? (K0 + u + 1 < B ? v[r][(K0 + u + 1) % B] : 0.f) : d;
+            }
+            cur[r] = c;
+            nx[r] = d;
+        }
+        float x[N];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            float p1 = 0.f, p2 = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                p1 = fmaf(v[r][j], cur[r], p1);
+                p2 = fmaf(v[r][j], nx[r], p2);
+            }
+            x[j] = j < K ? p1 : 0.f;
+            x[NQ + 1 + j] = j < K ? p2 : 0.f;
+        }
+        {
+            float p1 = 0.f, p2 = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                p1 = fmaf(cur[r], cur[r], p1);
+                p2 = fmaf(cur[r], nx[r], p2);
+            }
+            x[NQ] = p1;
+            x[2 * NQ + 1] = p2;
+        }
+        const float* t = block_sum<N, B>(x, sm, parity);
+
+        float h2[NQ > 0 ? NQ : 1], g[NQ > 0 ? NQ : 1];
+        float hh = 0.f, hg = 0.f;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            h2[j] = t[j];                        // zero for j >= K (masked products)
+            g[j] = t[NQ + 1 + j];
+            hh = fmaf(h2[j], h2[j], hh);
+            hg = fmaf(h2[j], g[j], hg);
+        }
+        const float nn = t[NQ];
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float a = cur[r];
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) a = fmaf(-v[r][j], h2[j], a);
+            acc[r] = a;
+        }
+        float normsq = nn - hh;
+        if (!(normsq >= 0.25f * nn)) {   // the second pass removed much of the norm: reduce it directly
+            float d[1];
+            d[0] = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[0] = fmaf(acc[r], acc[r], d[0]);
+            normsq = block_sum<1, B>(d, sm, parity)[0];
+        }
+        const float nrm = sqrtf(fmaxf(normsq, 0.f));
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        const bool next = K + 1 < b;           // column K+1 exists (then K+1 < B)
+        const float gq = next ? (t[2 * NQ + 1] - hg) * inv : 0.f;   // q_K^T a_{K+1}
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane < K) {
+                sm.Rs[lane][K] += t[lane];
+                if (next) sm.Rs[lane][K + 1] = t[NQ + 1 + lane];
+            }
+            if (lane == 0) {
+                sm.Rs[K][K] = nrm;
+                if (next) sm.Rs[K][K + 1] = gq;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float q = acc[r] * inv;
+            float a = nx[r];
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) a = fmaf(-v[r][j], g[j], a);
+            a = fmaf(-q, gq, a);
+#pragma unroll
+            for (int u = 0; u < KG; ++u) {
+                if (s == u) v[r][K0 + u] = q;
+                if (K0 + u + 1 < B && s == u) v[r][(K0 + u + 1) % B] = a;
+            }
+        }
+    }
+}
+
+template <int B, int R, int K0>
+struct Cgs2Flat {
+    static constexpr int KG = 4;
+    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+        if (K0 >= b) return;
+        cgs2_group<B, R, K0, KG>(v, b, sm, parity);
+        Cgs2Flat<B, R, K0 + KG>::run(v, b, sm, parity);
+    }
+};
+template <int B, int R>
+struct Cgs2Flat<B, R, B> {
+    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&) {}
+};
+
+__device__ __forceinline__ void flat_leaf_range(int m, int P0, int i, int& s, int& e) {
+    const int base = m / P0, extra = m % P0;
+    s = i * base + min(i, extra);
+    e = s + base + (i < extra ? 1 : 0);
+}
+
+__device__ __forceinline__ void flat_store_q(const FlatArgs& a, int row, int j, float q) {
+    a.W[(size_t)row + (size_t)(a.c0 + j) * a.ldw] = q;
+    const size_t h = (size_t)row + (size_t)(a.c0 + j) * a.ldh;
+    if (a.lowp == 0) reinterpret_cast<__half*>(a.Wh)[h] = __float2half_rn(q);
+    else if (a.lowp == 1) reinterpret_cast<__nv_bfloat16*>(a.Wh)[h] = __float2bfloat16_rn(q);
+}
+
+template <int B>
+__device__ __forceinline__ void flat_write_r(const FlatArgs& a, const FlatSmem<B>& sm) {
+    for (int i = threadIdx.x; i < a.b * a.b; i += kFT) {
+        const int r = i % a.b, c = i / a.b;
+        a.R[(size_t)(a.c0 + r) + (size_t)(a.c0 + c) * a.ldr] = r <= c ? sm.Rs[r][c] : 0.f;
+    }
+}
+
+template <int B, int RL>
+__global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
+    extern __shared__ __align__(16) unsigned char flat_smem[];
+    FlatSmem<B>& sm = *reinterpret_cast<FlatSmem<B>*>(flat_smem);
+    float* Ql = reinterpret_cast<float*>(flat_smem + sizeof(FlatSmem<B>));   // [RL * kFT][B + 1]
+    const int t = threadIdx.x, b = a.b;
+    int parity = 0;
+    for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
+    for (int i = t; i < B * B; i += kFT) (&sm.S[0][0])[i] = 0.f;
+    int s, e;
+    flat_leaf_range(a.m, a.P0, blockIdx.x, s, e);
+    const int rows = e - s;
+
+    float v[RL][B];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+        const int lr = t + r * kFT;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            v[r][j] = (lr < rows && j < b) ? a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] : 0.f;
+    }
+    __syncthreads();
+    Cgs2Flat<B, RL, 0>::run(v, b, sm, parity);
+    __syncthreads();
+
+    if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            const int lr = t + r * kFT;
+            if (lr >= rows) continue;
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j < b) flat_store_q(a, s + lr, j, v[r][j]);
+        }
+        flat_write_r<B>(a, sm);
+        return;
+    }
+
+    // leaf Q to shared memory, leaf R to the workspace
+#pragma unroll
+    for (int r = 0; r < RL; ++r)
+#pragma unroll
+        for (int j = 0; j < B; ++j) Ql[(t + r * kFT) * (B + 1) + j] = v[r][j];
+    float* rb = a.rbuf + (size_t)blockIdx.x * (B * B);
+    for (int i = t; i < B * B; i += kFT) rb[i] = sm.Rs[i / B][i % B];
+    __threadfence();
+    __syncthreads();
+    for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
+
+    // bounded grid barrier: every leaf R is in the workspace
+    if (t == 0) {
+        atomicAdd(a.bar, 1u);
+        int ok = 1;
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u32(a.bar) < (unsigned)a.P0) {
+            if (globaltimer_ns() - t0 > kSpinLimitNs) {
+                atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        sm.ok = ok;
+    }
+    __syncthreads();
+
+    if (sm.ok) {
+        // the stacked R factors: stacked row rho = child * b + rr
+        const int srows = a.P0 * b;
+        float vr[kRootRPT][B];
+#pragma unroll
+        for (int r = 0; r < kRootRPT; ++r) {
+            const int rho = t + r * kFT;
+            const int child = rho / b, rr = rho - child * b;
+            const float* src = a.rbuf + (size_t)child * (B * B) + rr * B;
+#pragma unroll
+            for (int j = 0; j < B; ++j) vr[r][j] = (rho < srows && j < b) ? __ldcg(src + j) : 0.f;
+        }
+        Cgs2Flat<B, kRootRPT, 0>::run(vr, b, sm, parity);
+        // this block's b x b slice of the tree's Q
+#pragma unroll
+        for (int r = 0; r < kRootRPT; ++r) {
+            const int rho = t + r * kFT;
+            const int rr = rho - (int)blockIdx.x * b;
+            if (rr >= 0 && rr < b)
+#pragma unroll
+                for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) flat_write_r<B>(a, sm);
+        // Q = Q_leaf * S
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            const int lr = t + r * kFT;
+            if (lr >= rows) continue;
+            float q[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) q[k] = Ql[lr * (B + 1) + k];
+            float o[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) o[j] = 0.f;
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const float4* Sk = reinterpret_cast<const float4*>(&sm.S[k][0]);
+#pragma unroll
+                for (int j4 = 0; j4 < B / 4; ++j4) {
+                    const float4 s4 = Sk[j4];
+                    o[4 * j4 + 0] = fmaf(q[k], s4.x, o[4 * j4 + 0]);
+                    o[4 * j4 + 1] = fmaf(q[k], s4.y, o[4 * j4 + 1]);
+                    o[4 * j4 + 2] = fmaf(q[k], s4.z, o[4 * j4 + 2]);
+                    o[4 * j4 + 3] = fmaf(q[k], s4.w, o[4 * j4 + 3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (j < b) flat_store_q(a, s + lr, j, o[j]);
+        }
+    }
+
+    // departure: the last CTA out resets the barrier words for the next panel
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(a.bar + 1, 1u) == (unsigned)(a.P0 - 1)) {
+            atomicExch(a.bar, 0u);
+            atomicExch(a.bar + 1, 0u);
+        }
+    }
+}
+
+template <int B, int RL>
+constexpr size_t flat_smem_bytes() {
+    return sizeof(FlatSmem<B>) + (size_t)RL * kFT * (B + 1) * sizeof(float);
+}
+
+// Per device: the dynamic shared memory opt-in and the co-resident CTA capacity.
+template <int B, int RL>
+static int flat_prepare(int& capacity) {
+    constexpr int kMaxDev = 64;
+    static int cap[kMaxDev];
+    static bool done[kMaxDev];
+    int dev = 0;
+    LLS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) return LLS_ERR_UNSUPPORTED;
+    if (!done[dev]) {
+        const size_t smem = flat_smem_bytes<B, RL>();
+        LLS_CUDA_TRY(cudaFuncSetAttribute(panel_flat_kernel<B, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        int sms = 0, per = 0;
+        LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_flat_kernel<B, RL>, kFT, smem));
+        cap[dev] = sms * per;
+        done[dev] = true;
+    }
+    capacity = cap[dev];
+    return LLS_OK;
+}
+
+template <int B, int RL>
+static int launch_flat(FlatArgs& a, cudaStream_t st) {
+    int cap = 0;
+    LLS_TRY((flat_prepare<B, RL>(cap)));
+    if (a.P0 > cap) return LLS_ERR_UNSUPPORTED;
+    const size_t smem = flat_smem_bytes<B, RL>();
+    if (a.P0 == 1) {
+        panel_flat_kernel<B, RL><<<1, kFT, smem, st>>>(a);
+    } else {
+        void* args[] = {&a};
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL>, dim3(a.P0), dim3(kFT), args,
+                                                 smem, st));
+    }
+    LLS_LAUNCH_CHECK("panel_flat", st);
+    return LLS_OK;
+}
+
+bool flat_disabled() {
+    static const bool off = [] {
+        const char* s = getenv("LLS_PANEL");
+        return s && s[0] == 't';   // LLS_PANEL=tree: always the multi-level kernel
+    }();
+    return off;
+}
+
+}  // namespace
+
+// Returns LLS_ERR_UNSUPPORTED (nothing launched) when the panel needs a deeper tree.
+int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
+    if (flat_disabled() || c.b < 1 || c.b > 16) return LLS_ERR_UNSUPPORTED;
+    FlatArgs a;
+    a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
+    a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
+    a.rbuf = c.rbuf; a.bar = c.cnt; a.err = c.err;
+    const int p2 = ceil_div(c.m, 2 * kFT), p4 = ceil_div(c.m, 4 * kFT);
+    int rl;
+    if (c.m <= 2 * kFT) { rl = 2; a.P0 = 1; }
+    else if (c.m <= 4 * kFT) { rl = 4; a.P0 = 1; }
+    else if (p2 * c.b <= kStackRows) { rl = 2; a.P0 = p2; }
+    else if (p4 * c.b <= kStackRows) { rl = 4; a.P0 = p4; }
+    else return LLS_ERR_UNSUPPORTED;
+    if (c.b <= 8) return rl == 2 ? launch_flat<8, 2>(a, st) : launch_flat<8, 4>(a, st);
+    return rl == 2 ? launch_flat<16, 2>(a, st) : launch_flat<16, 4>(a, st);
+}
+
+}  // namespace lls

@@ -98,29 +98,31 @@ def test_graph_replay_matches_direct_path():
     assert launches[0] == launches[1] == launches[2] > 10
 
 
-def test_fused_engine_matches_oracle():
-    # The single-pass CGLS engine (selected with LLS_KRYLOV_FUSED; the choice is read once per
-    # process, so it runs in a fresh process) against the oracle.
+def test_one_pass_engine_matches_oracle():
+    # The one-pass CGLS engine (A t, A^T q and A^T r from one read of a row-block copy of A;
+    # chosen with LLS_KRYLOV=onepass, read once per process, so it runs in a fresh process)
+    # against the oracle.
     import os
     import subprocess
     import sys
     code = (
         "import sys, json, torch, numpy as np; sys.path.insert(0, %r);"
         "from paper_1912_05508_gb300 import lls, synth;"
-        "p = synth.svd_lls(1500, 96, 'geometric', 1e3, seed=41);"
+        "p = synth.svd_lls(1501, 96, 'geometric', 1e3, seed=41);"
         "x, info = lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda());"
         "np.save(sys.argv[1], x.cpu().numpy()); print(json.dumps(info))"
     ) % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     import tempfile
     out = os.path.join(tempfile.mkdtemp(), "x.npy")
-    env = dict(os.environ, LLS_KRYLOV_FUSED="1")
+    env = dict(os.environ, LLS_KRYLOV="onepass")
     r = subprocess.run([sys.executable, "-c", code, out], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     import json
     info = json.loads(r.stdout.strip().splitlines()[-1])
     assert info["status"] == 0
-    assert info["a_passes"] == info["iters"] + 3       # one pass over A per iteration
-    p = synth.svd_lls(1500, 96, "geometric", 1e3, seed=41)
+    # the row-block copy of A (read + write), A^T b, one pass per iteration, final A x and A^T r
+    assert info["a_passes"] == info["iters"] + 5
+    p = synth.svd_lls(1501, 96, "geometric", 1e3, seed=41)
     x = np.load(out)
     assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
     assert metrics.forward_error(x, direct.lls(p.A, p.b)) <= 10 * p.kappa * 1e-12

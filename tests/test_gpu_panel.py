@@ -46,7 +46,11 @@ def graded(m, b, seed, kappa):
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
 @pytest.mark.parametrize("m,b,kappa", [(1, 1, 1.0), (16, 16, 10.0), (1000, 7, 1e2), (1024, 16, 1e3),
                                        (1025, 32, 1e3), (4099, 13, 1e4), (32771, 16, 1e3),
-                                       (70000, 32, 1e5)])
+                                       (70000, 32, 1e5),
+                                       # one-level tree: 512-row leaves, stack of exactly 1024 rows
+                                       (32768, 16, 1e3), (512, 16, 1e2), (513, 9, 1e2),
+                                       # one-level tree with 1024-row leaves; deeper tree beyond
+                                       (65536, 16, 1e4), (65537, 8, 1e2), (150000, 16, 1e3)])
 def test_panel_matches_oracle_tsqr(prec, m, b, kappa):
     A = graded(m, b, m + b, kappa)
     W, Wh, R = panel(A, prec)

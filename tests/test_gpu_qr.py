@@ -50,8 +50,12 @@ def test_fp32_products_match_householder(m, n):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
-@pytest.mark.parametrize("m,n,pw", [(1000, 100, 32), (2048, 256, 32), (777, 96, 16)])
+@pytest.mark.parametrize("m,n,pw", [(1000, 100, 32), (2048, 256, 32), (777, 96, 16),
+                                    # narrow nodes as single cooperative launches over many CTAs
+                                    (20000, 96, 16), (9000, 72, 8)])
 def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
+    if prec == "fp8" and pw % 16:
+        pytest.skip("FP8 products take panel widths that are multiples of 16")
     kappa = 1e3
     A = svd_matrix(m, n, kappa, seed=3 * m + n)
     Q, R = gpu_qr(A, prec, pw)
