@@ -172,7 +172,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t accb = smem_u32(bars + 2 * kTcStages);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
+    // The update walks N fastest: the CTAs that share one 128-row tile of Q1 (the larger
+    // operand) run together and read it once from DRAM, then from L2.
+    const int m0 = (EPI == TC_EPI_UPDATE ? blockIdx.y : blockIdx.x) * kTcBM;
+    const int n0 = (EPI == TC_EPI_UPDATE ? blockIdx.x : blockIdx.y) * BN;
     const int kt_total = (a.K + kKe - 1) / kKe;
     const int kt0 = blockIdx.z * a.k_tiles_per_split;
     const int kt1 = min(kt_total, kt0 + a.k_tiles_per_split);
@@ -451,7 +454,7 @@ int gemm_update(const UpdCall& c, cudaStream_t st) {
         a.M = c.m; a.N = c.w2; a.K = c.w1; a.k_tiles_per_split = ceil_div(c.w1, 2 * kTcBK);
         a.idesc = make_idesc(2, bn, false);
         a.out = c.A2; a.ldo = c.ldw; a.fexp = c.f; a.err = c.err;
-        dim3 grid(ceil_div(c.m, kTcBM), ceil_div(c.w2, bn), 1);
+        dim3 grid(ceil_div(c.w2, bn), ceil_div(c.m, kTcBM), 1);
         return launch_bn<false, TC_EPI_UPDATE, true>(bn, tA, tB, a, grid, st);
     }
     CUtensorMap tA, tB;
@@ -461,7 +464,7 @@ int gemm_update(const UpdCall& c, cudaStream_t st) {
     a.M = c.m; a.N = c.w2; a.K = c.w1; a.k_tiles_per_split = ceil_div(c.w1, kTcBK);
     a.idesc = make_idesc(c.lowp, bn, true);
     a.out = c.A2; a.ldo = c.ldw; a.fexp = c.f; a.err = c.err;
-    dim3 grid(ceil_div(c.m, kTcBM), ceil_div(c.w2, bn), 1);
+    dim3 grid(ceil_div(c.w2, bn), ceil_div(c.m, kTcBM), 1);
     return launch_bn<true, TC_EPI_UPDATE>(bn, tA, tB, a, grid, st);
 }
 

@@ -42,6 +42,7 @@ constexpr int kColChunk = 64;     // columns per A t work item
 constexpr int kRowChunk = 2048;   // rows per A^T r work item (staged in shared memory)
 constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
 constexpr int kMaxRestarts = 3;
+constexpr int kPrefetchCols = 8;  // L2 prefetch distance of the A passes (columns, or 32-lane steps)
 constexpr int kNPart = 4;         // block-partial slots
 
 struct KArgs {
@@ -63,6 +64,8 @@ struct KArgs {
     double *v1part, *v2part;     // fused engine: per-CTA partial A^T q and A^T r, [grid][n]
     int aligned16;               // A and lda allow 16-byte copies of 4-row column segments
     const float4* At;            // row-block copy of A: At[blk * n + j] = A[4 blk .. 4 blk + 3, j], or null
+    float2 *rdf, *tdf, *udf, *pdf;   // double-float copies (hi, lo) of r, t, u, p, written where the
+                                     // vectors are produced so no CTA re-splits a whole vector
     int vec_floats;              // floats reserved at the start of dynamic smem for vectors
 };
 
@@ -75,6 +78,18 @@ __device__ __forceinline__ void stage_vec(const double* __restrict__ v, int len)
         k_dsm[i] = make_float2(hi, lo);
     }
     __syncthreads();
+}
+
+// Copy a vector already split into double-float pairs into shared memory.
+__device__ __forceinline__ void stage_df(const float2* __restrict__ v, int len) {
+    for (int i = threadIdx.x; i < len; i += kKThreads) k_dsm[i] = __ldcg(v + i);
+    __syncthreads();
+}
+
+__device__ __forceinline__ float2 to_df(double v) {
+    float2 r;
+    split_df(v, r.x, r.y);
+    return r;
 }
 
 // Sum of one double per thread over the block, written to slot (k, blockIdx.x).
@@ -106,9 +121,27 @@ __device__ __forceinline__ double grid_total(const double* bpart, int k) {
     return r;
 }
 
+// sum_{k < count} p[k * stride] in a fixed order: four interleaved accumulators (k mod 4),
+// combined as (s0 + s1) + (s2 + s3), so four loads are in flight at a time.
+__device__ __forceinline__ double sum_parts(const double* __restrict__ p, int count, size_t stride) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 3 < count; k += 4) {
+        s0 += __ldcg(p + (size_t)k * stride);
+        s1 += __ldcg(p + (size_t)(k + 1) * stride);
+        s2 += __ldcg(p + (size_t)(k + 2) * stride);
+        s3 += __ldcg(p + (size_t)(k + 3) * stride);
+    }
+    if (k < count) s0 += __ldcg(p + (size_t)k * stride);
+    if (k + 1 < count) s1 += __ldcg(p + (size_t)(k + 1) * stride);
+    if (k + 2 < count) s2 += __ldcg(p + (size_t)(k + 2) * stride);
+    return (s0 + s1) + (s2 + s3);
+}
+
 // out_c = sum over r in [lo(c), hi(c)) of X[r + c n] * v_r, v staged in k_dsm.
 // upper: rows 0..c (column c of an upper-triangular X); lower: rows c..n-1.
-__device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, double* __restrict__ out) {
+__device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, double* __restrict__ out,
+                          float2* __restrict__ outdf = nullptr) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kKWarps + (threadIdx.x >> 5), nw = gridDim.x * kKWarps;
     double sq = 0.0;
@@ -121,7 +154,11 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
             dot2_step(s, cc, __ldg(col + r), v.x, v.y);
         }
         double val = warp_sum_d(join_df(s, cc));
-        if (lane == 0) { out[c] = val; sq += val * val; }
+        if (lane == 0) {
+            out[c] = val;
+            if (outdf) outdf[c] = to_df(val);
+            sq += val * val;
+        }
     }
     return sq;
 }
@@ -143,6 +180,10 @@ __device__ void a_times_partials(const KArgs& a) {
             const size_t step = (size_t)a.lda / 4;
 #pragma unroll 4
             for (int j = j0; j < j1; ++j) {
+                // pull column j + 8 of this thread's rows into L2 (deepens the loads in flight
+                // beyond the unrolled register loads)
+                if (j + kPrefetchCols < j1)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(colp + (size_t)(j + kPrefetchCols) * step));
                 const float4 v = __ldg(colp + (size_t)j * step);
                 const float2 t = k_dsm[j];
                 dot2_step(s0, c0, v.x, t.x, t.y);
@@ -170,17 +211,22 @@ __device__ void a_times_partials(const KArgs& a) {
 
 // upart[rc][j] = sum_{i in row chunk rc} A[i, j] * v_i for v (length m) in global memory.
 // v's chunk is staged in shared memory; each lane reads 4 consecutive rows per step.
-__device__ void at_times_partials(const KArgs& a, const double* __restrict__ v) {
+__device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
+                                  const float2* __restrict__ vdf = nullptr) {
     const int items = a.nrc * a.ncg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int rc = it % a.nrc, cg = it / a.nrc;
         const int r0 = rc * kRowChunk, rows = min(a.m - r0, kRowChunk);
         __syncthreads();
-        for (int i = threadIdx.x; i < rows; i += kKThreads) {
-            float hi, lo;
-            split_df(__ldcg(v + r0 + i), hi, lo);
-            k_dsm[i] = make_float2(hi, lo);
+        if (vdf) {
+            for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
+        } else {
+            for (int i = threadIdx.x; i < rows; i += kKThreads) {
+                float hi, lo;
+                split_df(__ldcg(v + r0 + i), hi, lo);
+                k_dsm[i] = make_float2(hi, lo);
+            }
         }
         __syncthreads();
         const bool full = a.aligned16 && rows == kRowChunk;
@@ -193,6 +239,8 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v) 
                 const float4* col4 = reinterpret_cast<const float4*>(col);
 #pragma unroll 4
                 for (int q = lane; q < kRowChunk / 4; q += 32) {
+                    if (q + 32 * kPrefetchCols < kRowChunk / 4)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(col4 + q + 32 * kPrefetchCols));
                     const float4 av = __ldg(col4 + q);
                     const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
                     dot2_step(s0, c0, av.x, w0.x, w0.y);
@@ -303,7 +351,14 @@ __device__ void fused_pass(const KArgs& a, const double* __restrict__ tvec, cons
     for (int c = 0; c < NC; ++c) {
         const int j = t + c * kKThreads;
         th[c] = tl[c] = 0.f;
-        if (doA && j < a.n) split_df(__ldcg(tvec + j), th[c], tl[c]);
+        if (doA && j < a.n) {
+            if (tvec == a.t) {
+                const float2 d = __ldcg(a.tdf + j);
+                th[c] = d.x; tl[c] = d.y;
+            } else {
+                split_df(__ldcg(tvec + j), th[c], tl[c]);
+            }
+        }
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) v1s[p] = v1c[p] = v2s[p] = v2c[p] = z2;
@@ -430,7 +485,12 @@ cgls_kernel(KArgs a) {
         // ---- true residual r = b - A x ----
         if (xzero) {
             double sq = 0.0;
-            for (int i = gtid; i < a.m; i += gthreads) { double bi = a.b[i]; a.r[i] = bi; sq += bi * bi; }
+            for (int i = gtid; i < a.m; i += gthreads) {
+                const double bi = a.b[i];
+                a.r[i] = bi;
+                a.rdf[i] = to_df(bi);
+                sq += bi * bi;
+            }
             block_partial(sq, a.bpart, 0);
             for (int j = gtid; j < a.n; j += gthreads) a.x[j] = 0.0;
         } else {
@@ -443,6 +503,7 @@ cgls_kernel(KArgs a) {
                 for (int i = gtid; i < a.m; i += gthreads) {
                     double ri = a.b[i] - __ldcg(a.q + i);
                     a.r[i] = ri;
+                    a.rdf[i] = to_df(ri);
                     sq += ri * ri;
                 }
                 block_partial(sq, a.bpart, 0);
@@ -454,9 +515,10 @@ cgls_kernel(KArgs a) {
                 double sq = 0.0;
                 for (int i = gtid; i < a.m; i += gthreads) {
                     double ax = 0.0;
-                    for (int cc = 0; cc < a.nck; ++cc) ax += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                    ax += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
                     double ri = a.b[i] - ax;
                     a.r[i] = ri;
+                    a.rdf[i] = to_df(ri);
                     sq += ri * ri;
                 }
                 block_partial(sq, a.bpart, 0);
@@ -470,7 +532,7 @@ cgls_kernel(KArgs a) {
             double dummy = 0.0;
             fused_pass<NC>(a, nullptr, a.r, false, false, true, dummy);
         } else {
-            at_times_partials(a, a.r);
+            at_times_partials(a, a.r, a.rdf);
         }
         ++apasses;
         KB_SYNC();
@@ -481,8 +543,9 @@ cgls_kernel(KArgs a) {
             } else {
                 for (int j = gtid; j < a.n; j += gthreads) {
                     double v = 0.0;
-                    for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                    v += sum_parts(a.upart + j, a.nrc, (size_t)a.n);
                     a.u[j] = v;
+                    a.udf[j] = to_df(v);
                     sq += v * v;
                 }
             }
@@ -494,7 +557,8 @@ cgls_kernel(KArgs a) {
         KB_SYNC();
         un2 = grid_total(a.bpart, 1);
         xn2 = grid_total(a.bpart, 3);
-        stage_vec(a.u, a.n);
+        if constexpr (NC > 0) stage_vec(a.u, a.n);
+        else stage_df(a.udf, a.n);
         block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
         ++mpasses;
         KB_SYNC();
@@ -507,14 +571,18 @@ cgls_kernel(KArgs a) {
         const double crit = a.target == LLS_TARGET_FP64 ? eta : fwd;
         if (crit <= a.tol) { status = 0; break; }
         if (iters >= a.max_iter || restart == kMaxRestarts) { status = 1; break; }
-        for (int j = gtid; j < a.n; j += gthreads) a.p[j] = __ldcg(a.s + j);
+        for (int j = gtid; j < a.n; j += gthreads) {
+            const double pj = __ldcg(a.s + j);
+            a.p[j] = pj;
+            a.pdf[j] = to_df(pj);
+        }
         KB_SYNC();
 
         // ---- iterate ----
         while (iters < a.max_iter) {
             // t = M p
-            stage_vec(a.p, a.n);
-            tri_gemv(a.Mt, a.n, false, a.t);
+            stage_df(a.pdf, a.n);
+            tri_gemv(a.Mt, a.n, false, a.t, a.tdf);
             ++mpasses;
             KB_SYNC();
             double delta;
@@ -527,14 +595,14 @@ cgls_kernel(KArgs a) {
                 KB_SYNC();
                 delta = grid_total(a.bpart, 0);
             } else {
-                stage_vec(a.t, a.n);
+                stage_df(a.tdf, a.n);
                 a_times_partials(a);
                 ++apasses;
                 KB_SYNC();
                 double sq = 0.0;
                 for (int i = gtid; i < a.m; i += gthreads) {
                     double v = 0.0;
-                    for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                    v += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
                     a.q[i] = v;
                     sq += v * v;
                 }
@@ -553,23 +621,28 @@ cgls_kernel(KArgs a) {
                     xs += xv * xv;
                 }
                 block_partial(xs, a.bpart, 3);
-                for (int i = gtid; i < a.m; i += gthreads) a.r[i] -= alpha * __ldcg(a.q + i);
+                for (int i = gtid; i < a.m; i += gthreads) {
+                    const double ri = a.r[i] - alpha * __ldcg(a.q + i);
+                    a.r[i] = ri;
+                    a.rdf[i] = to_df(ri);
+                }
                 if constexpr (NC > 0) reduce_u(a, alpha, true, gtid, gthreads);
             }
             KB_SYNC();
             if constexpr (NC == 0) {
                 // s = M^T (A^T r) with a second pass over A
-                at_times_partials(a, a.r);
+                at_times_partials(a, a.r, a.rdf);
                 ++apasses;
                 KB_SYNC();
                 for (int j = gtid; j < a.n; j += gthreads) {
-                    double v = 0.0;
-                    for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                    const double v = sum_parts(a.upart + j, a.nrc, (size_t)a.n);
                     a.u[j] = v;
+                    a.udf[j] = to_df(v);
                 }
                 KB_SYNC();
             }
-            stage_vec(a.u, a.n);
+            if constexpr (NC > 0) stage_vec(a.u, a.n);
+            else stage_df(a.udf, a.n);
             block_partial(tri_gemv(a.M, a.n, true, a.s), a.bpart, 2);
             ++mpasses;
             KB_SYNC();
@@ -577,7 +650,11 @@ cgls_kernel(KArgs a) {
             const double xn = sqrt(grid_total(a.bpart, 3));
             const double beta = gnew / gamma;
             gamma = gnew;
-            for (int j = gtid; j < a.n; j += gthreads) a.p[j] = __ldcg(a.s + j) + beta * a.p[j];
+            for (int j = gtid; j < a.n; j += gthreads) {
+                const double pj = __ldcg(a.s + j) + beta * a.p[j];
+                a.p[j] = pj;
+                a.pdf[j] = to_df(pj);
+            }
             const double sn = sqrt(gnew);
             const double e1 = xn > 0.0 ? sn / (anorm * xn) : INFINITY;
             const double f1 = xn > 0.0 ? mnorm * sn / xn : INFINITY;
@@ -638,7 +715,7 @@ lsqr_kernel(KArgs a) {
             double sq = 0.0;
             for (int i = gtid; i < a.m; i += gthreads) {
                 double ax = 0.0;
-                for (int cc = 0; cc < a.nck; ++cc) ax += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                ax += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
                 double ri = a.b[i] - ax;
                 a.r[i] = ri;
                 sq += ri * ri;
@@ -664,7 +741,7 @@ lsqr_kernel(KArgs a) {
             double sq = 0.0;
             for (int j = gtid; j < a.n; j += gthreads) {
                 double v = 0.0;
-                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                v += sum_parts(a.upart + j, a.nrc, (size_t)a.n);
                 sq += v * v;
                 a.u[j] = v * ib;
             }
@@ -710,7 +787,7 @@ lsqr_kernel(KArgs a) {
                 double sq = 0.0;
                 for (int i = gtid; i < a.m; i += gthreads) {
                     double v = 0.0;
-                    for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * a.m + i);
+                    v += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
                     v -= alpha * a.r[i];
                     a.q[i] = v;
                     sq += v * v;
@@ -727,7 +804,7 @@ lsqr_kernel(KArgs a) {
             KB_SYNC();
             for (int j = gtid; j < a.n; j += gthreads) {
                 double v = 0.0;
-                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * a.n + j);
+                v += sum_parts(a.upart + j, a.nrc, (size_t)a.n);
                 a.u[j] = v * ib;
             }
             KB_SYNC();
@@ -855,7 +932,7 @@ adjoint_kernel(AdjArgs aa) {
         KB_SYNC();
         for (int i = gtid; i < m; i += gthreads) {
             double v = 0.0;
-            for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+            v += sum_parts(a.qpart + i, a.nck, (size_t)m);
             a.q[i] = v;
         }
         KB_SYNC();
@@ -867,7 +944,7 @@ adjoint_kernel(AdjArgs aa) {
             double pw = 0.0;
             for (int j = gtid; j < n; j += gthreads) {
                 double v = 0.0;
-                for (int rc = 0; rc < a.nrc; ++rc) v += __ldcg(a.upart + (size_t)rc * n + j);
+                v += sum_parts(a.upart + j, a.nrc, (size_t)n);
                 w[j] = v;
                 pw += v * __ldcg(a.p + j);
             }
@@ -905,7 +982,7 @@ adjoint_kernel(AdjArgs aa) {
     KB_SYNC();
     for (int i = gtid; i < m; i += gthreads) {
         double v = 0.0;
-        for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+        v += sum_parts(a.qpart + i, a.nck, (size_t)m);
         a.q[i] = aa.bvec[i] - v;
     }
     KB_SYNC();
@@ -915,7 +992,7 @@ adjoint_kernel(AdjArgs aa) {
     KB_SYNC();
     for (int i = gtid; i < m; i += gthreads) {
         double v = 0.0;
-        for (int cc = 0; cc < a.nck; ++cc) v += __ldcg(a.qpart + (size_t)cc * m + i);
+        v += sum_parts(a.qpart + i, a.nck, (size_t)m);
         aa.gb[i] = v;
     }
     KB_SYNC();
@@ -938,7 +1015,7 @@ adjoint_kernel(AdjArgs aa) {
 struct KLayout {
     int nrt, nck, nrc, ncg;
     size_t off_r, off_q, off_t, off_p, off_s, off_u, off_d, off_qpart, off_upart, off_v1, off_v2, off_bpart,
-        off_bar, off_tile, total;
+        off_bar, off_rdf, off_tdf, off_udf, off_pdf, off_tile, total;
 };
 
 // The one-pass engine streams A from a copy in 4-row blocks (tiled = true): block blk is the
@@ -964,6 +1041,10 @@ static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     L.off_v2 = take(8ull * n * grid);
     L.off_bpart = take(8ull * kNPart * grid);
     L.off_bar = take(64);
+    L.off_rdf = take(8ull * m);
+    L.off_tdf = take(8ull * n);
+    L.off_udf = take(8ull * n);
+    L.off_pdf = take(8ull * n);
     L.off_tile = tiled ? take(16ull * (size_t)ceil_div(m, kRB) * n) : 0;
     L.total = o;
     return L;
@@ -1076,6 +1157,8 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
     a.bpart = (double*)(base + L.off_bpart);
     a.bar = (unsigned*)(base + L.off_bar);
+    a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
+    a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
     a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
@@ -1156,6 +1239,8 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.v1part = (double*)(base + L.off_v1); a.v2part = (double*)(base + L.off_v2);
     a.bpart = (double*)(base + L.off_bpart);
     a.bar = (unsigned*)(base + L.off_bar);
+    a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
+    a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
     a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&aa};

@@ -148,23 +148,28 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
         }
         const float* t = block_sum<N, B>(x, sm, parity);
 
+        // two interleaved chains per sum (even / odd j) halve the dependent FMA depth
         float h2[NQ > 0 ? NQ : 1], g[NQ > 0 ? NQ : 1];
-        float hh = 0.f, hg = 0.f;
+        float hh0 = 0.f, hh1 = 0.f, hg0 = 0.f, hg1 = 0.f;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
             h2[j] = t[j];                        // zero for j >= K (masked products)
             g[j] = t[NQ + 1 + j];
-            hh = fmaf(h2[j], h2[j], hh);
-            hg = fmaf(h2[j], g[j], hg);
+            if (j & 1) { hh1 = fmaf(h2[j], h2[j], hh1); hg1 = fmaf(h2[j], g[j], hg1); }
+            else { hh0 = fmaf(h2[j], h2[j], hh0); hg0 = fmaf(h2[j], g[j], hg0); }
         }
+        const float hh = hh0 + hh1, hg = hg0 + hg1;
         const float nn = t[NQ];
         float acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            float a = cur[r];
+            float a0 = cur[r], a1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) a = fmaf(-v[r][j], h2[j], a);
-            acc[r] = a;
+            for (int j = 0; j < NQ; ++j) {
+                if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
+                else a0 = fmaf(-v[r][j], h2[j], a0);
+            }
+            acc[r] = a0 + a1;
         }
         float normsq = nn - hh;
         if (!(normsq >= 0.25f * nn)) {   // the second pass removed much of the norm: reduce it directly
@@ -174,8 +179,11 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
             for (int r = 0; r < R; ++r) d[0] = fmaf(acc[r], acc[r], d[0]);
             normsq = block_sum<1, B>(d, sm, parity)[0];
         }
-        const float nrm = sqrtf(fmaxf(normsq, 0.f));
-        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        // R_KK and 1 / R_KK from one reciprocal square root (a few ulp; the CGS2 error bound
+        // is unchanged up to the constant)
+        const float ns = fmaxf(normsq, 0.f);
+        const float inv = ns > 0.f ? rsqrtf(ns) : 0.f;
+        const float nrm = ns * inv;
         const bool next = K + 1 < b;           // column K+1 exists (then K+1 < B)
         const float gq = next ? (t[2 * NQ + 1] - hg) * inv : 0.f;   // q_K^T a_{K+1}
         if (threadIdx.x < 32) {
@@ -192,10 +200,13 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float q = acc[r] * inv;
-            float a = nx[r];
+            float a0 = nx[r], a1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) a = fmaf(-v[r][j], g[j], a);
-            a = fmaf(-q, gq, a);
+            for (int j = 0; j < NQ; ++j) {
+                if (j & 1) a1 = fmaf(-v[r][j], g[j], a1);
+                else a0 = fmaf(-v[r][j], g[j], a0);
+            }
+            const float a = fmaf(-q, gq, a0 + a1);
 #pragma unroll
             for (int u = 0; u < KG; ++u) {
                 if (s == u) v[r][K0 + u] = q;
