@@ -121,40 +121,84 @@ __device__ __forceinline__ double grid_total(const double* bpart, int k) {
     return r;
 }
 
-// sum_{k < count} p[k * stride] in a fixed order: four interleaved accumulators (k mod 4),
-// combined as (s0 + s1) + (s2 + s3), so four loads are in flight at a time.
+// sum_{k < count} p[k * stride] in a fixed order: eight interleaved accumulators (k mod 8),
+// combined pairwise, so eight loads are in flight at a time.
 __device__ __forceinline__ double sum_parts(const double* __restrict__ p, int count, size_t stride) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int k = 0;
-    for (; k + 3 < count; k += 4) {
-        s0 += __ldcg(p + (size_t)k * stride);
-        s1 += __ldcg(p + (size_t)(k + 1) * stride);
-        s2 += __ldcg(p + (size_t)(k + 2) * stride);
-        s3 += __ldcg(p + (size_t)(k + 3) * stride);
+    for (; k + 7 < count; k += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += __ldcg(p + (size_t)(k + u) * stride);
     }
-    if (k < count) s0 += __ldcg(p + (size_t)k * stride);
-    if (k + 1 < count) s1 += __ldcg(p + (size_t)(k + 1) * stride);
-    if (k + 2 < count) s2 += __ldcg(p + (size_t)(k + 2) * stride);
-    return (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (k + u < count) acc[u] += __ldcg(p + (size_t)(k + u) * stride);
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // out_c = sum over r in [lo(c), hi(c)) of X[r + c n] * v_r, v staged in k_dsm.
 // upper: rows 0..c (column c of an upper-triangular X); lower: rows c..n-1.
+// One warp per column: 16-byte loads over the aligned body of the column (two compensated
+// chains, so two loads are in flight per lane), single elements at the ragged ends, and a
+// double-float warp sum joined to FP64 once.
 __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, double* __restrict__ out,
                           float2* __restrict__ outdf = nullptr) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kKWarps + (threadIdx.x >> 5), nw = gridDim.x * kKWarps;
+    const bool vec = (n & 3) == 0 && ((uintptr_t)X & 15) == 0;
     double sq = 0.0;
     for (int c = gw; c < n; c += nw) {
         const int lo = upper ? 0 : c, hi = upper ? c + 1 : n;
         const float* col = X + (size_t)c * n;
-        float s = 0.f, cc = 0.f;
-        for (int r = lo + lane; r < hi; r += 32) {
-            float2 v = k_dsm[r];
-            dot2_step(s, cc, __ldg(col + r), v.x, v.y);
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        int blo = lo, bhi = lo;                       // aligned body [blo, bhi), multiples of 4
+        if (vec) {
+            blo = min((lo + 3) & ~3, hi);
+            bhi = max(blo, hi & ~3);
+            const float4* col4 = reinterpret_cast<const float4*>(col);
+            int q = blo / 4 + lane;
+            for (; q + 32 < bhi / 4; q += 64) {
+                const float4 a0 = __ldg(col4 + q), a1 = __ldg(col4 + q + 32);
+                const float2 v0 = k_dsm[4 * q], v1 = k_dsm[4 * q + 1], v2 = k_dsm[4 * q + 2], v3 = k_dsm[4 * q + 3];
+                const float2 w0 = k_dsm[4 * q + 128], w1 = k_dsm[4 * q + 129], w2 = k_dsm[4 * q + 130],
+                             w3 = k_dsm[4 * q + 131];
+                dot2_step(s0, c0, a0.x, v0.x, v0.y);
+                dot2_step(s1, c1, a1.x, w0.x, w0.y);
+                dot2_step(s0, c0, a0.y, v1.x, v1.y);
+                dot2_step(s1, c1, a1.y, w1.x, w1.y);
+                dot2_step(s0, c0, a0.z, v2.x, v2.y);
+                dot2_step(s1, c1, a1.z, w2.x, w2.y);
+                dot2_step(s0, c0, a0.w, v3.x, v3.y);
+                dot2_step(s1, c1, a1.w, w3.x, w3.y);
+            }
+            if (q < bhi / 4) {
+                const float4 a0 = __ldg(col4 + q);
+                const float2 v0 = k_dsm[4 * q], v1 = k_dsm[4 * q + 1], v2 = k_dsm[4 * q + 2], v3 = k_dsm[4 * q + 3];
+                dot2_step(s0, c0, a0.x, v0.x, v0.y);
+                dot2_step(s0, c0, a0.y, v1.x, v1.y);
+                dot2_step(s0, c0, a0.z, v2.x, v2.y);
+                dot2_step(s0, c0, a0.w, v3.x, v3.y);
+            }
         }
-        double val = warp_sum_d(join_df(s, cc));
+        // ragged ends: [lo, blo) and [bhi, hi) (the whole range when not vectorized)
+        {
+            const int r = lo + lane;
+            if (r < blo) {
+                const float2 v = k_dsm[r];
+                dot2_step(s1, c1, __ldg(col + r), v.x, v.y);
+            }
+            for (int r2 = bhi + lane; r2 < hi; r2 += 32) {
+                const float2 v = k_dsm[r2];
+                dot2_step(s1, c1, __ldg(col + r2), v.x, v.y);
+            }
+        }
+        float t, e;
+        two_sum(s0, s1, t, e);
+        s0 = t;
+        c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+        warp_sum_df(s0, c0);
         if (lane == 0) {
+            const double val = join_df(s0, c0);
             out[c] = val;
             if (outdf) outdf[c] = to_df(val);
             sq += val * val;

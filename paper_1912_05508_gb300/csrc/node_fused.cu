@@ -27,6 +27,8 @@ using namespace nvcuda;
 constexpr int kNT = 256;                 // threads per CTA = rows per CTA
 constexpr int kNW = kNT / 32;
 constexpr int kLdK = kNT + 8;            // halves per column of the K-contiguous tiles
+constexpr int kNodeMaxW1 = 32;           // widest left half handled here (at w1 = 64 the
+                                         // tensor-core path measured as fast)
 
 struct NodeArgs {
     float* W; int ldw;                   // FP32 work matrix: Q1 columns [c0, c0+w1), A2 after
@@ -48,15 +50,16 @@ struct NodeSmem {
     __align__(32) TL QsT[kNT][W1 + 8];   // Q1l rows: QsT[r][i]       (update operand A)
     __align__(32) TL Rl[W1][W1];         // R12l column-major         (update operand B)
     __align__(32) float Us[kNT][W1 + 4]; // update products, row-major
-    float red[kNW][32];
+    float red[2][kNW][32];               // column maxima, up to two chunks of 32 columns
     float sc[W1];                        // 2^e_j (phase B), 2^-f_j (phase D)
     float part_g[kNT];
     float colm[W1];
 };
 
-// Lane L ends with the warp-wide maximum of value index (L mod S).
+// Lane L ends with the warp-wide maximum of value index (L mod S), S <= 32.
 template <int S>
 __device__ __forceinline__ float warp_transpose_max(float (&x)[S]) {
+    static_assert(S >= 1 && S <= 32 && (S & (S - 1)) == 0, "one power-of-two chunk of at most 32 values");
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = S / 2; o >= 1; o >>= 1) {
@@ -100,15 +103,20 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
         sm.QsT[t][i] = q;
     }
     if (a.kind != 0) {
-        float mx[W1];
+        // per chunk of (up to) 32 columns: lane L ends with the warp maximum of column 32 c + L
+        constexpr int kCh = W1 < 32 ? W1 : 32;
 #pragma unroll
-        for (int j = 0; j < W1; ++j) mx[j] = fabsf(av[j]);
-        sm.red[warp][lane] = warp_transpose_max<W1>(mx);
+        for (int c = 0; c < W1 / kCh; ++c) {
+            float mx[kCh];
+#pragma unroll
+            for (int j = 0; j < kCh; ++j) mx[j] = fabsf(av[c * kCh + j]);
+            sm.red[c][warp][lane] = warp_transpose_max<kCh>(mx);
+        }
         __syncthreads();
         if (t < w2) {
             float m = 0.f;
 #pragma unroll
-            for (int q = 0; q < kNW; ++q) m = fmaxf(m, sm.red[q][t]);
+            for (int q = 0; q < kNW; ++q) m = fmaxf(m, sm.red[t / kCh][q][t % kCh]);
             atomicMax(a.colmax + cA + t, __float_as_uint(m));
         }
         if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
@@ -129,8 +137,8 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
     __syncthreads();
     using WT = typename WmmaT<TL>::type;
     constexpr int kTiles = (W1 / 16) * (W1 / 16);
-    if (warp < kTiles) {
-        const int mt = warp / (W1 / 16), nt = warp % (W1 / 16);
+    for (int tile = warp; tile < kTiles; tile += kNW) {
+        const int mt = tile / (W1 / 16), nt = tile % (W1 / 16);
         wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
         wmma::fill_fragment(acc, 0.f);
 #pragma unroll 4
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             wmma::load_matrix_sync(fb, reinterpret_cast<const WT*>(&sm.As[nt * 16][k0]), kLdK);
             wmma::mma_sync(acc, fa, fb, acc);
         }
-        float* pp = a.part + (size_t)blockIdx.x * (W1 * W1) + (size_t)(nt * 16) * W1 + mt * 16;
+        float* pp = a.part + (size_t)blockIdx.x * (W1 * W1) + (size_t)(nt * 16) * W1 + mt * 16;   // plane of W1 x W1
         wmma::store_matrix_sync(pp, acc, W1, wmma::mem_col_major);
     }
     if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
@@ -177,9 +185,14 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             if (t < w1) a.R[(size_t)(a.c0 + t) + (size_t)(cA + j) * a.ldr] = r12;
         }
         float mx = (t < w1) ? fabsf(r12) : 0.f;
-        mx = warp_max_f(mx);                      // rows 0..W1-1 live in warp 0
+        mx = warp_max_f(mx);                      // rows 0..W1-1 live in warps 0..W1/32-1
+        if (lane == 0 && warp < (W1 + 31) / 32) sm.red[0][0][warp] = mx;
+        __syncthreads();
         if (t == 0) {
-            const int fj = scale_exponent(a.kind, mx);
+            float m2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < (W1 + 31) / 32; ++q) m2 = fmaxf(m2, sm.red[0][0][q]);
+            const int fj = scale_exponent(a.kind, m2);
             a.f[j] = fj;
             sm.part_g[0] = pow2f(fj);
         }
@@ -261,11 +274,11 @@ static int launch_node(NodeArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-size_t node_fused_part_floats(int m) { return (size_t)ceil_div(m, kNT) * 32 * 32; }
+size_t node_fused_part_floats(int m) { return (size_t)ceil_div(m, kNT) * kNodeMaxW1 * kNodeMaxW1; }
 
 int node_fused(const NodeCall& c, cudaStream_t st) {
-    if ((c.lowp != 0 && c.lowp != 1) || c.w1 > 32 || c.w2 > c.w1 || c.w2 < 1) return LLS_ERR_UNSUPPORTED;
-    if ((size_t)ceil_div(c.m, kNT) * 32 * 32 > c.part_floats) return LLS_ERR_UNSUPPORTED;
+    if ((c.lowp != 0 && c.lowp != 1) || c.w1 > kNodeMaxW1 || c.w2 > c.w1 || c.w2 < 1) return LLS_ERR_UNSUPPORTED;
+    if (node_fused_part_floats(c.m) > c.part_floats) return LLS_ERR_UNSUPPORTED;
     NodeArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh;
     a.m = c.m; a.c0 = c.c0; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;

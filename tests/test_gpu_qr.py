@@ -52,7 +52,7 @@ def test_fp32_products_match_householder(m, n):
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp8"])
 @pytest.mark.parametrize("m,n,pw", [(1000, 100, 32), (2048, 256, 32), (777, 96, 16),
                                     # narrow nodes as single cooperative launches over many CTAs
-                                    (20000, 96, 16), (9000, 72, 8)])
+                                    (20000, 96, 16), (9000, 72, 8), (12000, 256, 32)])
 def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
     if prec == "fp8" and pw % 16:
         pytest.skip("FP8 products take panel widths that are multiples of 16")
@@ -80,6 +80,22 @@ def test_column_scaling_handles_wide_column_range():
     colrel = np.linalg.norm(E, axis=0) / np.linalg.norm(A.astype(np.float64), axis=0)
     assert colrel.max() <= 16 * ULOW["fp16"]
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * ULOW["fp16"]
+
+
+@pytest.mark.parametrize("pw", [16, 32])
+def test_column_scaling_in_every_node_width(pw):
+    # n = 256 puts nodes of w1 = 16/32/64 (one cooperative launch each) and w1 = 128 (the
+    # tensor-core path) into one factorization. With column norms over twelve decades (beyond
+    # FP16's range, subnormals included) a column scaled by another column's exponent loses
+    # its low-precision copy; the R12 entries of that column, and the orthogonality of the
+    # next Q, are then off by several u16 (the oracle with that mistake planted gives 5.5 and
+    # 6 u16; the oracle itself 0.1 and 0.24 u16).
+    A = synth.scaled_gaussian(9000, 256, seed=12, lo=-6.0, hi=6.0)
+    Q, R = gpu_qr(A, "fp16", pw)
+    Qo, Ro = rgsqrf.rgsqrf(A, pw, "fp16", leaf_rows=256)
+    colrel = np.linalg.norm(R - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
+    assert colrel.max() <= 2 * ULOW["fp16"]
+    assert metrics.orthogonality(Q, "2") <= 2 * ULOW["fp16"]
 
 
 def test_rank_deficient_column_gives_zero_diagonal():
