@@ -136,6 +136,28 @@ __device__ __forceinline__ double sum_parts(const double* __restrict__ p, int co
     return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
+// The same sum spread over the four lanes of an aligned lane quad (lane k of the quad takes
+// partials k, k + 4, ...); the quad combines its four sums as (s0 + s1) + (s2 + s3), so every
+// lane returns the same total in a fixed order. All 32 lanes of the warp must call it;
+// `valid` false contributes nothing.
+__device__ __forceinline__ double sum_parts_quad(const double* __restrict__ p, int count, size_t stride,
+                                                 bool valid) {
+    const int sub = threadIdx.x & 3;
+    double s0 = 0.0, s1 = 0.0;
+    if (valid) {
+        int k = sub;
+        for (; k + 4 < count; k += 8) {
+            s0 += __ldcg(p + (size_t)k * stride);
+            s1 += __ldcg(p + (size_t)(k + 4) * stride);
+        }
+        if (k < count) s0 += __ldcg(p + (size_t)k * stride);
+    }
+    double s = s0 + s1;
+    s += __shfl_xor_sync(kFullMask, s, 1);
+    s += __shfl_xor_sync(kFullMask, s, 2);
+    return s;
+}
+
 // out_c = sum over r in [lo(c), hi(c)) of X[r + c n] * v_r, v staged in k_dsm.
 // upper: rows 0..c (column c of an upper-triangular X); lower: rows c..n-1.
 // One warp per column: 16-byte loads over the aligned body of the column (two compensated
@@ -279,6 +301,8 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
             if (j >= a.n) break;
             const float* col = a.A + (size_t)j * a.lda + r0;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+            if (full && jj + 1 < kColGroup / kKWarps && j + 1 < a.n)   // the warp's next column, 4 KB
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(col + a.lda + 32 * (threadIdx.x & 31)));
             if (full) {
                 const float4* col4 = reinterpret_cast<const float4*>(col);
 #pragma unroll 4
@@ -557,13 +581,15 @@ cgls_kernel(KArgs a) {
                 ++apasses;
                 KB_SYNC();
                 double sq = 0.0;
-                for (int i = gtid; i < a.m; i += gthreads) {
-                    double ax = 0.0;
-                    ax += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
-                    double ri = a.b[i] - ax;
-                    a.r[i] = ri;
-                    a.rdf[i] = to_df(ri);
-                    sq += ri * ri;
+                for (int base = (gtid >> 5) * 8; base < a.m; base += (gthreads >> 5) * 8) {
+                    const int i = base + ((threadIdx.x & 31) >> 2);
+                    const double ax = sum_parts_quad(a.qpart + i, a.nck, (size_t)a.m, i < a.m);
+                    if ((threadIdx.x & 3) == 0 && i < a.m) {
+                        const double ri = a.b[i] - ax;
+                        a.r[i] = ri;
+                        a.rdf[i] = to_df(ri);
+                        sq += ri * ri;
+                    }
                 }
                 block_partial(sq, a.bpart, 0);
             }
@@ -585,12 +611,14 @@ cgls_kernel(KArgs a) {
             if constexpr (NC > 0) {
                 sq = reduce_u(a, 0.0, false, gtid, gthreads);
             } else {
-                for (int j = gtid; j < a.n; j += gthreads) {
-                    double v = 0.0;
-                    v += sum_parts(a.upart + j, a.nrc, (size_t)a.n);
-                    a.u[j] = v;
-                    a.udf[j] = to_df(v);
-                    sq += v * v;
+                for (int base = (gtid >> 5) * 8; base < a.n; base += (gthreads >> 5) * 8) {
+                    const int j = base + ((threadIdx.x & 31) >> 2);
+                    const double v = sum_parts_quad(a.upart + j, a.nrc, (size_t)a.n, j < a.n);
+                    if ((threadIdx.x & 3) == 0 && j < a.n) {
+                        a.u[j] = v;
+                        a.udf[j] = to_df(v);
+                        sq += v * v;
+                    }
                 }
             }
             block_partial(sq, a.bpart, 1);
@@ -644,11 +672,13 @@ cgls_kernel(KArgs a) {
                 ++apasses;
                 KB_SYNC();
                 double sq = 0.0;
-                for (int i = gtid; i < a.m; i += gthreads) {
-                    double v = 0.0;
-                    v += sum_parts(a.qpart + i, a.nck, (size_t)a.m);
-                    a.q[i] = v;
-                    sq += v * v;
+                for (int base = (gtid >> 5) * 8; base < a.m; base += (gthreads >> 5) * 8) {
+                    const int i = base + ((threadIdx.x & 31) >> 2);
+                    const double v = sum_parts_quad(a.qpart + i, a.nck, (size_t)a.m, i < a.m);
+                    if ((threadIdx.x & 3) == 0 && i < a.m) {
+                        a.q[i] = v;
+                        sq += v * v;
+                    }
                 }
                 block_partial(sq, a.bpart, 0);
                 KB_SYNC();
@@ -678,10 +708,13 @@ cgls_kernel(KArgs a) {
                 at_times_partials(a, a.r, a.rdf);
                 ++apasses;
                 KB_SYNC();
-                for (int j = gtid; j < a.n; j += gthreads) {
-                    const double v = sum_parts(a.upart + j, a.nrc, (size_t)a.n);
-                    a.u[j] = v;
-                    a.udf[j] = to_df(v);
+                for (int base = (gtid >> 5) * 8; base < a.n; base += (gthreads >> 5) * 8) {
+                    const int j = base + ((threadIdx.x & 31) >> 2);
+                    const double v = sum_parts_quad(a.upart + j, a.nrc, (size_t)a.n, j < a.n);
+                    if ((threadIdx.x & 3) == 0 && j < a.n) {
+                        a.u[j] = v;
+                        a.udf[j] = to_df(v);
+                    }
                 }
                 KB_SYNC();
             }

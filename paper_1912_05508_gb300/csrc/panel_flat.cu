@@ -1,6 +1,6 @@
 // Tall-skinny panel QR with a one-level tree: communication-avoiding QR (Eq. caqr,
 // Sec. 3.1.3) with CGS2 leaves, for panels whose stacked leaf R factors fit one 1024-row
-// block (P0 * b <= 1024; at b = 16 every m <= 65536).
+// block (P0 * B <= 1024 with B = 8 or 16 the bucketed width; at b = 16 every m <= 65536).
 //
 //  1. (Eq. caqr, circled 1) each of P0 CTAs factors a row block of at most RL * 256 rows by
 //     CGS2, RL rows per thread in registers; its Q goes to shared memory and its b x b R to
@@ -8,7 +8,8 @@
 //  2. One bounded grid barrier (cooperative launch: all CTAs are resident).
 //  3. (circled 2-3) every CTA loads the P0 stacked R factors and factors the stack with the
 //     same code in the same order, so each CTA holds the tree's Q without a second exchange
-//     through memory. CTA 0 writes R.
+//     through memory. CTA 0 writes R. The stack is held row-index-major, so the warps whose
+//     rows of the upper-triangular factors are still zero skip a step's arithmetic.
 //  4. (circled 4-5) each CTA multiplies its block's Q by its b x b slice of the tree's Q and
 //     stores the result: FP32 to W and, rounded to nearest even, to the product-precision
 //     copy Wh.
@@ -62,22 +63,29 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // CTA-wide sums of the N (<= 64) values x[] held by every thread. Returns this warp's row of
 // `tot`, whose entries 0..N-1 hold the CTA totals. One barrier; `red` alternates between
 // two buffers, so the next call may start writing before every warp has read this one.
+// A warp whose rows are all zero (`idle`, warp-uniform) contributes zeros without shuffling.
 template <int N, int B>
-__device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<B>& sm, int& parity) {
+__device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<B>& sm, int& parity,
+                                                  bool idle = false) {
     static_assert(N >= 1 && N <= 64, "block_sum handles at most 64 values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int N0 = N < 32 ? N : 32;
     constexpr int S0 = pow2ceil(N0);
-    float c0[S0];
+    if (idle) {
+        sm.red[parity][0][warp][lane] = 0.f;
+        if constexpr (N > 32) sm.red[parity][1][warp][lane] = 0.f;
+    } else {
+        float c0[S0];
 #pragma unroll
-    for (int i = 0; i < S0; ++i) c0[i] = i < N0 ? x[i] : 0.f;
-    sm.red[parity][0][warp][lane] = warp_transpose_reduce<S0>(c0);
-    if constexpr (N > 32) {
-        constexpr int S1 = pow2ceil(N - 32);
-        float c1[S1];
+        for (int i = 0; i < S0; ++i) c0[i] = i < N0 ? x[i] : 0.f;
+        sm.red[parity][0][warp][lane] = warp_transpose_reduce<S0>(c0);
+        if constexpr (N > 32) {
+            constexpr int S1 = pow2ceil(N - 32);
+            float c1[S1];
 #pragma unroll
-        for (int i = 0; i < S1; ++i) c1[i] = 32 + i < N ? x[32 + i] : 0.f;
-        sm.red[parity][1][warp][lane] = warp_transpose_reduce<S1>(c1);
+            for (int i = 0; i < S1; ++i) c1[i] = 32 + i < N ? x[32 + i] : 0.f;
+            sm.red[parity][1][warp][lane] = warp_transpose_reduce<S1>(c1);
+        }
     }
     __syncthreads();
     float t0 = 0.f;
@@ -104,14 +112,19 @@ __device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<
 // group's widest step, with the columns not yet orthogonalised masked to zero, and pick the
 // current and next columns by register selects. Sharing bodies keeps the kernel's code
 // small enough for the instruction cache at a cost of at most KG - 1 extra products.
+// rr0: the smallest in-block row index held by this warp in the stacked-R layout (the root),
+// or 0 (the leaves). In the stacked upper-triangular R factors, row index K + 1 and beyond is
+// zero in q_0..q_K and in column K, so such rows contribute nothing to step K's products and
+// the step leaves them unchanged: a warp with rr0 >= K + 1 skips the step's arithmetic.
 template <int B, int R, int K0, int KG>
-__device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+__device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
     constexpr int NQ = K0 + KG - 1;              // q columns any step of the group may use
     constexpr int N = 2 * NQ + 2;                // h2[NQ], nn, g[NQ], c
 #pragma unroll 1
     for (int s = 0; s < KG; ++s) {
         const int K = K0 + s;
         if (K >= b) return;
+        const bool idle = rr0 >= K + 1;  // rows >= K + 1: zero contributions, and unchanged by the step
         float cur[R], nx[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -146,7 +159,7 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
             x[NQ] = p1;
             x[2 * NQ + 1] = p2;
         }
-        const float* t = block_sum<N, B>(x, sm, parity);
+        const float* t = block_sum<N, B>(x, sm, parity, idle);
 
         // two interleaved chains per sum (even / odd j) halve the dependent FMA depth
         float h2[NQ > 0 ? NQ : 1], g[NQ > 0 ? NQ : 1];
@@ -162,14 +175,18 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
         const float nn = t[NQ];
         float acc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float a0 = cur[r], a1 = 0.f;
+        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+        if (!idle) {
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
-                else a0 = fmaf(-v[r][j], h2[j], a0);
+            for (int r = 0; r < R; ++r) {
+                float a0 = cur[r], a1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
+                    else a0 = fmaf(-v[r][j], h2[j], a0);
+                }
+                acc[r] = a0 + a1;
             }
-            acc[r] = a0 + a1;
         }
         float normsq = nn - hh;
         if (!(normsq >= 0.25f * nn)) {   // the second pass removed much of the norm: reduce it directly
@@ -177,7 +194,7 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
             d[0] = 0.f;
 #pragma unroll
             for (int r = 0; r < R; ++r) d[0] = fmaf(acc[r], acc[r], d[0]);
-            normsq = block_sum<1, B>(d, sm, parity)[0];
+            normsq = block_sum<1, B>(d, sm, parity, idle)[0];
         }
         // R_KK and 1 / R_KK from one reciprocal square root (a few ulp; the CGS2 error bound
         // is unchanged up to the constant)
@@ -197,6 +214,7 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
                 if (next) sm.Rs[K][K + 1] = gq;
             }
         }
+        if (idle) continue;              // the warp's rows stay zero
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float q = acc[r] * inv;
@@ -219,15 +237,15 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
 template <int B, int R, int K0>
 struct Cgs2Flat {
     static constexpr int KG = 4;
-    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
         if (K0 >= b) return;
-        cgs2_group<B, R, K0, KG>(v, b, sm, parity);
-        Cgs2Flat<B, R, K0 + KG>::run(v, b, sm, parity);
+        cgs2_group<B, R, K0, KG>(v, b, sm, parity, rr0);
+        Cgs2Flat<B, R, K0 + KG>::run(v, b, sm, parity, rr0);
     }
 };
 template <int B, int R>
 struct Cgs2Flat<B, R, B> {
-    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&) {}
+    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
 };
 
 __device__ __forceinline__ void flat_leaf_range(int m, int P0, int i, int& s, int& e) {
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
             v[r][j] = (lr < rows && j < b) ? a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] : 0.f;
     }
     __syncthreads();
-    Cgs2Flat<B, RL, 0>::run(v, b, sm, parity);
+    Cgs2Flat<B, RL, 0>::run(v, b, sm, parity, 0);
     __syncthreads();
 
     if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
@@ -318,24 +336,28 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
     __syncthreads();
 
     if (sm.ok) {
-        // the stacked R factors: stacked row rho = child * b + rr
-        const int srows = a.P0 * b;
+        // the stacked R factors, row-index-major: thread t holds row rr = t / TPR of the R
+        // factors of children (t mod TPR) + TPR r, so each warp holds one or two row indices
+        // (rr0 = its first) and can skip the steps where its rows are still zero
+        constexpr int TPR = kFT / B;
+        const int rr = t / TPR, cl = t % TPR;
         float vr[kRootRPT][B];
 #pragma unroll
         for (int r = 0; r < kRootRPT; ++r) {
-            const int rho = t + r * kFT;
-            const int child = rho / b, rr = rho - child * b;
-            const float* src = a.rbuf + (size_t)child * (B * B) + rr * B;
+            const int child = cl + TPR * r;
+            const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
+            const bool live = child < a.P0 && rr < b;
 #pragma unroll
-            for (int j = 0; j < B; ++j) vr[r][j] = (rho < srows && j < b) ? __ldcg(src + j) : 0.f;
+            for (int j4 = 0; j4 < B / 4; ++j4) {
+                const float4 q = live ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
+            }
         }
-        Cgs2Flat<B, kRootRPT, 0>::run(vr, b, sm, parity);
-        // this block's b x b slice of the tree's Q
+        Cgs2Flat<B, kRootRPT, 0>::run(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
+        // this block's b x b slice of the tree's Q: the rows of child blockIdx.x
 #pragma unroll
         for (int r = 0; r < kRootRPT; ++r) {
-            const int rho = t + r * kFT;
-            const int rr = rho - (int)blockIdx.x * b;
-            if (rr >= 0 && rr < b)
+            if (cl + TPR * r == (int)blockIdx.x && rr < b)
 #pragma unroll
                 for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
         }
@@ -415,8 +437,9 @@ static int launch_flat(FlatArgs& a, cudaStream_t st) {
     LLS_TRY((flat_prepare<B, RL>(cap)));
     if (a.P0 > cap) return LLS_ERR_UNSUPPORTED;
     const size_t smem = flat_smem_bytes<B, RL>();
-    if (a.P0 == 1) {
-        panel_flat_kernel<B, RL><<<1, kFT, smem, st>>>(a);
+    static const bool coop = getenv("LLS_PANEL_PLAIN") == nullptr;
+    if (a.P0 == 1 || !coop) {
+        panel_flat_kernel<B, RL><<<a.P0, kFT, smem, st>>>(a);
     } else {
         void* args[] = {&a};
         LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL>, dim3(a.P0), dim3(kFT), args,
@@ -444,11 +467,12 @@ int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
     a.rbuf = c.rbuf; a.bar = c.cnt; a.err = c.err;
     const int p2 = ceil_div(c.m, 2 * kFT), p4 = ceil_div(c.m, 4 * kFT);
+    const int bw = c.b <= 8 ? 8 : 16;   // the stack holds TPR * 4 children of B rows each
     int rl;
     if (c.m <= 2 * kFT) { rl = 2; a.P0 = 1; }
     else if (c.m <= 4 * kFT) { rl = 4; a.P0 = 1; }
-    else if (p2 * c.b <= kStackRows) { rl = 2; a.P0 = p2; }
-    else if (p4 * c.b <= kStackRows) { rl = 4; a.P0 = p4; }
+    else if (p2 * bw <= kStackRows) { rl = 2; a.P0 = p2; }
+    else if (p4 * bw <= kStackRows) { rl = 4; a.P0 = p4; }
     else return LLS_ERR_UNSUPPORTED;
     if (c.b <= 8) return rl == 2 ? launch_flat<8, 2>(a, st) : launch_flat<8, 4>(a, st);
     return rl == 2 ? launch_flat<16, 2>(a, st) : launch_flat<16, 4>(a, st);
