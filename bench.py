@@ -161,7 +161,11 @@ def run_reference(args):
 
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
 # it stands, from the captures summarised under profiles/; None once a kernel changes.
-NCU_TRAFFIC = {"panel": None, "tc_projection": None, "tc_update": None, "cgls": None}
+# tc_projection is the product kernel alone (the split-K reduce is a separate, small launch).
+NCU_TRAFFIC = {"panel": 2214912 + 256,
+               "tc_projection": 362140416 + 40631296,
+               "tc_update": 414549504 + 223791104,
+               "cgls": 24844714000 + 392099328}
 
 
 def split_point(w, pw):

@@ -437,9 +437,8 @@ static int launch_flat(FlatArgs& a, cudaStream_t st) {
     LLS_TRY((flat_prepare<B, RL>(cap)));
     if (a.P0 > cap) return LLS_ERR_UNSUPPORTED;
     const size_t smem = flat_smem_bytes<B, RL>();
-    static const bool coop = getenv("LLS_PANEL_PLAIN") == nullptr;
-    if (a.P0 == 1 || !coop) {
-        panel_flat_kernel<B, RL><<<a.P0, kFT, smem, st>>>(a);
+    if (a.P0 == 1) {
+        panel_flat_kernel<B, RL><<<1, kFT, smem, st>>>(a);
     } else {
         void* args[] = {&a};
         LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL>, dim3(a.P0), dim3(kFT), args,
