@@ -222,7 +222,7 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
         assert st == 0, st
     ms = time_launches(panel, 100, stream)
     by = 10.0 * m * pw
-    out["panel"] = {"kernel": f"panel_coop_kernel (CAQR panel {m}x{pw}, CGS2 leaves)", "bound": "hbm",
+    out["panel"] = {"kernel": f"panel_flat_kernel (CAQR panel {m}x{pw}, CGS2 leaves, one-level tree)", "bound": "hbm",
                     "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "us_per_launch": ms * 1e3, "algorithmic_bytes_per_launch": by}
     del W, Wh
