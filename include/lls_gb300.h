@@ -68,6 +68,12 @@ typedef struct {
     int leaf_rows;     /* reserved, 0 or 256 (the GPU panel's CAQR row blocks are 1024 rows, Sec. 3.1.3) */
     int reorth;        /* 1: re-orthogonalize (Sec. 4.2.1): factor Q once more, Q1 = Q2 R2, and return
                           Q2 and R = R2 R1 (twice the QR cost); 0 (default): one pass */
+    int panel_leaf;    /* leaf factorization of the CAQR panel: 0 (default) CGS2, classical
+                          Gram-Schmidt with one reorthogonalization; 1 MGS, the paper's modified
+                          Gram-Schmidt leaf (Alg. 4), which loses orthogonality in proportion to the
+                          panel's condition number. MGS panels are built for panels whose stacked
+                          leaf R factors fit one level (m <= 65536 at panel_width 16); taller panels,
+                          and the batched solver, return LLS_ERR_UNSUPPORTED with it. */
 } lls_options;
 
 typedef struct {

@@ -46,6 +46,7 @@ static bool valid_opts(const lls_options& o) {
     if (o.gemm_prec == LLS_PREC_FP8 && o.panel_width % 16 != 0) return false;   // 16-byte aligned FP8 slices
     if (o.leaf_rows != 256) return false;
     if (o.reorth != 0 && o.reorth != 1) return false;
+    if (o.panel_leaf != 0 && o.panel_leaf != 1) return false;
     return true;
 }
 
@@ -114,7 +115,7 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
 }
 
 struct QrCtx {
-    int m, n, pw, lowp;
+    int m, n, pw, lowp, leaf;
     QrWs w;
     float* R; int ldr;
     cudaStream_t st;
@@ -134,7 +135,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         PanelCall p;
         p.W = c.w.W; p.ldw = c.w.ldw; p.Wh = c.w.Wh; p.ldh = c.w.ldh; p.R = c.R; p.ldr = c.ldr;
         p.m = c.m; p.c0 = c0; p.b = w; p.lowp = c.lowp == 2 ? 3 : c.lowp;
-        p.rbuf = c.w.rbuf; p.qbuf = c.w.qbuf; p.cnt = c.w.cnt; p.err = c.w.err;
+        p.rbuf = c.w.rbuf; p.qbuf = c.w.qbuf; p.cnt = c.w.cnt; p.err = c.w.err; p.leaf = c.leaf;
         LLS_TRY(panel_qr(p, c.st));
         if (c.lowp == 2) {
             // FP8: the copy of Q needs per-column scales (|q| ~ m^-1/2 is below E4M3's normal
@@ -195,7 +196,7 @@ static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, cons
     LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
     QrCtx c;
-    c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec);
+    c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec); c.leaf = o.panel_leaf;
     c.w = w; c.R = R; c.ldr = ldr; c.st = st;
     LLS_TRY(qr_rec(c, 0, n));
     if (o.reorth) {
@@ -609,7 +610,8 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
     resolve(opts, o);
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
-    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8 || o.reorth)
+    if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8 || o.reorth ||
+        o.panel_leaf != 0)
         return LLS_ERR_UNSUPPORTED;
     if (!A || !lda || !b || !x || !ws) return LLS_ERR_ARG;
     for (int i = 0; i < batch; ++i) {

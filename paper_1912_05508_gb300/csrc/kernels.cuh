@@ -15,6 +15,7 @@ struct PanelCall {
     int lowp;              // 0 FP16, 1 BF16, 3 none
     float* rbuf; float* qbuf; unsigned* cnt;
     int* err;
+    int leaf = 0;          // 0 CGS2, 1 MGS (Alg. 4; one-level panels only)
 };
 void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t& cnt_words);
 int panel_qr(const PanelCall& c, cudaStream_t st);

@@ -362,7 +362,7 @@ int panel_qr(const PanelCall& c, cudaStream_t st) {
     if (c.b < 1 || c.b > 32) return LLS_ERR_UNSUPPORTED;
     // one-level tree when the stacked leaf R factors fit one block (panel_flat.cu)
     const int flat = panel_flat_qr(c, st);
-    if (flat != LLS_ERR_UNSUPPORTED) return flat;
+    if (flat != LLS_ERR_UNSUPPORTED || c.leaf != 0) return flat;   // MGS leaves: one-level panels only
     PanelArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;

@@ -234,6 +234,83 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
     }
 }
 
+// Steps K = K0 .. K0 + KG - 1 of modified Gram-Schmidt (Alg. 4) on the register block v:
+// before step K, columns < K hold q_0..q_{K-1} and every column >= K has already had
+// q_0..q_{K-1} removed. One CTA-wide reduction gives ||a_K||^2 and a_K^T a_j (j > K); then
+// R_KK = ||a_K||, q_K = a_K / R_KK, R_Kj = a_K^T a_j / R_KK (= q_K^T a_j) and
+// a_j -= q_K R_Kj. Products for columns j <= K are masked to zero, so the shared group body
+// leaves them untouched. rr0 as in cgs2_group.
+template <int B, int R, int K0, int KG>
+__device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+    constexpr int N = B - K0;                    // ||a_K||^2, then a_K^T a_j for j = K0+1 .. B-1
+#pragma unroll 1
+    for (int s = 0; s < KG; ++s) {
+        const int K = K0 + s;
+        if (K >= b) return;
+        const bool idle = rr0 >= K + 1;
+        float cur[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float c = v[r][K0];
+#pragma unroll
+            for (int u = 1; u < KG; ++u) c = s == u ? v[r][K0 + u] : c;
+            cur[r] = c;
+        }
+        float x[N];
+        {
+            float p = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) p = fmaf(cur[r], cur[r], p);
+            x[0] = p;
+        }
+#pragma unroll
+        for (int i = 1; i < N; ++i) {
+            const int j = K0 + i;
+            float p = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) p = fmaf(v[r][j], cur[r], p);
+            x[i] = j > K ? p : 0.f;
+        }
+        const float* t = block_sum<N, B>(x, sm, parity, idle);
+        const float ns = fmaxf(t[0], 0.f);
+        const float inv = ns > 0.f ? rsqrtf(ns) : 0.f;
+        const float nrm = ns * inv;
+        float rk[N];                             // R_Kj for j = K0 + i (zero for j <= K)
+        rk[0] = 0.f;
+#pragma unroll
+        for (int i = 1; i < N; ++i) rk[i] = t[i] * inv;
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane == 0) sm.Rs[K][K] = nrm;
+            if (lane > K && lane < b) sm.Rs[K][lane] = t[lane - K0] * inv;
+        }
+        if (idle) continue;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float q = cur[r] * inv;
+#pragma unroll
+            for (int i = 1; i < N; ++i) v[r][K0 + i] = fmaf(-q, rk[i], v[r][K0 + i]);
+#pragma unroll
+            for (int u = 0; u < KG; ++u)
+                if (s == u) v[r][K0 + u] = q;
+        }
+    }
+}
+
+template <int B, int R, int K0>
+struct MgsFlat {
+    static constexpr int KG = 4;
+    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+        if (K0 >= b) return;
+        mgs_group<B, R, K0, KG>(v, b, sm, parity, rr0);
+        MgsFlat<B, R, K0 + KG>::run(v, b, sm, parity, rr0);
+    }
+};
+template <int B, int R>
+struct MgsFlat<B, R, B> {
+    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
+};
+
 template <int B, int R, int K0>
 struct Cgs2Flat {
     static constexpr int KG = 4;
@@ -247,6 +324,13 @@ template <int B, int R>
 struct Cgs2Flat<B, R, B> {
     static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
 };
+
+// The leaf factorization of the panel: CGS2 (default) or MGS (Alg. 4).
+template <bool MGS, int B, int R>
+__device__ __forceinline__ void leaf_qr(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+    if constexpr (MGS) MgsFlat<B, R, 0>::run(v, b, sm, parity, rr0);
+    else Cgs2Flat<B, R, 0>::run(v, b, sm, parity, rr0);
+}
 
 __device__ __forceinline__ void flat_leaf_range(int m, int P0, int i, int& s, int& e) {
     const int base = m / P0, extra = m % P0;
@@ -269,7 +353,7 @@ __device__ __forceinline__ void flat_write_r(const FlatArgs& a, const FlatSmem<B
     }
 }
 
-template <int B, int RL>
+template <int B, int RL, bool MGS>
 __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
     extern __shared__ __align__(16) unsigned char flat_smem[];
     FlatSmem<B>& sm = *reinterpret_cast<FlatSmem<B>*>(flat_smem);
@@ -291,7 +375,7 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
             v[r][j] = (lr < rows && j < b) ? a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] : 0.f;
     }
     __syncthreads();
-    Cgs2Flat<B, RL, 0>::run(v, b, sm, parity, 0);
+    leaf_qr<MGS, B, RL>(v, b, sm, parity, 0);
     __syncthreads();
 
     if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
@@ -353,7 +437,7 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
                 vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
             }
         }
-        Cgs2Flat<B, kRootRPT, 0>::run(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
+        leaf_qr<MGS, B, kRootRPT>(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
         // this block's b x b slice of the tree's Q: the rows of child blockIdx.x
 #pragma unroll
         for (int r = 0; r < kRootRPT; ++r) {
@@ -409,7 +493,7 @@ constexpr size_t flat_smem_bytes() {
 }
 
 // Per device: the dynamic shared memory opt-in and the co-resident CTA capacity.
-template <int B, int RL>
+template <int B, int RL, bool MGS>
 static int flat_prepare(int& capacity) {
     constexpr int kMaxDev = 64;
     static int cap[kMaxDev];
@@ -419,11 +503,11 @@ static int flat_prepare(int& capacity) {
     if (dev < 0 || dev >= kMaxDev) return LLS_ERR_UNSUPPORTED;
     if (!done[dev]) {
         const size_t smem = flat_smem_bytes<B, RL>();
-        LLS_CUDA_TRY(cudaFuncSetAttribute(panel_flat_kernel<B, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LLS_CUDA_TRY(cudaFuncSetAttribute(panel_flat_kernel<B, RL, MGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         int sms = 0, per = 0;
         LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_flat_kernel<B, RL>, kFT, smem));
+        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_flat_kernel<B, RL, MGS>, kFT, smem));
         cap[dev] = sms * per;
         done[dev] = true;
     }
@@ -431,17 +515,17 @@ static int flat_prepare(int& capacity) {
     return LLS_OK;
 }
 
-template <int B, int RL>
+template <int B, int RL, bool MGS>
 static int launch_flat(FlatArgs& a, cudaStream_t st) {
     int cap = 0;
-    LLS_TRY((flat_prepare<B, RL>(cap)));
+    LLS_TRY((flat_prepare<B, RL, MGS>(cap)));
     if (a.P0 > cap) return LLS_ERR_UNSUPPORTED;
     const size_t smem = flat_smem_bytes<B, RL>();
     if (a.P0 == 1) {
-        panel_flat_kernel<B, RL><<<1, kFT, smem, st>>>(a);
+        panel_flat_kernel<B, RL, MGS><<<1, kFT, smem, st>>>(a);
     } else {
         void* args[] = {&a};
-        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL>, dim3(a.P0), dim3(kFT), args,
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL, MGS>, dim3(a.P0), dim3(kFT), args,
                                                  smem, st));
     }
     LLS_LAUNCH_CHECK("panel_flat", st);
@@ -473,8 +557,12 @@ int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
     else if (p2 * bw <= kStackRows) { rl = 2; a.P0 = p2; }
     else if (p4 * bw <= kStackRows) { rl = 4; a.P0 = p4; }
     else return LLS_ERR_UNSUPPORTED;
-    if (c.b <= 8) return rl == 2 ? launch_flat<8, 2>(a, st) : launch_flat<8, 4>(a, st);
-    return rl == 2 ? launch_flat<16, 2>(a, st) : launch_flat<16, 4>(a, st);
+    if (c.leaf == 1) {
+        if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, true>(a, st) : launch_flat<8, 4, true>(a, st);
+        return rl == 2 ? launch_flat<16, 2, true>(a, st) : launch_flat<16, 4, true>(a, st);
+    }
+    if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, false>(a, st) : launch_flat<8, 4, false>(a, st);
+    return rl == 2 ? launch_flat<16, 2, false>(a, st) : launch_flat<16, 4, false>(a, st);
 }
 
 }  // namespace lls

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(PKG, "liblls_gb300.so")
 PREC = {"fp16": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp64": 4}
 TARGET = {"fp32": 0, "fp64": 1}
 KRYLOV = {"cgls": 0, "lsqr": 1}
+PANEL_LEAF = {"cgs2": 0, "mgs": 1}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
           -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED",
           -7: "LLS_ERR_TOO_LARGE"}
@@ -32,7 +33,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
 class lls_options(C.Structure):
     _fields_ = [("gemm_prec", C.c_int), ("target", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("panel_width", C.c_int), ("krylov", C.c_int),
-                ("leaf_rows", C.c_int), ("reorth", C.c_int)]
+                ("leaf_rows", C.c_int), ("reorth", C.c_int), ("panel_leaf", C.c_int)]
 
 
 class lls_info(C.Structure):
@@ -118,7 +119,7 @@ def default_options() -> lls_options:
 
 
 def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-                 krylov="cgls", leaf_rows=256, reorth=0) -> lls_options:
+                 krylov="cgls", leaf_rows=256, reorth=0, panel_leaf="cgs2") -> lls_options:
     o = lls_options()
     load().lls_default_options(C.byref(o))
     o.gemm_prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -129,6 +130,7 @@ def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=
     o.krylov = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
     o.leaf_rows = int(leaf_rows)
     o.reorth = int(reorth)
+    o.panel_leaf = PANEL_LEAF[panel_leaf] if isinstance(panel_leaf, str) else int(panel_leaf)
     return o
 
 
@@ -290,12 +292,12 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=0):
+def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=0, panel_leaf="cgs2"):
     """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False."""
     torch = _torch()
     _check_colmajor(A)
     m, n = A.shape
-    o = make_options(prec=prec, panel_width=panel_width, reorth=reorth)
+    o = make_options(prec=prec, panel_width=panel_width, reorth=reorth, panel_leaf=panel_leaf)
     nb = qr_factor_workspace_size(m, n, o)
     if nb == 0:
         raise LLSError(-1, "qr_factor_workspace_size")
@@ -310,7 +312,7 @@ def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=
 
 
 def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-          krylov="cgls", want_r=False, ws=None, stream=None, check=True, reorth=0):
+          krylov="cgls", want_r=False, ws=None, stream=None, check=True, reorth=0, panel_leaf="cgs2"):
     """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
 
     Returns (x, info_dict[, R]). Synchronizes the stream (to fill info)."""
@@ -318,7 +320,7 @@ def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0
     _check_colmajor(A)
     m, n = A.shape
     o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter,
-                     panel_width=panel_width, krylov=krylov, reorth=reorth)
+                     panel_width=panel_width, krylov=krylov, reorth=reorth, panel_leaf=panel_leaf)
     nb = lls_solve_workspace_size(m, n, o)
     if nb == 0:
         raise LLSError(-1, "lls_solve_workspace_size")

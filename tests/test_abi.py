@@ -61,3 +61,12 @@ def test_workspace_queries_and_argument_errors(lib):
     # misaligned / too small workspace
     assert lls.qr_factor(100, 10, 256, 100, None, 0, 256, 10, 257, 1 << 30, o, None) == -4
     assert lls.qr_factor(100, 10, 256, 100, None, 0, 256, 10, 256, 1024, o, None) == -4
+
+
+def test_panel_leaf_option(lib):
+    # the options struct carries the panel leaf (0 CGS2, 1 MGS of Alg. 4); other values are
+    # argument errors, and the default is CGS2
+    assert lls.lls_default_options().panel_leaf == 0
+    assert lls.qr_factor_workspace_size(1000, 64, lls.make_options(panel_leaf="mgs")) > 0
+    assert lls.qr_factor_workspace_size(1000, 64, lls.make_options(panel_leaf=2)) == 0
+    assert lls.lls_solve_workspace_size(1000, 64, lls.make_options(panel_leaf=-1)) == 0

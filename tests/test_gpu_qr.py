@@ -130,3 +130,80 @@ def test_reorth_restores_orthogonality(prec, u):
     assert o2 <= 16 * u * 128 ** 0.5
     assert metrics.qr_factorization_error(A, Q2, R2) <= 16 * u * 128 ** 0.5
     assert np.allclose(np.tril(R2, -1), 0.0)
+
+
+# ---- the paper's MGS leaf (Alg. 4) as the panel factorization (opts.panel_leaf = 1) ----
+
+def graded(m, n, seed, kappa):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = kappa ** (-np.arange(n) / max(n - 1, 1))
+    return ((U * s) @ V.T).astype(np.float32)
+
+
+@pytest.mark.parametrize("m,b,kappa", [(3000, 16, 1e2), (32768, 16, 1e4), (65536, 13, 1e3), (4100, 8, 1e5)])
+def test_mgs_panel_matches_oracle_mgs_tsqr(m, b, kappa):
+    # one panel (n = panel width): CAQR with MGS leaves. MGS loses orthogonality like
+    # kappa * u (CGS2 does not), so Q is bounded by c kappa u32; R is the unique
+    # positive-diagonal factor, equal to the oracle's to c kappa u32 normwise.
+    A = graded(m, b, m + b, kappa)
+    Q, R = lls.qr(lls.colmajor(A), prec="fp32", panel_width=b, panel_leaf="mgs")
+    torch.cuda.synchronize()
+    Q, R = Q.cpu().numpy().astype(np.float64), R.cpu().numpy().astype(np.float64)
+    A64 = A.astype(np.float64)
+    Qo, Ro = rgsqrf.tsqr(A64, leaf_rows=1024, leaf="mgs")
+    assert np.allclose(np.tril(R, -1), 0.0) and (np.diag(R) > 0).all()
+    assert metrics.qr_factorization_error(A64, Q, R) <= 8 * b * U32
+    assert metrics.orthogonality(Q, "2") <= 16 * b * kappa * U32
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 4 * np.sqrt(b) * kappa * U32 + 4 * b * U32
+
+
+def test_cgs2_panel_keeps_orthogonality_where_mgs_loses_it():
+    A = graded(32768, 16, 5, 1e6)
+    Qc, _ = lls.qr(lls.colmajor(A), prec="fp32", panel_width=16)
+    Qm, _ = lls.qr(lls.colmajor(A), prec="fp32", panel_width=16, panel_leaf="mgs")
+    torch.cuda.synchronize()
+    oc = metrics.orthogonality(Qc.cpu().numpy().astype(np.float64), "2")
+    om = metrics.orthogonality(Qm.cpu().numpy().astype(np.float64), "2")
+    assert oc <= 64 * U32
+    assert om > 100 * oc        # MGS: ~kappa u32
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_mgs_leaves_in_the_recursion_match_oracle(prec):
+    A = svd_matrix(6000, 128, 1e3, seed=31)
+    Q, R = lls.qr(lls.colmajor(A), prec=prec, panel_width=16, panel_leaf="mgs")
+    torch.cuda.synchronize()
+    Q, R = Q.cpu().numpy().astype(np.float64), R.cpu().numpy().astype(np.float64)
+    Qo, Ro = rgsqrf.rgsqrf(A, 16, prec, leaf_rows=256, leaf="mgs")
+    u = ULOW[prec]
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    assert metrics.qr_factorization_error(A, Q, R) <= 4 * u
+
+
+def test_mgs_leaves_solve_to_fp64_target():
+    p = synth.svd_lls(4096, 96, "geometric", 1e3, seed=33)
+    x, info = lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda(), panel_width=16, panel_leaf="mgs")
+    assert info["status"] == 0, info
+    xs = direct.lls(p.A, p.b)
+    assert metrics.eta_kw(p.A, p.b, x.cpu().numpy()) <= 1e-12
+    assert metrics.forward_error(x.cpu().numpy(), xs) <= 10 * p.kappa * 1e-12
+
+
+def test_mgs_leaves_unsupported_where_built_for_cgs2_only():
+    # a panel taller than one tree level (m > 65536 at width 16) and the batched solver
+    A = torch.zeros((16, 70000), device="cuda").t()
+    with pytest.raises(lls.LLSError) as e:
+        lls.qr(A, prec="fp32", panel_width=16, panel_leaf="mgs")
+    assert e.value.status == -6
+    o = lls.make_options(panel_leaf="mgs", target="fp32")
+    nb = lls.lls_solve_batched_workspace_size(1, [256], [16], o)
+    ws = lls.workspace(max(nb, 1 << 20))
+    Ab = torch.randn((16, 256), device="cuda").t()
+    bb = torch.randn(256, dtype=torch.float64, device="cuda")
+    xb = torch.empty(16, dtype=torch.float64, device="cuda")
+    infos = (lls.lls_info * 1)()
+    st = lls.lls_solve_batched(1, [256], [16], [Ab.data_ptr()], [256], [bb.data_ptr()], [xb.data_ptr()], None,
+                               None, ws.data_ptr(), ws.numel(), o, infos, torch.cuda.current_stream().cuda_stream)
+    assert st == -6
