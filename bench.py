@@ -164,8 +164,20 @@ def run_reference(args):
 # tc_projection is the product kernel alone (the split-K reduce is a separate, small launch).
 NCU_TRAFFIC = {"panel": 2214912 + 256,
                "tc_projection": 362140416 + 40631296,
-               "tc_update": 414549504 + 223791104,
+               "tc_update": None,
                "cgls": 24844714000 + 392099328}
+
+
+def max_over_ranks(value, world_size, device):
+    """The slowest rank's value (every rank returns it); the job's time per step is the
+    slowest replica's. device: where the collective's tensor lives (cuda under NCCL, cpu
+    under gloo)."""
+    if world_size <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
 
 
 def split_point(w, pw):
@@ -380,11 +392,7 @@ def main():
     total_ms = ev0.elapsed_time(ev1)
     launches = lls.lls_kernel_launch_count() - launches0
     clocks = sampler.stop()
-    ms = total_ms / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / args.steps, ws, dev)
 
     # QR alone (for the QR TFLOP/s half of the metric)
     qo = lls.make_options(prec=args.prec, panel_width=args.pw, reorth=args.reorth)

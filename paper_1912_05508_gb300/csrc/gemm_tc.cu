@@ -34,6 +34,9 @@ constexpr int kTcThreads = 128;
 constexpr int kTcBM = 128;
 constexpr int kTcBK = 64;
 constexpr int kTcStages = 4;
+// Pipeline depth: the 128-wide update tile keeps 3 stages (97 KB of shared memory), so two CTAs
+// share an SM and one CTA's read-modify-write epilogue overlaps the other's main loop.
+constexpr int tc_stages(int bn, int epi) { return (epi == 1 && bn == 128) ? 3 : kTcStages; }
 constexpr int kTcABytes = kTcBM * kTcBK * 2;     // 16 KB
 enum TcEpi { TC_EPI_PARTIAL = 0, TC_EPI_UPDATE = 1 };
 
@@ -162,14 +165,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     static_assert(!(F8 && A_MN), "8-bit operands are used K-major only");
     constexpr int kKe = F8 ? 2 * kTcBK : kTcBK;   // K elements per 128-byte k-tile row
+    constexpr int kStages = tc_stages(BN, EPI);
     constexpr int kBBytes = BN * kTcBK * 2;
     constexpr int kStageBytes = kTcABytes + kBBytes;
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = (uint64_t*)(smem + kTcStages * kStageBytes);
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kTcStages + 1);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages);
-    const uint32_t accb = smem_u32(bars + 2 * kTcStages);
+    uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
+    const uint32_t accb = smem_u32(bars + 2 * kStages);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // The update walks N fastest: the CTAs that share one 128-row tile of Q1 (the larger
@@ -182,7 +186,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int nk = kt1 - kt0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -210,8 +214,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (warp == 0 && lane == 0) {
             // ---- TMA producer ----
             for (int i = 0; i < nk && ok; ++i) {
-                const int s = i % kTcStages;
-                const uint32_t ph = (i / kTcStages) & 1;
+                const int s = i % kStages;
+                const uint32_t ph = (i / kStages) & 1;
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1, a.err)) { ok = false; break; }
                 const uint32_t sa = smem_u32(smem + s * kStageBytes);
                 const uint32_t sb = sa + kTcABytes;
@@ -228,8 +232,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         } else if (warp == 1 && lane == 0) {
             // ---- MMA issuer ----
             for (int i = 0; i < nk && ok; ++i) {
-                const int s = i % kTcStages;
-                const uint32_t ph = (i / kTcStages) & 1;
+                const int s = i % kStages;
+                const uint32_t ph = (i / kStages) & 1;
                 if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + s * kStageBytes);
@@ -306,7 +310,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // land before the CTA exits (bounded).
             if (warp == 0 && lane == 0) {
                 const unsigned long long t0 = globaltimer_ns();
-                for (int s = 0; s < kTcStages; ++s)
+                for (int s = 0; s < kStages; ++s)
                     while (!mbar_try_wait(full0 + 8 * s, 0) && !mbar_try_wait(full0 + 8 * s, 1) &&
                            globaltimer_ns() - t0 < kSpinLimitNs) {
                     }
@@ -376,7 +380,7 @@ static int pick_bn(int n) { return n <= 64 ? 64 : (n <= 128 ? 128 : 256); }
 
 template <int BN, bool A_MN, int EPI, bool F8>
 static int launch_tc(const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
-    constexpr int smem = kTcStages * (kTcABytes + BN * kTcBK * 2) + 1024 + 256;
+    constexpr int smem = tc_stages(BN, EPI) * (kTcABytes + BN * kTcBK * 2) + 1024 + 256;
     auto k = tc_gemm_kernel<BN, A_MN, EPI, F8>;
     static bool attr = false;
     if (!attr) {
@@ -443,7 +447,7 @@ int gemm_projection(const ProjCall& c, cudaStream_t st) {
 }
 
 int gemm_update(const UpdCall& c, cudaStream_t st) {
-    const int bn = pick_bn(c.w2);
+    const int bn = c.w2 <= 64 ? 64 : 128;
     if (c.lowp == 2) {
         // FP8: A = Q1 row-major (K-major, rows of ldq bytes), B = R12l (K-major)
         if (!c.QT) return LLS_ERR_UNSUPPORTED;
