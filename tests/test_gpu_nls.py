@@ -1,0 +1,64 @@
+"""GPU check of batched nonlinear least squares (Gauss-Newton over lls_solve_batched), the
+paper's named next application (Sec. 6).
+
+Reference: scipy.optimize.least_squares (Levenberg-Marquardt, MINPACK) on the CPU from the
+same starting points, in FP64. The GPU iteration uses FP32 Jacobians, so its fixed point is the
+minimiser to cond(J) u32 relative, and its cost matches to second order in that difference.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1912_05508_gb300 import nls
+
+pytestmark = pytest.mark.gpu
+
+
+def make_fits(count, seed):
+    # y = a exp(-b t) + c + noise, uneven sample counts, starting points 30 % off
+    rng = np.random.default_rng(seed)
+    probs = []
+    for _ in range(count):
+        m = int(rng.integers(200, 1200))
+        t = np.linspace(0.0, 4.0, m)
+        theta = np.array([rng.uniform(0.5, 2.0), rng.uniform(0.3, 1.5), rng.uniform(-0.5, 0.5)])
+        y = theta[0] * np.exp(-theta[1] * t) + theta[2] + 1e-3 * rng.standard_normal(m)
+        theta0 = theta * (1.0 + 0.3 * rng.uniform(-1.0, 1.0, 3))
+        probs.append((t, y, theta, theta0))
+    return probs
+
+
+def residual_np(th, t, y):
+    return th[0] * np.exp(-th[1] * t) + th[2] - y
+
+
+def jacobian_np(th, t, y):
+    e = np.exp(-th[1] * t)
+    return np.stack([e, -th[0] * t * e, np.ones_like(t)], axis=1)
+
+
+def test_gauss_newton_batch_matches_minpack():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    probs = make_fits(48, seed=5)
+    ts = [torch.from_numpy(p[0]).cuda() for p in probs]
+    ys = [torch.from_numpy(p[1]).cuda() for p in probs]
+
+    def fun(idx, thetas):
+        rs, Js = [], []
+        for i, th in zip(idx, thetas):
+            e = torch.exp(-th[1] * ts[i])
+            rs.append(th[0] * e + th[2] - ys[i])
+            Js.append(torch.stack([e, -th[0] * ts[i] * e, torch.ones_like(e)], dim=1))
+        return rs, Js
+
+    th0 = [torch.from_numpy(p[3]).cuda() for p in probs]
+    thetas, infos = nls.gauss_newton_batched(fun, th0, max_iter=60, xtol=1e-13)
+    for (t, y, _, start), th, info in zip(probs, thetas, infos):
+        ref = scipy_opt.least_squares(residual_np, start, jac=jacobian_np, args=(t, y), method="lm",
+                                      xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        got = th.cpu().numpy()
+        assert info["converged"], info
+        # the FP32 Jacobian moves the fixed point by about cond(J) u32 (nls module docstring)
+        cond = np.linalg.cond(jacobian_np(ref.x, t, y))
+        assert np.linalg.norm(got - ref.x) <= 16 * cond * 2.0 ** -24 * np.linalg.norm(ref.x), (got, ref.x, cond)
+        assert info["cost"] <= ref.cost * (1 + 1e-6)
