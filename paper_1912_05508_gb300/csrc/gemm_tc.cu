@@ -34,9 +34,10 @@ constexpr int kTcThreads = 128;
 constexpr int kTcBM = 128;
 constexpr int kTcBK = 64;
 constexpr int kTcStages = 4;
-// Pipeline depth: the 128-wide update tile keeps 3 stages (97 KB of shared memory), so two CTAs
-// share an SM and one CTA's read-modify-write epilogue overlaps the other's main loop.
-constexpr int tc_stages(int bn, int epi) { return (epi == 1 && bn == 128) ? 3 : kTcStages; }
+// Pipeline depth: 128-wide tiles keep 3 stages (97 KB of shared memory), so two CTAs share an
+// SM and one CTA's epilogue (the update's read-modify-write, the projection's partial store)
+// overlaps the other's main loop.
+constexpr int tc_stages(int bn, int epi) { return bn == 128 ? 3 : kTcStages; }
 constexpr int kTcABytes = kTcBM * kTcBK * 2;     // 16 KB
 enum TcEpi { TC_EPI_PARTIAL = 0, TC_EPI_UPDATE = 1 };
 
@@ -376,7 +377,7 @@ static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
     return d;
 }
 
-static int pick_bn(int n) { return n <= 64 ? 64 : (n <= 128 ? 128 : 256); }
+static int pick_bn(int n) { return n <= 64 ? 64 : 128; }
 
 template <int BN, bool A_MN, int EPI, bool F8>
 static int launch_tc(const CUtensorMap& tA, const CUtensorMap& tB, const TcArgs& a, dim3 grid, cudaStream_t st) {
