@@ -43,7 +43,7 @@ typedef enum {
     LLS_ERR_TOO_LARGE = -7     /* sizes need more scratch than a fixed-scratch entry point holds */
 } lls_status;
 
-/* Precision of the two tensor-core products of each recursion step (Alg. 2 lines 8-9).
+/* Precision of the two tensor-core products of each recursion step (Alg. 2: projection and update).
  * FP16 is the paper's choice (Sec. 2.1); BF16 trades resolution for range; FP8 is E4M3 with a
  * power-of-two scale per column of both operands (max in [2^7, 2^8)), 3 significand bits
  * (requires panel_width 16 or 32); FP32 runs the products on the FP32 units (no rounding of
@@ -190,7 +190,7 @@ int lls_backward(int batch, const int* m, const int* n, const float* const* A, c
 
 /* ---------------------------------------------------------------------------
  * Kernel-level building blocks: the two tensor-core products of one recursion step of
- * Alg. 2 (line 8: R12 = Q1^T A2; line 9: A2 = A2 - Q1 R12), with the operands already
+ * Alg. 2 (projection R12 = Q1^T A2, update A2 = A2 - Q1 R12), with the operands already
  * rounded to FP16 or BF16 (prec = LLS_PREC_FP16 / LLS_PREC_BF16) and FP32 accumulation.
  * Exposed for testing and for callers that run their own recursion.
  *

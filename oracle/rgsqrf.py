@@ -112,8 +112,8 @@ def rgsqrf(A: np.ndarray, panel_width: int = 32, prec: str = "fp16",
            leaf_rows: int = 256, leaf: str = "cgs2"):
     """Alg. 2 with the GEMM inputs rounded to ``prec`` ('fp16', 'bf16', 'fp32', 'fp64').
 
-    R12 = (round(Q1)^T round(A2 * 2^e)) * 2^-e           (line 8, A2 columns scaled)
-    A2  = A2 - (round(Q1) round(R12 * 2^f)) * 2^-f        (line 9, R12 columns scaled)
+    R12 = (round(Q1)^T round(A2 * 2^e)) * 2^-e           (projection, A2 columns scaled)
+    A2  = A2 - (round(Q1) round(R12 * 2^f)) * 2^-f        (update, R12 columns scaled)
     Q1 is not scaled for FP16/BF16 (|q| <= 1). For 'fp8' (E4M3, whose normal range starts at
     2^-6, above the ~m^-1/2 entries of Q) Q1's columns are scaled too, Q1l = round(Q1 2^s):
     R12 = 2^-s (Q1l^T A2l) 2^-e, and the update uses Q1 R12 = Q1l (2^-s R12), so R12's rows

@@ -3,8 +3,8 @@
 // qr_factor runs Alg. 2 (recursive Gram-Schmidt QR, Eq. recqr) depth first on the host,
 // enqueueing for every internal node of width w = w1 + w2:
 //   scale/cast of A2 (columns [c0+w1, c0+w))          -> low-precision A2 and exponents e
-//   projection R12 = Q1^T A2 (Alg. 2 line 8)          -> FP32 R12 block of R, scaled low-precision R12
-//   update A2 <- A2 - Q1 R12 (Alg. 2 line 9)          -> FP32 in place
+//   projection R12 = Q1^T A2 (Alg. 2)                 -> FP32 R12 block of R, scaled low-precision R12
+//   update A2 <- A2 - Q1 R12 (Alg. 2)                 -> FP32 in place
 // and for every leaf (<= panel_width columns) the CAQR panel (Eq. caqr). All of it is
 // asynchronous on the caller's stream; nothing is allocated.
 #include <stdlib.h>
@@ -121,11 +121,19 @@ struct QrCtx {
     cudaStream_t st;
 };
 
-// LLS_NODE=split keeps narrow nodes on the four-kernel path (for comparisons).
+// LLS_NODE=split keeps narrow nodes on the four-kernel path, LLS_NODE=node runs them as one
+// launch each but keeps the lowest nodes' panels separate (for comparisons).
 static bool use_fused_nodes() {
     static const bool on = [] {
         const char* v = getenv("LLS_NODE");
         return !(v && v[0] == 's');
+    }();
+    return on;
+}
+static bool use_fused_blocks() {
+    static const bool on = [] {
+        const char* v = getenv("LLS_NODE");
+        return !(v && (v[0] == 's' || v[0] == 'n'));
     }();
     return on;
 }
@@ -147,6 +155,16 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         return LLS_OK;
     }
     const int w1 = split_point(w, c.pw), w2 = w - w1;
+    if (w1 == c.pw && w2 <= c.pw && (c.lowp == 0 || c.lowp == 1) && c.leaf == 0 && use_fused_blocks()) {
+        // both halves are panels: left panel, node and right panel in one launch
+        BlockCall bc;
+        bc.W = c.w.W; bc.ldw = c.w.ldw; bc.Wh = c.w.Wh; bc.ldh = c.w.ldh; bc.R = c.R; bc.ldr = c.ldr;
+        bc.m = c.m; bc.c0 = c0; bc.w1 = w1; bc.w2 = w2; bc.lowp = c.lowp;
+        bc.rbuf = c.w.rbuf; bc.cnt = c.w.cnt; bc.part = c.w.part; bc.part_floats = c.w.part_floats;
+        bc.colmax = c.w.colmax + c0 + w1; bc.err = c.w.err;
+        const int r = block_fused_qr(bc, c.st);
+        if (r != LLS_ERR_UNSUPPORTED) return r;
+    }
     LLS_TRY(qr_rec(c, c0, w1));
     float* R12 = c.R + (size_t)c0 + (size_t)(c0 + w1) * c.ldr;
     float* A2 = c.w.W + (size_t)(c0 + w1) * c.w.ldw;

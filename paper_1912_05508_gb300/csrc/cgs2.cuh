@@ -33,6 +33,28 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&x)[S]) {
     return r;
 }
 
+// The same butterfly with max instead of sum: lane L ends with the warp-wide maximum of value
+// index (L mod S), S a power of two <= 32.
+template <int S>
+__device__ __forceinline__ float warp_transpose_max(float (&x)[S]) {
+    static_assert(S >= 1 && S <= 32 && (S & (S - 1)) == 0, "one power-of-two chunk of at most 32 values");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = S / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? x[i] : x[i + o];
+            const float keep = up ? x[i + o] : x[i];
+            x[i] = fmaxf(keep, __shfl_xor_sync(kFullMask, send, o));
+        }
+    }
+    float r = x[0];
+#pragma unroll
+    for (int o = S; o < 32; o <<= 1) r = fmaxf(r, __shfl_xor_sync(kFullMask, r, o));
+    return r;
+}
+
 // Reduction scratch: two alternating buffers, each with room for two vectors of 32 per warp.
 constexpr int kRedStride = 2 * kPanelWarps * 32;
 constexpr int kRedFloats = 2 * kRedStride;

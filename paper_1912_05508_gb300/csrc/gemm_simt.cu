@@ -98,7 +98,7 @@ int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, in
 }
 
 // ---------------------------------------------------------------------------------------
-// Split-K reduction and epilogue of the projection R12 = Q1^T A2 (Alg. 2 line 8):
+// Split-K reduction and epilogue of the projection R12 = Q1^T A2 (the projection step of Alg. 2):
 // R12[i, j] = (sum_s part[s][i, j]) * 2^-e_j in a fixed order, stored in FP32; then the
 // column exponent f_j of R12 and R12l = round(R12 * 2^f_j) for the update product.
 // One CTA per column j.

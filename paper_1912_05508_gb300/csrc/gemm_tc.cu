@@ -1,4 +1,4 @@
-// Tensor-core products of the recursion (Alg. 2 lines 8-9) on sm_103a: tcgen05.mma with the
+// Tensor-core products of the recursion (the projection and update of Alg. 2) on sm_103a: tcgen05.mma with the
 // accumulator in tensor memory (TMEM), operands staged in shared memory by TMA.
 //
 //   projection  P = Q1l^T A2l       M = w1, N = w2, K = m   (both operands K-major)

@@ -17,10 +17,28 @@ struct PanelCall {
     int* err;
     int leaf = 0;          // 0 CGS2, 1 MGS (Alg. 4; one-level panels only)
 };
+// cnt[kFlatBarWord .. +kFlatBarWords): the grid barrier (count, generation) of the one-level
+// panel, apart from the multi-level panel's words so that the two can follow one another
+constexpr int kFlatBarWord = 2, kFlatBarWords = 2;
 void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t& cnt_words);
 int panel_qr(const PanelCall& c, cudaStream_t st);
 // One-level-tree variant (panel_flat.cu); LLS_ERR_UNSUPPORTED when the panel needs a deeper tree.
 int panel_flat_qr(const PanelCall& c, cudaStream_t st);
+// Two one-level panels and the recursion node between them in one cooperative launch
+// (panel_flat.cu): columns [c0, c0 + w1) and [c0 + w1, c0 + w1 + w2), 8 < w1 <= 16,
+// 1 <= w2 <= w1, FP16 or BF16 products. LLS_ERR_UNSUPPORTED (nothing launched) otherwise.
+struct BlockCall {
+    float* W; int ldw;
+    void* Wh; int ldh;
+    float* R; int ldr;
+    int m, c0, w1, w2;
+    int lowp;              // 0 FP16, 1 BF16
+    float* rbuf; unsigned* cnt;
+    float* part; size_t part_floats;
+    unsigned* colmax;      // 16 words, zero on entry (left zero)
+    int* err;
+};
+int block_fused_qr(const BlockCall& c, cudaStream_t st);
 
 // ---- scale / cast (cast.cu) ---------------------------------------------------------------
 // For columns [c0, c0 + w) of the FP32 matrix X (m rows, ldx): e_j = column scale exponent
@@ -31,9 +49,9 @@ int scale_cast_columns(const float* X, int ldx, int m, int c0, int w, void* Xh, 
 int rowmajor_copy8(const void* X, int ldx, int m, int c0, int w, void* T, int ldt, cudaStream_t st);
 
 // ---- tensor-core products (gemm_tc.cu) ----------------------------------------------------
-// G1 (Alg. 2 line 8): part[s] = Q1l^T A2l over K-split s; then R12 = sum_s part[s] * 2^-e_j
+// G1 (Alg. 2, projection): part[s] = Q1l^T A2l over K-split s; then R12 = sum_s part[s] * 2^-e_j
 //     written to R (FP32), and R12l = round(R12 * 2^f_j) with its own column exponents f_j.
-// G2 (Alg. 2 line 9): A2 -= (Q1l R12l) * 2^-f_j, FP32 in place.
+// G2 (Alg. 2, update): A2 -= (Q1l R12l) * 2^-f_j, FP32 in place.
 struct ProjCall {
     const void* Q1l; const void* A2l; int ldh;   // low-precision operands (column-major, ld ldh)
     int m, w1, w2;                                // M = w1, N = w2, K = m

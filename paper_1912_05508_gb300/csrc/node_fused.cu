@@ -1,4 +1,4 @@
-// One narrow recursion node (Alg. 2 lines 8-9, w1 <= 32 columns) in a single cooperative
+// One narrow recursion node (the projection and update of Alg. 2, w1 <= 32 columns) in a single cooperative
 // launch, with the same rounding points as the tensor-core path:
 //
 //   A. every CTA owns 256 rows: it loads its rows of Q1 (product precision) and A2 (FP32)
@@ -16,6 +16,7 @@
 // the FP32 accumulation. Every grid-barrier wait is bounded.
 #include <mma.h>
 
+#include "cgs2.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -55,27 +56,6 @@ struct NodeSmem {
     float part_g[kNT];
     float colm[W1];
 };
-
-// Lane L ends with the warp-wide maximum of value index (L mod S), S <= 32.
-template <int S>
-__device__ __forceinline__ float warp_transpose_max(float (&x)[S]) {
-    static_assert(S >= 1 && S <= 32 && (S & (S - 1)) == 0, "one power-of-two chunk of at most 32 values");
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = S / 2; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = up ? x[i] : x[i + o];
-            const float keep = up ? x[i + o] : x[i];
-            x[i] = fmaxf(keep, __shfl_xor_sync(kFullMask, send, o));
-        }
-    }
-    float r = x[0];
-#pragma unroll
-    for (int o = S; o < 32; o <<= 1) r = fmaxf(r, __shfl_xor_sync(kFullMask, r, o));
-    return r;
-}
 
 template <typename TL> struct WmmaT;
 template <> struct WmmaT<__half> { using type = __half; };

@@ -294,7 +294,8 @@ panel_coop_kernel(PanelArgs a) {
 // ---------------------------------------------------------------------------------------
 static int bucket(int b) { return b <= 8 ? 8 : (b <= 16 ? 16 : 32); }
 
-constexpr int kSyncWords = 2;   // cnt[0..1]: root-done flag and exit count of the one-launch path
+constexpr int kSyncWords = 2 + kFlatBarWords;   // cnt[0..1]: root-done flag and exit count of the
+                                                  // one-launch path; then the one-level panel's barrier
 
 static void panel_levels(int m, int b, PanelLevels& lv, int& P0, int& fanin) {
     P0 = ceil_div(m, kNodeRows);

@@ -21,6 +21,8 @@
 // orthogonalised twice; in exact arithmetic Q and R are those of CGS2. The column loop is
 // unrolled in groups of four columns, so every register index is a constant and each step
 // forms at most three products it does not need.
+#include <mma.h>
+
 #include "cgs2.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -41,7 +43,7 @@ struct FlatArgs {
     float* R; int ldr;
     int m, c0, b, P0, lowp;
     float* rbuf;            // P0 row-major B x B blocks: the leaf R factors
-    unsigned* bar;          // [0] arrivals, [1] departures: zero on entry, reset by the last CTA
+    unsigned* bar;          // grid barrier words (count, generation): count zero on entry
     int* err;
 };
 
@@ -53,12 +55,6 @@ struct FlatSmem {
     __align__(16) float S[B][B];         // this block's slice of the tree's Q
     int ok;
 };
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // CTA-wide sums of the N (<= 64) values x[] held by every thread. Returns this warp's row of
 // `tot`, whose entries 0..N-1 hold the CTA totals. One barrier; `red` alternates between
@@ -353,27 +349,16 @@ __device__ __forceinline__ void flat_write_r(const FlatArgs& a, const FlatSmem<B
     }
 }
 
+// The panel of columns [a.c0, a.c0 + b), this CTA's rows [s, s + rows) of which are in v:
+// leaf factorization, the one-level tree and the reconstruction. Q goes to W and Wh, R to R
+// (CTA 0). On return v holds this CTA's rows of Q (zero beyond `rows`). Returns false if a
+// bounded grid barrier gave up (the error word is set).
 template <int B, int RL, bool MGS>
-__global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
-    extern __shared__ __align__(16) unsigned char flat_smem[];
-    FlatSmem<B>& sm = *reinterpret_cast<FlatSmem<B>*>(flat_smem);
-    float* Ql = reinterpret_cast<float*>(flat_smem + sizeof(FlatSmem<B>));   // [RL * kFT][B + 1]
+__device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B], FlatSmem<B>& sm, float* Ql, int& parity,
+                           int s, int rows) {
     const int t = threadIdx.x, b = a.b;
-    int parity = 0;
     for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
     for (int i = t; i < B * B; i += kFT) (&sm.S[0][0])[i] = 0.f;
-    int s, e;
-    flat_leaf_range(a.m, a.P0, blockIdx.x, s, e);
-    const int rows = e - s;
-
-    float v[RL][B];
-#pragma unroll
-    for (int r = 0; r < RL; ++r) {
-        const int lr = t + r * kFT;
-#pragma unroll
-        for (int j = 0; j < B; ++j)
-            v[r][j] = (lr < rows && j < b) ? a.W[(size_t)(s + lr) + (size_t)(a.c0 + j) * a.ldw] : 0.f;
-    }
     __syncthreads();
     leaf_qr<MGS, B, RL>(v, b, sm, parity, 0);
     __syncthreads();
@@ -388,7 +373,8 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
                 if (j < b) flat_store_q(a, s + lr, j, v[r][j]);
         }
         flat_write_r<B>(a, sm);
-        return;
+        __syncthreads();
+        return true;
     }
 
     // leaf Q to shared memory, leaf R to the workspace
@@ -403,87 +389,316 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
     for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
 
     // bounded grid barrier: every leaf R is in the workspace
-    if (t == 0) {
-        atomicAdd(a.bar, 1u);
-        int ok = 1;
-        const unsigned long long t0 = globaltimer_ns();
-        while (ld_acquire_u32(a.bar) < (unsigned)a.P0) {
-            if (globaltimer_ns() - t0 > kSpinLimitNs) {
-                atomicCAS(a.err, DEV_OK, DEV_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
+    if (!grid_barrier(a.bar, a.P0, a.err)) return false;
+
+    // the stacked R factors, row-index-major: thread t holds row rr = t / TPR of the R
+    // factors of children (t mod TPR) + TPR r, so each warp holds one or two row indices
+    // (rr0 = its first) and can skip the steps where its rows are still zero
+    constexpr int TPR = kFT / B;
+    const int rr = t / TPR, cl = t % TPR;
+    float vr[kRootRPT][B];
+#pragma unroll
+    for (int r = 0; r < kRootRPT; ++r) {
+        const int child = cl + TPR * r;
+        const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
+        const bool live = child < a.P0 && rr < b;
+#pragma unroll
+        for (int j4 = 0; j4 < B / 4; ++j4) {
+            const float4 q = live ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
         }
-        sm.ok = ok;
+    }
+    leaf_qr<MGS, B, kRootRPT>(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
+    // this block's b x b slice of the tree's Q: the rows of child blockIdx.x
+#pragma unroll
+    for (int r = 0; r < kRootRPT; ++r) {
+        if (cl + TPR * r == (int)blockIdx.x && rr < b)
+#pragma unroll
+            for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
     }
     __syncthreads();
-
-    if (sm.ok) {
-        // the stacked R factors, row-index-major: thread t holds row rr = t / TPR of the R
-        // factors of children (t mod TPR) + TPR r, so each warp holds one or two row indices
-        // (rr0 = its first) and can skip the steps where its rows are still zero
-        constexpr int TPR = kFT / B;
-        const int rr = t / TPR, cl = t % TPR;
-        float vr[kRootRPT][B];
+    if (blockIdx.x == 0) flat_write_r<B>(a, sm);
+    // Q = Q_leaf * S
 #pragma unroll
-        for (int r = 0; r < kRootRPT; ++r) {
-            const int child = cl + TPR * r;
-            const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
-            const bool live = child < a.P0 && rr < b;
+    for (int r = 0; r < RL; ++r) {
+        const int lr = t + r * kFT;
+        if (lr >= rows) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) v[r][j] = 0.f;
+            continue;
+        }
+        float q[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) q[k] = Ql[lr * (B + 1) + k];
+        float o[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) o[j] = 0.f;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const float4* Sk = reinterpret_cast<const float4*>(&sm.S[k][0]);
 #pragma unroll
             for (int j4 = 0; j4 < B / 4; ++j4) {
-                const float4 q = live ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
-                vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
+                const float4 s4 = Sk[j4];
+                o[4 * j4 + 0] = fmaf(q[k], s4.x, o[4 * j4 + 0]);
+                o[4 * j4 + 1] = fmaf(q[k], s4.y, o[4 * j4 + 1]);
+                o[4 * j4 + 2] = fmaf(q[k], s4.z, o[4 * j4 + 2]);
+                o[4 * j4 + 3] = fmaf(q[k], s4.w, o[4 * j4 + 3]);
             }
         }
-        leaf_qr<MGS, B, kRootRPT>(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
-        // this block's b x b slice of the tree's Q: the rows of child blockIdx.x
 #pragma unroll
-        for (int r = 0; r < kRootRPT; ++r) {
-            if (cl + TPR * r == (int)blockIdx.x && rr < b)
-#pragma unroll
-                for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
+        for (int j = 0; j < B; ++j) {
+            v[r][j] = o[j];
+            if (j < b) flat_store_q(a, s + lr, j, o[j]);
         }
+    }
+    __syncthreads();   // Ql, S and Rs are free again
+    return true;
+}
+
+template <int B, int RL>
+__device__ __forceinline__ void load_rows(const FlatArgs& a, int c0, float (&v)[RL][B], int s, int rows, int ncol) {
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+        const int lr = threadIdx.x + r * kFT;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            v[r][j] = (lr < rows && j < ncol) ? a.W[(size_t)(s + lr) + (size_t)(c0 + j) * a.ldw] : 0.f;
+    }
+}
+
+template <int B, int RL, bool MGS>
+__global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
+    extern __shared__ __align__(128) unsigned char flat_smem[];
+    FlatSmem<B>& sm = *reinterpret_cast<FlatSmem<B>*>(flat_smem);
+    float* Ql = reinterpret_cast<float*>(flat_smem + sizeof(FlatSmem<B>));   // [RL * kFT][B + 1]
+    int parity = 0;
+    int s, e;
+    flat_leaf_range(a.m, a.P0, blockIdx.x, s, e);
+    float v[RL][B];
+    load_rows<B, RL>(a, a.c0, v, s, e - s, a.b);
+    panel_body<B, RL, MGS>(a, v, sm, Ql, parity, s, e - s);
+}
+
+// ---- a block of two panels and the recursion node between them, in one launch ----------
+//
+// At the lowest internal nodes of the recursion (w = w1 + w2 with w1 = the panel width) the
+// left panel, the node's two products and the right panel run as one cooperative launch; the
+// CTAs keep the same rows throughout, so A2 goes from its load through the update into the
+// second panel in registers:
+//   1. panel of columns [c0, c0 + w1) (panel_body): Q1 rows in registers, Q1l = round(Q1) in
+//      shared memory (the copy the panel also stores to Wh);
+//   2. FP16: column maxima of |A2| per CTA -> grid barrier -> e_j; A2l = round(A2 2^e_j);
+//   3. the CTA's partial Q1l^T A2l (warp MMAs, FP32 accumulation, fixed-order warp sum)
+//      -> grid barrier -> every CTA sums the P0 partials in the same fixed order, so all hold
+//      the same R12 = sum 2^-e_j (CTA 0 writes it to R), f_j and R12l = round(R12 2^f_j);
+//   4. A2 -= (Q1l R12l) 2^-f_j for the CTA's rows (warp MMAs, FP32), in registers;
+//   5. panel of columns [c0 + w1, c0 + w1 + w2) on the updated rows.
+// The rounding points are those of the separate kernels (Alg. 2 with the column scaling of
+// Sec. 3.1.2); only the order of the FP32 accumulations differs.
+
+constexpr int kBlkLdK = 8;          // padding (halves) of the K-contiguous operand rows
+constexpr int kUsLd = 20;           // row stride (floats) of the update products
+
+constexpr int kBlockMaxP0 = kStackRows / 16;   // CTAs of a one-level panel of width 16
+
+struct BlockArgs {
+    FlatArgs p1, p2;                // the two panels
+    float* part;                    // P0 x 256 projection partials
+    unsigned* colmax;               // 16 words: bits of max |A2_:j| (zero on entry, left zero)
+    int w1, w2, kind;               // kind: 1 FP16 column scaling, 0 none (BF16)
+};
+
+template <typename TL, int RL>
+struct BlockSmem {
+    __align__(32) TL Qs[16][RL * kFT + kBlkLdK];   // Q1l: Qs[i][row]
+    __align__(32) TL As[16][RL * kFT + kBlkLdK];   // A2l: As[j][row]
+    __align__(32) TL Rl[16][16];                   // R12l column-major: Rl[j][i]
+    __align__(32) float wp[kFW][256];              // per-warp projection partials (column-major)
+    __align__(32) float us[kFW][32][kUsLd];        // per-warp update products, row-major
+    float r12[16][17];                             // R12: r12[j][i]
+    float red[kFW][16];                            // per-warp column maxima
+    float sc[16], einv[16], fpos[16], fneg[16];    // 2^e_j, 2^-e_j, 2^f_j, 2^-f_j
+};
+
+template <int RL>
+constexpr size_t block_ql_off() { return (sizeof(FlatSmem<16>) + 127) / 128 * 128; }
+template <typename TL, int RL>
+constexpr size_t block_node_off() {
+    return (block_ql_off<RL>() + sizeof(float) * RL * kFT * 17 + 127) / 128 * 128;
+}
+template <typename TL, int RL>
+constexpr size_t block_smem_bytes() { return block_node_off<TL, RL>() + sizeof(BlockSmem<TL, RL>); }
+
+// Steps 1 (Q1l), 2, 3 and 4 of the block for this CTA's rows: on entry v holds the rows of Q1,
+// on return the rows of the updated A2. False if a grid barrier gave up.
+template <typename TL, int RL>
+__device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16], BlockSmem<TL, RL>& bs,
+                                           int s, int rows) {
+    using namespace nvcuda;
+    constexpr int kLd = RL * kFT + kBlkLdK;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int P0 = a.p1.P0, w1 = a.w1, w2 = a.w2;
+#pragma unroll
+    for (int r = 0; r < RL; ++r)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bs.Qs[i][t + r * kFT] = LowPrec<TL>::from_float(v[r][i]);
+
+    // 2. A2 rows; FP16 column scaling from the global column maxima
+    load_rows<16, RL>(a.p1, a.p1.c0 + w1, v, s, rows, w2);
+    if (a.kind != 0) {
+        float mx[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float x = 0.f;
+#pragma unroll
+            for (int r = 0; r < RL; ++r) x = fmaxf(x, fabsf(v[r][j]));
+            mx[j] = x;
+        }
+        const float wm = warp_transpose_max<16>(mx);
+        if (lane < 16) bs.red[warp][lane] = wm;
         __syncthreads();
-        if (blockIdx.x == 0) flat_write_r<B>(a, sm);
-        // Q = Q_leaf * S
+        if (t < w2) {
+            float x = 0.f;
+#pragma unroll
+            for (int q = 0; q < kFW; ++q) x = fmaxf(x, bs.red[q][t]);
+            atomicMax(a.colmax + t, __float_as_uint(x));   // non-negative floats order as their bits
+        }
+        if (!grid_barrier(a.p1.bar, P0, a.p1.err)) return false;
+        if (t < 16) {
+            const float x = t < w2 ? __uint_as_float(__ldcg(a.colmax + t)) : 0.f;
+            const int ej = scale_exponent(1, x);
+            bs.sc[t] = pow2f(ej);
+            bs.einv[t] = pow2f(-ej);
+        }
+    } else if (t < 16) {
+        bs.sc[t] = 1.f;
+        bs.einv[t] = 1.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RL; ++r)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) bs.As[j][t + r * kFT] = LowPrec<TL>::from_float(v[r][j] * bs.sc[j]);
+    __syncwarp();   // a warp's MMA steps read only the rows its own lanes wrote
+
+    // 3. projection partials: warp w takes the 32-row slices w of every 256-row group
+    {
+        wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
+        wmma::fill_fragment(acc, 0.f);
+#pragma unroll
+        for (int r = 0; r < RL; ++r)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k0 = r * kFT + warp * 32 + h * 16;
+                wmma::fragment<wmma::matrix_a, 16, 16, 16, TL, wmma::row_major> fa;
+                wmma::fragment<wmma::matrix_b, 16, 16, 16, TL, wmma::col_major> fb;
+                wmma::load_matrix_sync(fa, &bs.Qs[0][k0], kLd);
+                wmma::load_matrix_sync(fb, &bs.As[0][k0], kLd);
+                wmma::mma_sync(acc, fa, fb, acc);
+            }
+        wmma::store_matrix_sync(&bs.wp[warp][0], acc, 16, wmma::mem_col_major);
+    }
+    __syncthreads();
+    {
+        float x = 0.f;
+#pragma unroll
+        for (int q = 0; q < kFW; ++q) x += bs.wp[q][t];   // entry (t mod 16, t / 16)
+        a.part[(size_t)blockIdx.x * 256 + t] = x;
+    }
+    if (!grid_barrier(a.p1.bar, P0, a.p1.err)) return false;
+    // every CTA has read the column maxima before the barrier above: CTA 0 clears them
+    if (blockIdx.x == 0 && a.kind != 0 && t < w2) a.colmax[t] = 0u;
+    {
+        // entry t summed over the P0 partials in a fixed order; all loads are issued first
+        const float* p = a.part + t;
+        float x[kBlockMaxP0];
+#pragma unroll
+        for (int c = 0; c < kBlockMaxP0; ++c) x[c] = c < P0 ? __ldcg(p + (size_t)c * 256) : 0.f;
+        float acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float s8 = 0.f;
+#pragma unroll
+            for (int c = u; c < kBlockMaxP0; c += 8) s8 += x[c];
+            acc[u] = s8;
+        }
+        const float tot = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        const int i = t & 15, j = t >> 4;
+        const bool live = i < w1 && j < w2;
+        const float r12 = live ? tot * bs.einv[j] : 0.f;
+        bs.r12[j][i] = r12;
+        if (blockIdx.x == 0 && live)
+            a.p1.R[(size_t)(a.p1.c0 + i) + (size_t)(a.p1.c0 + w1 + j) * a.p1.ldr] = r12;
+    }
+    __syncthreads();
+    if (t < 16) {
+        float mx = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(bs.r12[t][i]));
+        const int fj = scale_exponent(a.kind, mx);
+        bs.fpos[t] = pow2f(fj);
+        bs.fneg[t] = pow2f(-fj);
+    }
+    __syncthreads();
+    bs.Rl[t >> 4][t & 15] = LowPrec<TL>::from_float(bs.r12[t >> 4][t & 15] * bs.fpos[t >> 4]);
+    __syncthreads();
+
+    // 4. A2 -= (Q1l R12l) 2^-f_j on this warp's rows
+    {
+        float* us = &bs.us[warp][0][0];
+        wmma::fragment<wmma::matrix_b, 16, 16, 16, TL, wmma::col_major> fb;
+        wmma::load_matrix_sync(fb, &bs.Rl[0][0], 16);
+        float fneg[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) fneg[j] = bs.fneg[j];
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
-            const int lr = t + r * kFT;
-            if (lr >= rows) continue;
-            float q[B];
 #pragma unroll
-            for (int k = 0; k < B; ++k) q[k] = Ql[lr * (B + 1) + k];
-            float o[B];
-#pragma unroll
-            for (int j = 0; j < B; ++j) o[j] = 0.f;
-#pragma unroll
-            for (int k = 0; k < B; ++k) {
-                const float4* Sk = reinterpret_cast<const float4*>(&sm.S[k][0]);
-#pragma unroll
-                for (int j4 = 0; j4 < B / 4; ++j4) {
-                    const float4 s4 = Sk[j4];
-                    o[4 * j4 + 0] = fmaf(q[k], s4.x, o[4 * j4 + 0]);
-                    o[4 * j4 + 1] = fmaf(q[k], s4.y, o[4 * j4 + 1]);
-                    o[4 * j4 + 2] = fmaf(q[k], s4.z, o[4 * j4 + 2]);
-                    o[4 * j4 + 3] = fmaf(q[k], s4.w, o[4 * j4 + 3]);
-                }
+            for (int h = 0; h < 2; ++h) {
+                wmma::fragment<wmma::matrix_a, 16, 16, 16, TL, wmma::col_major> fa;
+                wmma::load_matrix_sync(fa, &bs.Qs[0][r * kFT + warp * 32 + h * 16], kLd);
+                wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
+                wmma::fill_fragment(acc, 0.f);
+                wmma::mma_sync(acc, fa, fb, acc);
+                wmma::store_matrix_sync(us + h * 16 * kUsLd, acc, kUsLd, wmma::mem_row_major);
             }
+            __syncwarp();
+            const float4* u4 = reinterpret_cast<const float4*>(us + lane * kUsLd);
 #pragma unroll
-            for (int j = 0; j < B; ++j)
-                if (j < b) flat_store_q(a, s + lr, j, o[j]);
+            for (int j4 = 0; j4 < 4; ++j4) {
+                const float4 u = u4[j4];
+                v[r][4 * j4 + 0] = fmaf(-u.x, fneg[4 * j4 + 0], v[r][4 * j4 + 0]);
+                v[r][4 * j4 + 1] = fmaf(-u.y, fneg[4 * j4 + 1], v[r][4 * j4 + 1]);
+                v[r][4 * j4 + 2] = fmaf(-u.z, fneg[4 * j4 + 2], v[r][4 * j4 + 2]);
+                v[r][4 * j4 + 3] = fmaf(-u.w, fneg[4 * j4 + 3], v[r][4 * j4 + 3]);
+            }
+            __syncwarp();
         }
     }
 
-    // departure: the last CTA out resets the barrier words for the next panel
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        if (atomicAdd(a.bar + 1, 1u) == (unsigned)(a.P0 - 1)) {
-            atomicExch(a.bar, 0u);
-            atomicExch(a.bar + 1, 0u);
-        }
+    return true;
+}
+
+template <typename TL, int RL>
+__global__ void __launch_bounds__(kFT, 1) block_fused_kernel(BlockArgs a) {
+    extern __shared__ __align__(128) unsigned char flat_smem[];
+    FlatSmem<16>& sm = *reinterpret_cast<FlatSmem<16>*>(flat_smem);
+    float* Ql = reinterpret_cast<float*>(flat_smem + block_ql_off<RL>());
+    BlockSmem<TL, RL>& bs = *reinterpret_cast<BlockSmem<TL, RL>*>(flat_smem + block_node_off<TL, RL>());
+    int parity = 0, s, e;
+    flat_leaf_range(a.p1.m, a.p1.P0, blockIdx.x, s, e);
+    const int rows = e - s;
+    float v[RL][16];
+    load_rows<16, RL>(a.p1, a.p1.c0, v, s, rows, a.w1);
+    // the two panels share one copy of the panel code (a two-trip loop), which keeps the
+    // kernel within the instruction cache
+    FlatArgs pa = a.p1;
+#pragma unroll 1
+    for (int pass = 0;; ++pass) {
+        if (!panel_body<16, RL, false>(pa, v, sm, Ql, parity, s, rows)) return;   // 1. / 5.
+        if (pass == 1) break;
+        if (!block_node<TL, RL>(a, v, bs, s, rows)) return;                      // 1. - 4.
+        pa = a.p2;
     }
 }
 
@@ -532,6 +747,48 @@ static int launch_flat(FlatArgs& a, cudaStream_t st) {
     return LLS_OK;
 }
 
+template <typename TL, int RL>
+static int launch_block(BlockArgs& a, cudaStream_t st) {
+    constexpr int kMaxDev = 64;
+    static int cap[kMaxDev];
+    static bool done[kMaxDev];
+    int dev = 0;
+    LLS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) return LLS_ERR_UNSUPPORTED;
+    const size_t smem = block_smem_bytes<TL, RL>();
+    if (!done[dev]) {
+        LLS_CUDA_TRY(cudaFuncSetAttribute(block_fused_kernel<TL, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        int sms = 0, per = 0;
+        LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, block_fused_kernel<TL, RL>, kFT, smem));
+        cap[dev] = sms * per;
+        done[dev] = true;
+    }
+    if (a.p1.P0 > cap[dev]) return LLS_ERR_UNSUPPORTED;
+    if (a.p1.P0 == 1) {
+        block_fused_kernel<TL, RL><<<1, kFT, smem, st>>>(a);
+    } else {
+        void* args[] = {&a};
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)block_fused_kernel<TL, RL>, dim3(a.p1.P0), dim3(kFT), args,
+                                                 smem, st));
+    }
+    LLS_LAUNCH_CHECK("block_fused", st);
+    return LLS_OK;
+}
+
+// Rows per thread and number of CTAs of a one-level panel of m rows and bucketed width bw;
+// false when the stacked leaf R factors would not fit one block.
+static bool flat_shape(int m, int bw, int& rl, int& P0) {
+    const int p2 = ceil_div(m, 2 * kFT), p4 = ceil_div(m, 4 * kFT);
+    if (m <= 2 * kFT) { rl = 2; P0 = 1; }
+    else if (m <= 4 * kFT) { rl = 4; P0 = 1; }
+    else if (p2 * bw <= kStackRows) { rl = 2; P0 = p2; }
+    else if (p4 * bw <= kStackRows) { rl = 4; P0 = p4; }
+    else return false;
+    return true;
+}
+
 bool flat_disabled() {
     static const bool off = [] {
         const char* s = getenv("LLS_PANEL");
@@ -548,21 +805,35 @@ int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
     FlatArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh; a.R = c.R; a.ldr = c.ldr;
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
-    a.rbuf = c.rbuf; a.bar = c.cnt; a.err = c.err;
-    const int p2 = ceil_div(c.m, 2 * kFT), p4 = ceil_div(c.m, 4 * kFT);
+    a.rbuf = c.rbuf; a.bar = c.cnt + kFlatBarWord; a.err = c.err;
     const int bw = c.b <= 8 ? 8 : 16;   // the stack holds TPR * 4 children of B rows each
     int rl;
-    if (c.m <= 2 * kFT) { rl = 2; a.P0 = 1; }
-    else if (c.m <= 4 * kFT) { rl = 4; a.P0 = 1; }
-    else if (p2 * bw <= kStackRows) { rl = 2; a.P0 = p2; }
-    else if (p4 * bw <= kStackRows) { rl = 4; a.P0 = p4; }
-    else return LLS_ERR_UNSUPPORTED;
+    if (!flat_shape(c.m, bw, rl, a.P0)) return LLS_ERR_UNSUPPORTED;
     if (c.leaf == 1) {
         if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, true>(a, st) : launch_flat<8, 4, true>(a, st);
         return rl == 2 ? launch_flat<16, 2, true>(a, st) : launch_flat<16, 4, true>(a, st);
     }
     if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, false>(a, st) : launch_flat<8, 4, false>(a, st);
     return rl == 2 ? launch_flat<16, 2, false>(a, st) : launch_flat<16, 4, false>(a, st);
+}
+
+int block_fused_qr(const BlockCall& c, cudaStream_t st) {
+    if (flat_disabled() || (c.lowp != 0 && c.lowp != 1)) return LLS_ERR_UNSUPPORTED;
+    if (c.w1 <= 8 || c.w1 > 16 || c.w2 < 1 || c.w2 > c.w1) return LLS_ERR_UNSUPPORTED;
+    BlockArgs a;
+    FlatArgs& p = a.p1;
+    p.W = c.W; p.ldw = c.ldw; p.Wh = c.Wh; p.ldh = c.ldh; p.R = c.R; p.ldr = c.ldr;
+    p.m = c.m; p.c0 = c.c0; p.b = c.w1; p.lowp = c.lowp;
+    p.rbuf = c.rbuf; p.bar = c.cnt + kFlatBarWord; p.err = c.err;
+    int rl;
+    if (!flat_shape(c.m, 16, rl, p.P0)) return LLS_ERR_UNSUPPORTED;
+    if (p.P0 > kBlockMaxP0 || (size_t)p.P0 * 256 > c.part_floats) return LLS_ERR_UNSUPPORTED;
+    a.p2 = p;
+    a.p2.c0 = c.c0 + c.w1;
+    a.p2.b = c.w2;
+    a.part = c.part; a.colmax = c.colmax; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;
+    if (c.lowp == 0) return rl == 2 ? launch_block<__half, 2>(a, st) : launch_block<__half, 4>(a, st);
+    return rl == 2 ? launch_block<__nv_bfloat16, 2>(a, st) : launch_block<__nv_bfloat16, 4>(a, st);
 }
 
 }  // namespace lls

@@ -1,4 +1,4 @@
-"""GPU parity of the two tensor-core products of a recursion step (Alg. 2 lines 8-9),
+"""GPU parity of the two tensor-core products of a recursion step (Alg. 2: projection and update),
 through the kernel-level C entry points, against an FP64 product of the SAME rounded inputs.
 
 Bound: with FP32 accumulation over K terms, |fl(sum) - sum| <= K * u32 * sum |a_k b_k|

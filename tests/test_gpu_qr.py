@@ -69,6 +69,42 @@ def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
     assert fe >= metrics.qr_factorization_error(A, Qo, Ro) / 16
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("m,n", [(40000, 64), (3000, 24), (600, 17), (20000, 48)])
+def test_two_panel_blocks_match_oracle(prec, m, n):
+    # The lowest recursion nodes (w1 = 16, w2 <= 16 at panel width 16) run as one launch:
+    # left panel, the node's two products, right panel. m = 40000 takes four rows per thread
+    # over 40 CTAs, m = 600 one CTA; n = 24 and 17 give ragged right halves, n = 48 a block
+    # under a fused 32-wide node.
+    kappa = 1e3
+    A = svd_matrix(m, n, kappa, seed=m + 7 * n)
+    Q, R = gpu_qr(A, prec, 16)
+    Qo, Ro = rgsqrf.rgsqrf(A, 16, prec, leaf_rows=256)
+    u = ULOW[prec]
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    fe = metrics.qr_factorization_error(A, Q, R)
+    assert fe <= 4 * u
+    assert metrics.orthogonality(Q, "2") <= 4 * u * kappa * n ** 0.5
+    assert fe >= metrics.qr_factorization_error(A, Qo, Ro) / 16
+
+
+def test_two_panel_block_is_one_launch():
+    # At panel width 16 a 32-column factorization is one block: it takes as many launches as
+    # a single 16-column panel.
+    A = lls.colmajor(svd_matrix(5000, 32, 1e2, seed=5))
+
+    def launches(n):
+        An = A[:, :n]                                  # column-major view, ld 5000
+        lls.qr(An, prec="fp16", panel_width=16)      # a first call may record its graph
+        torch.cuda.synchronize()
+        c0 = lls.lls_kernel_launch_count()
+        lls.qr(An, prec="fp16", panel_width=16)
+        torch.cuda.synchronize()
+        return lls.lls_kernel_launch_count() - c0
+
+    assert launches(32) == launches(16)
+
+
 def test_column_scaling_handles_wide_column_range():
     # Column norms 10^U(-2, 2): without per-column scaling FP16 would lose the small columns.
     A = synth.scaled_gaussian(2000, 64, seed=11)
