@@ -162,10 +162,11 @@ def run_reference(args):
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
 # it stands, from the captures summarised under profiles/; None once a kernel changes.
 # tc_projection is the product kernel alone (the split-K reduce is a separate, small launch).
-NCU_TRAFFIC = {"panel": 2214912 + 256,
+NCU_TRAFFIC = {"panel": None,
+               "block": None,
                "tc_projection": None,
                "tc_update": None,
-               "cgls": 24844714000 + 392099328}
+               "cgls": None}
 
 
 def max_over_ranks(value, world_size, device):
@@ -238,6 +239,28 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
                     "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "us_per_launch": ms * 1e3, "algorithmic_bytes_per_launch": by}
     del W, Wh
+
+    if prec in ("fp16", "bf16") and pw <= 16 and 2 * pw <= n:
+        # the lowest recursion node as the solve runs it: left panel, node, right panel in one
+        # launch; algorithmic bytes = read m*2pw FP32 + write Q (FP32 and the 2-byte copy)
+        w = 2 * pw
+        nbuf = max(2, -(-(160 << 20) // (m * w * 4)))
+        W = torch.randn((nbuf * w, m), device=dev, generator=g).t()
+        Wh = torch.empty((nbuf * w, m), dtype=tdt, device=dev).t()
+        R = torch.empty((w, w), device=dev)
+        bws = lls.workspace(lls.lls_panel_block_qr_workspace_size(m, pw, pw), dev).zero_()
+
+        def blk(i):
+            k = i % nbuf
+            st = lls.lls_panel_block_qr(m, pw, pw, pcode, W[:, k * w:].data_ptr(), m, Wh[:, k * w:].data_ptr(), m,
+                                        R.data_ptr(), w, bws.data_ptr(), bws.numel(), sh)
+            assert st == 0, st
+        ms = time_launches(blk, 100, stream)
+        by = 10.0 * m * w
+        out["block"] = {"kernel": f"block_fused_kernel (panel {m}x{pw}, node, panel {m}x{pw} in one launch)",
+                        "bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "us_per_launch": ms * 1e3, "algorithmic_bytes_per_launch": by}
+        del W, Wh
 
     if prec not in ("fp16", "bf16"):
         for k, v in out.items():
@@ -455,8 +478,9 @@ def main():
     kernels["cgls"] = {"kernel": f"{args.krylov}_kernel (persistent {args.krylov.upper()} iteration, whole Krylov phase)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                        "traffic": NCU_TRAFFIC["cgls"], "algorithmic_bytes_per_launch": kry_bytes}
-    # the panel has the largest share of the solve in the ncu launch list
-    roofline = dict(kernels["panel"])
+    # the block kernel (two panels and the node between them) has the largest share of the
+    # solve in the ncu launch list
+    roofline = dict(kernels["block"] if "block" in kernels else kernels["panel"])
     roofline["peak_source"] = ("measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peak_src == "measured"
                                else "fallback 6800 GB/s")
     out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,

@@ -242,6 +242,30 @@ int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, f
                  void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * lls_panel_block_qr: the lowest node of the recursion (Alg. 2) in one launch: the panel of
+ * columns [0, w1) (as lls_panel_qr), the node's projection R12 = Q1^T A2 and update
+ * A2 = A2 - Q1 R12 with FP16/BF16 operands, FP32 accumulation and the power-of-two column
+ * scaling of Sec. 3.1.2, then the panel of columns [w1, w1 + w2). Exposed for testing and for
+ * callers that run their own recursion.
+ *   8 < w1 <= 16, 1 <= w2 <= w1, m >= w1 + w2; prec = LLS_PREC_FP16 or LLS_PREC_BF16.
+ *   W   [in/out] m x (w1 + w2) FP32, column-major (ldw >= m): A in, Q out.
+ *   Wh  [out]    m x (w1 + w2) copy of Q rounded to nearest even to prec (ldh >= m).
+ *   R   [out]    (w1 + w2) x (w1 + w2) upper triangular FP32 (ldr >= w1 + w2): R11, R12 and
+ *                R22 of A = Q R; the strict lower triangle is written with zeros.
+ *   ws           lls_panel_block_qr_workspace_size(m, w1, w2) bytes, 256-B aligned. Zero-fill
+ *                it once before its first use: every call leaves it ready for the next call
+ *                on the same stream (calls that overlap on the GPU race).
+ * Asynchronous on `stream`. All CTAs must be co-resident (cooperative launch); each grid
+ * wait is bounded (about 2 s) and, if it gives up, Q and R are undefined, the call's error
+ * word stays set and the workspace must be zero-filled again.
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_CUDA; LLS_ERR_UNSUPPORTED (nothing launched)
+ * when m is beyond the one-level panel (m > 65536) or w1, w2 are outside the range above.
+ * -------------------------------------------------------------------------- */
+size_t lls_panel_block_qr_workspace_size(int m, int w1, int w2);
+int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
+                       int ldr, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Plain Householder least squares (Alg. 1, Sec. 3.2.2): the comparison solver the
  * mixed-precision method is measured against, in FP64 (prec = LLS_PREC_FP64) or FP32
  * (LLS_PREC_FP32) arithmetic throughout. Blocked Householder QR of [A, b] in compact-WY

@@ -405,6 +405,45 @@ int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, f
     return panel_qr(p, stream);
 }
 
+struct BlockWs {
+    PanelWs p; float* part; unsigned* colmax;
+};
+
+static void block_layout(WsArena& ar, int m, BlockWs& w) {
+    panel_layout(ar, m, w.p);
+    w.part = ar.take<float>(block_fused_part_floats());
+    w.colmax = ar.take<unsigned>(16);
+}
+
+size_t lls_panel_block_qr_workspace_size(int m, int w1, int w2) {
+    if (m < 1 || w1 < 1 || w2 < 1 || m < w1 + w2) return 0;
+    WsArena ar(nullptr, ~(size_t)0);
+    BlockWs w;
+    block_layout(ar, m, w);
+    return ar.off;
+}
+
+int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
+                       int ldr, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (w1 < 1 || w2 < 1 || m < w1 + w2 || ldw < m || ldh < m || ldr < w1 + w2) return LLS_ERR_ARG;
+    if (!W || !Wh || !R || !ws) return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP16 && prec != LLS_PREC_BF16) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, ws_bytes);
+    BlockWs w;
+    block_layout(ar, m, w);
+    if (!ar.ok) return LLS_ERR_WORKSPACE;
+    BlockCall bc;
+    bc.W = W; bc.ldw = ldw; bc.Wh = Wh; bc.ldh = ldh; bc.R = R; bc.ldr = ldr;
+    bc.m = m; bc.c0 = 0; bc.w1 = w1; bc.w2 = w2; bc.lowp = lowp_code(prec);
+    bc.rbuf = w.p.rbuf; bc.cnt = w.p.cnt; bc.part = w.part; bc.part_floats = block_fused_part_floats();
+    bc.colmax = w.colmax; bc.err = w.p.err;
+    if (!block_fused_supported(bc)) return LLS_ERR_UNSUPPORTED;
+    const size_t wt = (size_t)(w1 + w2);
+    LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * wt, wt, stream));
+    return block_fused_qr(bc, stream);
+}
+
 static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w, float*& R,
                        float*& Minv, float*& Mt, float*& tmp, void*& ks, size_t& ks_bytes) {
     qr_layout(ar, m, n, o, w);

@@ -39,6 +39,8 @@ struct BlockCall {
     int* err;
 };
 int block_fused_qr(const BlockCall& c, cudaStream_t st);
+bool block_fused_supported(const BlockCall& c);   // the shape checks of block_fused_qr alone
+size_t block_fused_part_floats();                  // partial sums the block needs at most
 
 // ---- scale / cast (cast.cu) ---------------------------------------------------------------
 // For columns [c0, c0 + w) of the FP32 matrix X (m rows, ldx): e_j = column scale exponent

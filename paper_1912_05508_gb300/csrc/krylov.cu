@@ -39,7 +39,8 @@ constexpr int kKThreads = 256;
 constexpr int kKWarps = kKThreads / 32;
 constexpr int kRowTile = 1024;    // rows per A t work item (four rows per thread)
 constexpr int kColChunk = 64;     // columns per A t work item
-constexpr int kRowChunk = 2048;   // rows per A^T r work item (staged in shared memory)
+constexpr int kRowChunk = 1024;   // rows per A^T r work item (staged in shared memory); 4096
+                                  // items at m = 32768, n = 4096 fill 9 waves of 456 CTAs
 constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
 constexpr int kMaxRestarts = 3;
 constexpr int kPrefetchCols = 8;  // L2 prefetch distance of the A passes (columns, or 32-lane steps)
@@ -146,6 +147,7 @@ __device__ __forceinline__ double sum_parts_quad(const double* __restrict__ p, i
     double s0 = 0.0, s1 = 0.0;
     if (valid) {
         int k = sub;
+#pragma unroll 4   // loads of later trips issue ahead of the (ordered) additions
         for (; k + 4 < count; k += 8) {
             s0 += __ldcg(p + (size_t)k * stride);
             s1 += __ldcg(p + (size_t)(k + 4) * stride);

@@ -307,9 +307,11 @@ struct MgsFlat<B, R, B> {
     static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
 };
 
+constexpr int kCgsGroup = 4;       // CGS2 steps per shared group body
+
 template <int B, int R, int K0>
 struct Cgs2Flat {
-    static constexpr int KG = 4;
+    static constexpr int KG = kCgsGroup < B ? kCgsGroup : B;
     static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
         if (K0 >= b) return;
         cgs2_group<B, R, K0, KG>(v, b, sm, parity, rr0);
@@ -817,17 +819,24 @@ int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
     return rl == 2 ? launch_flat<16, 2, false>(a, st) : launch_flat<16, 4, false>(a, st);
 }
 
+size_t block_fused_part_floats() { return (size_t)kBlockMaxP0 * 256; }
+
+bool block_fused_supported(const BlockCall& c) {
+    if (flat_disabled() || (c.lowp != 0 && c.lowp != 1)) return false;
+    if (c.w1 <= 8 || c.w1 > 16 || c.w2 < 1 || c.w2 > c.w1) return false;
+    int rl, P0;
+    return flat_shape(c.m, 16, rl, P0) && P0 <= kBlockMaxP0 && (size_t)P0 * 256 <= c.part_floats;
+}
+
 int block_fused_qr(const BlockCall& c, cudaStream_t st) {
-    if (flat_disabled() || (c.lowp != 0 && c.lowp != 1)) return LLS_ERR_UNSUPPORTED;
-    if (c.w1 <= 8 || c.w1 > 16 || c.w2 < 1 || c.w2 > c.w1) return LLS_ERR_UNSUPPORTED;
+    if (!block_fused_supported(c)) return LLS_ERR_UNSUPPORTED;
     BlockArgs a;
     FlatArgs& p = a.p1;
     p.W = c.W; p.ldw = c.ldw; p.Wh = c.Wh; p.ldh = c.ldh; p.R = c.R; p.ldr = c.ldr;
     p.m = c.m; p.c0 = c.c0; p.b = c.w1; p.lowp = c.lowp;
     p.rbuf = c.rbuf; p.bar = c.cnt + kFlatBarWord; p.err = c.err;
     int rl;
-    if (!flat_shape(c.m, 16, rl, p.P0)) return LLS_ERR_UNSUPPORTED;
-    if (p.P0 > kBlockMaxP0 || (size_t)p.P0 * 256 > c.part_floats) return LLS_ERR_UNSUPPORTED;
+    flat_shape(c.m, 16, rl, p.P0);
     a.p2 = p;
     a.p2.c0 = c.c0 + c.w1;
     a.p2.b = c.w2;

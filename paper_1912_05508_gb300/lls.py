@@ -27,6 +27,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_backward_workspace_size", "lls_backward",
            "lls_solve_batched_workspace_size", "lls_solve_batched",
            "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr",
+           "lls_panel_block_qr_workspace_size", "lls_panel_block_qr",
            "lls_householder_workspace_size", "lls_householder_solve")
 
 
@@ -89,6 +90,10 @@ def load(path: str = LIB_PATH):
     lib.lls_panel_qr_workspace_size.restype = sz
     lib.lls_panel_qr.argtypes = [i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]
     lib.lls_panel_qr.restype = i
+    lib.lls_panel_block_qr_workspace_size.argtypes = [i, i, i]
+    lib.lls_panel_block_qr_workspace_size.restype = sz
+    lib.lls_panel_block_qr.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]
+    lib.lls_panel_block_qr.restype = i
     lib.lls_householder_workspace_size.argtypes = [i, i, i]
     lib.lls_householder_workspace_size.restype = sz
     lib.lls_householder_solve.argtypes = [i, i, i, vp, i, vp, vp, vp, sz, vp]
@@ -185,6 +190,14 @@ def lls_panel_qr_workspace_size(m, b) -> int:
 
 def lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream) -> int:
     return load().lls_panel_qr(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream)
+
+
+def lls_panel_block_qr_workspace_size(m, w1, w2) -> int:
+    return load().lls_panel_block_qr_workspace_size(m, w1, w2)
+
+
+def lls_panel_block_qr(m, w1, w2, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream) -> int:
+    return load().lls_panel_block_qr(m, w1, w2, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream)
 
 
 def lls_householder_workspace_size(m, n, prec) -> int:
