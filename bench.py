@@ -163,10 +163,10 @@ def run_reference(args):
 # it stands, from the captures summarised under profiles/; None once a kernel changes.
 # tc_projection is the product kernel alone (the split-K reduce is a separate, small launch).
 NCU_TRAFFIC = {"panel": None,
-               "block": None,
-               "tc_projection": None,
-               "tc_update": None,
-               "cgls": None}
+               "block": 4336640 + 0,
+               "tc_projection": 335482624 + 23355136,
+               "tc_update": 415756288 + 224454400,
+               "cgls": 24802414592 + 402266880}
 
 
 def max_over_ranks(value, world_size, device):
