@@ -458,6 +458,7 @@ def main():
             e2e_ms.append(s0.elapsed_time(s1))
 
     x_ref = x.clone()
+    hh = householder_baseline(A, b, x_ref, stream, dev) if not args.no_householder else None
 
     last = infos[-1]
     kry_ms = statistics.mean(i["krylov_ms"] for i in infos)
@@ -474,9 +475,6 @@ def main():
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))   # FP16 and BF16 have the same dense rate
     achieved = kry_bytes / (kry_ms * 1e-3) / 1e9
     kernels = kernel_rooflines(m, n, pw, args.prec, stream, dev, hbm_peak, tc_peak)
-    # after the kernel-level timings: the FP64 Householder run leaves the next kernels measurably
-    # slower for a while (a standalone panel read 47 us after it and 33 us without it)
-    hh = householder_baseline(A, b, x_ref, stream, dev) if not args.no_householder else None
     kernels["cgls"] = {"kernel": f"{args.krylov}_kernel (persistent {args.krylov.upper()} iteration, whole Krylov phase)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                        "traffic": NCU_TRAFFIC["cgls"], "algorithmic_bytes_per_launch": kry_bytes}
