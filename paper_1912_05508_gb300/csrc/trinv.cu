@@ -79,8 +79,8 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
         C = M + (size_t)c0 + (size_t)(c0 + w1) * n;
         K = w1; alpha = -1.f;
     }
-    __shared__ float As[kTK][kTB + 4];
-    __shared__ float Bs[kTK][kTB + 4];
+    __shared__ __align__(16) float As[kTK][kTB + 4];
+    __shared__ __align__(16) float Bs[kTK][kTB + 4];
     const int t = threadIdx.x;
     const int ti = (t % 16) * 4, tj = (t / 16) * 4;
     float acc[4][4] = {};
@@ -101,9 +101,11 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kTK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { av[u] = As[kk][ti + u]; bv[u] = Bs[kk][tj + u]; }
+            // 16-byte reads: the 16 lanes of a half-warp read 16 distinct A segments, the two
+            // half-warps the same ones (broadcast); all lanes of a half-warp one B segment
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ti]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tj]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -144,8 +146,8 @@ __global__ void __launch_bounds__(256)
 triu_product_kernel(const float* __restrict__ U, int ldu, const float* __restrict__ V, int ldv,
                     float* __restrict__ C, int ldc, int n) {
     const int i0 = blockIdx.x * kTB, j0 = blockIdx.y * kTB;
-    __shared__ float As[kTK][kTB + 4];
-    __shared__ float Bs[kTK][kTB + 4];
+    __shared__ __align__(16) float As[kTK][kTB + 4];
+    __shared__ __align__(16) float Bs[kTK][kTB + 4];
     const int t = threadIdx.x;
     const int ti = (t % 16) * 4, tj = (t / 16) * 4;
     float acc[4][4] = {};
