@@ -162,8 +162,8 @@ __device__ __forceinline__ double sum_parts_quad(const double* __restrict__ p, i
 
 // out_c = sum over r in [lo(c), hi(c)) of X[r + c n] * v_r, v staged in k_dsm.
 // upper: rows 0..c (column c of an upper-triangular X); lower: rows c..n-1.
-// One warp per column: 16-byte loads over the aligned body of the column (two compensated
-// chains, so two loads are in flight per lane), single elements at the ragged ends, and a
+// One warp per column: 16-byte loads over the aligned body of the column (four compensated
+// chains, so four loads are in flight per lane), single elements at the ragged ends, and a
 // double-float warp sum joined to FP64 once.
 __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, double* __restrict__ out,
                           float2* __restrict__ outdf = nullptr) {
@@ -174,34 +174,43 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
     for (int c = gw; c < n; c += nw) {
         const int lo = upper ? 0 : c, hi = upper ? c + 1 : n;
         const float* col = X + (size_t)c * n;
-        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
         int blo = lo, bhi = lo;                       // aligned body [blo, bhi), multiples of 4
         if (vec) {
             blo = min((lo + 3) & ~3, hi);
             bhi = max(blo, hi & ~3);
             const float4* col4 = reinterpret_cast<const float4*>(col);
+            const int qe = bhi / 4;
             int q = blo / 4 + lane;
-            for (; q + 32 < bhi / 4; q += 64) {
+            // four 16-byte loads in flight per lane (a column of 4096 entries is 8 trips)
+            for (; q + 96 < qe; q += 128) {
                 const float4 a0 = __ldg(col4 + q), a1 = __ldg(col4 + q + 32);
-                const float2 v0 = k_dsm[4 * q], v1 = k_dsm[4 * q + 1], v2 = k_dsm[4 * q + 2], v3 = k_dsm[4 * q + 3];
-                const float2 w0 = k_dsm[4 * q + 128], w1 = k_dsm[4 * q + 129], w2 = k_dsm[4 * q + 130],
-                             w3 = k_dsm[4 * q + 131];
-                dot2_step(s0, c0, a0.x, v0.x, v0.y);
-                dot2_step(s1, c1, a1.x, w0.x, w0.y);
-                dot2_step(s0, c0, a0.y, v1.x, v1.y);
-                dot2_step(s1, c1, a1.y, w1.x, w1.y);
-                dot2_step(s0, c0, a0.z, v2.x, v2.y);
-                dot2_step(s1, c1, a1.z, w2.x, w2.y);
-                dot2_step(s0, c0, a0.w, v3.x, v3.y);
-                dot2_step(s1, c1, a1.w, w3.x, w3.y);
+                const float4 a2 = __ldg(col4 + q + 64), a3 = __ldg(col4 + q + 96);
+                const float2* v = k_dsm + 4 * q;
+                dot2_step(s0, c0, a0.x, v[0].x, v[0].y);
+                dot2_step(s1, c1, a1.x, v[128].x, v[128].y);
+                dot2_step(s2, c2, a2.x, v[256].x, v[256].y);
+                dot2_step(s3, c3, a3.x, v[384].x, v[384].y);
+                dot2_step(s0, c0, a0.y, v[1].x, v[1].y);
+                dot2_step(s1, c1, a1.y, v[129].x, v[129].y);
+                dot2_step(s2, c2, a2.y, v[257].x, v[257].y);
+                dot2_step(s3, c3, a3.y, v[385].x, v[385].y);
+                dot2_step(s0, c0, a0.z, v[2].x, v[2].y);
+                dot2_step(s1, c1, a1.z, v[130].x, v[130].y);
+                dot2_step(s2, c2, a2.z, v[258].x, v[258].y);
+                dot2_step(s3, c3, a3.z, v[386].x, v[386].y);
+                dot2_step(s0, c0, a0.w, v[3].x, v[3].y);
+                dot2_step(s1, c1, a1.w, v[131].x, v[131].y);
+                dot2_step(s2, c2, a2.w, v[259].x, v[259].y);
+                dot2_step(s3, c3, a3.w, v[387].x, v[387].y);
             }
-            if (q < bhi / 4) {
+            for (; q < qe; q += 32) {
                 const float4 a0 = __ldg(col4 + q);
-                const float2 v0 = k_dsm[4 * q], v1 = k_dsm[4 * q + 1], v2 = k_dsm[4 * q + 2], v3 = k_dsm[4 * q + 3];
-                dot2_step(s0, c0, a0.x, v0.x, v0.y);
-                dot2_step(s0, c0, a0.y, v1.x, v1.y);
-                dot2_step(s0, c0, a0.z, v2.x, v2.y);
-                dot2_step(s0, c0, a0.w, v3.x, v3.y);
+                const float2* v = k_dsm + 4 * q;
+                dot2_step(s0, c0, a0.x, v[0].x, v[0].y);
+                dot2_step(s0, c0, a0.y, v[1].x, v[1].y);
+                dot2_step(s0, c0, a0.z, v[2].x, v[2].y);
+                dot2_step(s0, c0, a0.w, v[3].x, v[3].y);
             }
         }
         // ragged ends: [lo, blo) and [bhi, hi) (the whole range when not vectorized)
@@ -217,9 +226,9 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
             }
         }
         float t, e;
-        two_sum(s0, s1, t, e);
-        s0 = t;
-        c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+        two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+        two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
+        two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
         warp_sum_df(s0, c0);
         if (lane == 0) {
             const double val = join_df(s0, c0);

@@ -61,7 +61,11 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
                      float* __restrict__ tmp, int n, NodeList nl) {
     const int node = blockIdx.z;
     const int c0 = nl.c0[node], w1 = nl.w1[node], w2 = nl.w2[node];
-    const int i0 = blockIdx.x * kTB, j0 = blockIdx.y * kTB;
+    // a tile's K range grows with j in phase 0 (B = M22 is upper triangular) and shrinks with i
+    // in phase 1: the grid is ordered so the longest tiles start first and the short ones fill
+    // the last wave
+    const int i0 = blockIdx.x * kTB;
+    const int j0 = (phase == 0 ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kTB;
     if (i0 >= w1 || j0 >= w2) return;
     const float* A;
     const float* B;
@@ -79,39 +83,52 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
         C = M + (size_t)c0 + (size_t)(c0 + w1) * n;
         K = w1; alpha = -1.f;
     }
-    __shared__ __align__(16) float As[kTK][kTB + 4];
-    __shared__ __align__(16) float Bs[kTK][kTB + 4];
+    // two shared-memory stages: the global loads of step k + 1 are issued into registers
+    // before step k's products, so their latency overlaps the arithmetic; one barrier a step
+    __shared__ __align__(16) float As[2][kTK][kTB + 4];
+    __shared__ __align__(16) float Bs[2][kTK][kTB + 4];
     const int t = threadIdx.x;
     const int ti = (t % 16) * 4, tj = (t / 16) * 4;
     float acc[4][4] = {};
     // phase 0: B = M22 upper triangular, rows k <= j; phase 1: A = M11 upper, columns k >= i
     const int kbeg = phase == 1 ? (i0 / kTK) * kTK : 0;
     const int kend = phase == 0 ? min(K, j0 + kTB) : K;
-    for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+    float ra[4], rb[4];
+    auto fetch = [&](int k0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int idx = t + r * 256;
             const int ii = idx % kTB, kk = idx / kTB;
             const int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < w1 && gk < K) ? A[(size_t)gi + (size_t)gk * lda] : 0.f;
+            ra[r] = (gi < w1 && gk < K) ? A[(size_t)gi + (size_t)gk * lda] : 0.f;
             const int kk2 = idx % kTK, jj = idx / kTK;
             const int gj = j0 + jj, gk2 = k0 + kk2;
-            Bs[kk2][jj] = (gj < w2 && gk2 < K) ? B[(size_t)gk2 + (size_t)gj * ldb] : 0.f;
+            rb[r] = (gj < w2 && gk2 < K) ? B[(size_t)gk2 + (size_t)gj * ldb] : 0.f;
+        }
+    };
+    if (kbeg < kend) fetch(kbeg);
+    int stage = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += kTK, stage ^= 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = t + r * 256;
+            As[stage][idx / kTB][idx % kTB] = ra[r];
+            Bs[stage][idx % kTK][idx / kTK] = rb[r];
         }
         __syncthreads();
+        if (k0 + kTK < kend) fetch(k0 + kTK);
 #pragma unroll
         for (int kk = 0; kk < kTK; ++kk) {
             // 16-byte reads: the 16 lanes of a half-warp read 16 distinct A segments, the two
             // half-warps the same ones (broadcast); all lanes of a half-warp one B segment
-            const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ti]);
-            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tj]);
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[stage][kk][ti]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[stage][kk][tj]);
             const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
