@@ -142,6 +142,28 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
               lls_info* info, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * lls_solve_host: lls_solve on operands that live in page-locked HOST memory (allocated
+ * with cudaHostAlloc / cudaMallocHost or registered with cudaHostRegister). The library has
+ * no counterpart in the paper; it exists so that a caller whose data is on the host pays for
+ * the upload only once, overlapped with the factorization: A is copied up in column chunks of
+ * doubling width (64, 64, 128, 256, ... columns) on a library-owned side stream, and the
+ * recursion of Alg. 2 waits for a chunk just before it first touches the chunk's columns
+ * (columns are first touched in increasing order). x is copied back at the end of the same
+ * stream order.
+ *  A  [in]  m x n FP32 page-locked host memory, column-major, lda >= m.
+ *  b  [in]  m FP64 page-locked host memory.
+ *  x  [out] n FP64 page-locked host memory; valid once `stream` has synchronized (the call
+ *           synchronizes itself when info is non-NULL).
+ *  ws       lls_solve_host_workspace_size(m, n, opts) bytes of DEVICE memory, 256-B
+ *           aligned: the lls_solve workspace plus device copies of A, b and x.
+ *  opts, info, stream: as lls_solve (no R_out).
+ * Errors: as lls_solve; LLS_ERR_ARG also when A, b or x is not page-locked host memory.
+ * -------------------------------------------------------------------------- */
+size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts);
+int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
+                   size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Batched solve: `batch` independent problems min ||A_i x_i - b_i||, uneven sizes, in one
  * persistent launch (each SM takes whole problems from a device work queue, largest first,
  * and runs factorization, preconditioner and CGLS on its own; 16-column panels).

@@ -8,6 +8,8 @@
 // and for every leaf (<= panel_width columns) the CAQR panel (Eq. caqr). All of it is
 // asynchronous on the caller's stream; nothing is allocated.
 #include <stdlib.h>
+
+#include <mutex>
 #include <string.h>
 
 #include <vector>
@@ -114,12 +116,35 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.red = ar.take<double>(8192);
 }
 
+// Columns of W that arrive in chunks on another stream (the host-input solve): chunk k covers
+// columns [start[k], start[k + 1]) and is complete when ev[k] fires. The recursion first
+// touches columns in increasing order, so it waits for the chunks up to the last column a
+// launch touches, just before that launch.
+constexpr int kMaxChunks = 32;
+struct ColumnGate {
+    int count = 0;
+    int start[kMaxChunks + 1];
+    cudaEvent_t ev[kMaxChunks];
+    int ready = 0;                      // chunks the stream already waits for
+};
+
 struct QrCtx {
     int m, n, pw, lowp, leaf;
     QrWs w;
     float* R; int ldr;
     cudaStream_t st;
+    ColumnGate* gate = nullptr;
 };
+
+static int gate_upto(QrCtx& c, int col_end) {
+    if (!c.gate) return LLS_OK;
+    ColumnGate& g = *c.gate;
+    while (g.ready < g.count && g.start[g.ready] < col_end) {
+        LLS_CUDA_TRY(cudaStreamWaitEvent(c.st, g.ev[g.ready], 0));
+        ++g.ready;
+    }
+    return LLS_OK;
+}
 
 // LLS_NODE=split keeps narrow nodes on the four-kernel path, LLS_NODE=node runs them as one
 // launch each but keeps the lowest nodes' panels separate (for comparisons).
@@ -140,6 +165,7 @@ static bool use_fused_blocks() {
 
 static int qr_rec(QrCtx& c, int c0, int w) {
     if (w <= c.pw) {
+        LLS_TRY(gate_upto(c, c0 + w));
         PanelCall p;
         p.W = c.w.W; p.ldw = c.w.ldw; p.Wh = c.w.Wh; p.ldh = c.w.ldh; p.R = c.R; p.ldr = c.ldr;
         p.m = c.m; p.c0 = c0; p.b = w; p.lowp = c.lowp == 2 ? 3 : c.lowp;
@@ -157,6 +183,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
     const int w1 = split_point(w, c.pw), w2 = w - w1;
     if (w1 == c.pw && w2 <= c.pw && (c.lowp == 0 || c.lowp == 1) && c.leaf == 0 && use_fused_blocks()) {
         // both halves are panels: left panel, node and right panel in one launch
+        LLS_TRY(gate_upto(c, c0 + w));
         BlockCall bc;
         bc.W = c.w.W; bc.ldw = c.w.ldw; bc.Wh = c.w.Wh; bc.ldh = c.w.ldh; bc.R = c.R; bc.ldr = c.ldr;
         bc.m = c.m; bc.c0 = c0; bc.w1 = w1; bc.w2 = w2; bc.lowp = c.lowp;
@@ -166,6 +193,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         if (r != LLS_ERR_UNSUPPORTED) return r;
     }
     LLS_TRY(qr_rec(c, c0, w1));
+    LLS_TRY(gate_upto(c, c0 + w));
     float* R12 = c.R + (size_t)c0 + (size_t)(c0 + w1) * c.ldr;
     float* A2 = c.w.W + (size_t)(c0 + w1) * c.w.ldw;
     const float* Q1 = c.w.W + (size_t)c0 * c.w.ldw;
@@ -206,17 +234,19 @@ static int qr_rec(QrCtx& c, int c0, int w) {
     return qr_rec(c, c0 + w1, w2);
 }
 
+// gate: null when A is copied into W here; otherwise W fills in chunks on another stream.
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
-                  QrWs& w, cudaStream_t st) {
+                  QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * ((size_t)n + 2), st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
-    LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
+    if (!gate) LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
     QrCtx c;
     c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec); c.leaf = o.panel_leaf;
-    c.w = w; c.R = R; c.ldr = ldr; c.st = st;
+    c.w = w; c.R = R; c.ldr = ldr; c.st = st; c.gate = gate;
     LLS_TRY(qr_rec(c, 0, n));
+    LLS_TRY(gate_upto(c, n));
     if (o.reorth) {
         // A = Q1 R1 with Q1 in W; factor Q1 = Q2 R2 by the same recursion, so A = Q2 (R2 R1)
         LLS_CUDA_TRY(cudaMemcpy2DAsync(w.R1, sizeof(float) * (size_t)n, R, sizeof(float) * (size_t)ldr,
@@ -474,12 +504,12 @@ struct SolveCall {
     void* ks; size_t kb;
 };
 
-static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
-    SolveCall& c = *(SolveCall*)p;
+// The solve on `st`; gate non-null when W fills in chunks on another stream (host input).
+static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool capturing, ColumnGate* gate) {
     const int m = c.m, n = c.n;
     if (ev) record_phase(ev[0], st, capturing);
     LLS_CUDA_TRY(cudaMemsetAsync(c.w.dinfo, 0, sizeof(double) * 16, st));
-    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.w, st));
+    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.w, st, gate));
     if (c.R_out) LLS_TRY(copy_matrix(c.R, n, c.R_out, c.ldr, n, n, st));
     LLS_TRY(check_diag(c.R, n, n, c.w.err, st));
     LLS_TRY(tri_inverse(c.R, n, n, c.o.panel_width, c.Minv, c.Mt, c.tmp, c.w.err, st));
@@ -493,6 +523,37 @@ static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturi
     LLS_TRY(krylov_solve(kc, st));
     if (ev) record_phase(ev[2], st, capturing);
     return LLS_OK;
+}
+
+static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+    return solve_body(*(SolveCall*)p, st, ev, capturing, nullptr);
+}
+
+// Reads the device info record and error word after the solve (synchronizes the stream) and
+// fills info; returns the solve's status.
+static int finish_info(const QrWs& w, cudaEvent_t* ev, lls_info* info, cudaStream_t stream) {
+    double hinfo[16];
+    int herr = 0;
+    LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
+    LLS_CUDA_TRY(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LLS_CUDA_TRY(cudaStreamSynchronize(stream));
+    cudaEventElapsedTime(&info->qr_ms, ev[0], ev[1]);
+    cudaEventElapsedTime(&info->krylov_ms, ev[1], ev[2]);
+    info->iters = (int)hinfo[0];
+    info->eta = hinfo[1];
+    info->fwd_est = hinfo[2];
+    info->res_norm = hinfo[3];
+    info->atr_norm = hinfo[4];
+    info->anorm_f = hinfo[5];
+    info->xnorm = hinfo[6];
+    info->a_passes = (int)hinfo[10];
+    info->m_passes = (int)hinfo[11];
+    int st = (int)hinfo[7] == 0 ? LLS_OK : LLS_NOT_CONVERGED;
+    if (herr == DEV_SINGULAR) st = LLS_ERR_SINGULAR;
+    else if (herr == DEV_TIMEOUT) st = LLS_ERR_TIMEOUT;
+    else if (herr != DEV_OK) st = LLS_ERR_CUDA;
+    info->status = st;
+    return st;
 }
 
 int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
@@ -531,29 +592,156 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
         for (auto& e : own) if (e) cudaEventDestroy(e);
         return rc;
     }
-    double hinfo[16];
-    int herr = 0;
-    LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, c.w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
-    LLS_CUDA_TRY(cudaMemcpyAsync(&herr, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    LLS_CUDA_TRY(cudaStreamSynchronize(stream));
-    cudaEventElapsedTime(&info->qr_ms, ev[0], ev[1]);
-    cudaEventElapsedTime(&info->krylov_ms, ev[1], ev[2]);
+    rc = finish_info(c.w, ev, info, stream);
     for (auto& e : own) cudaEventDestroy(e);
-    info->iters = (int)hinfo[0];
-    info->eta = hinfo[1];
-    info->fwd_est = hinfo[2];
-    info->res_norm = hinfo[3];
-    info->atr_norm = hinfo[4];
-    info->anorm_f = hinfo[5];
-    info->xnorm = hinfo[6];
-    info->a_passes = (int)hinfo[10];
-    info->m_passes = (int)hinfo[11];
-    int st = (int)hinfo[7] == 0 ? LLS_OK : LLS_NOT_CONVERGED;
-    if (herr == DEV_SINGULAR) st = LLS_ERR_SINGULAR;
-    else if (herr == DEV_TIMEOUT) st = LLS_ERR_TIMEOUT;
-    else if (herr != DEV_OK) st = LLS_ERR_CUDA;
-    info->status = st;
-    return st;
+    return rc;
+}
+
+
+// ---------------------------------------------------------------------------------------
+// The solve from page-locked host buffers. A goes up in column chunks of doubling width
+// (64, 64, 128, 256, ... columns) on a side stream, each chunk into a device copy of A and
+// into W; the recursion waits for a chunk just before it first touches the chunk's columns,
+// so all but the first chunk's upload overlaps the factorization. x comes back at the end.
+
+struct HostRes {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t ev[kMaxChunks];
+};
+static std::mutex g_host_mu;            // one enqueue at a time: the events are shared
+static HostRes g_host_res[64];
+
+static int host_res(HostRes*& r) {
+    int dev = 0;
+    LLS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return LLS_ERR_UNSUPPORTED;
+    HostRes& h = g_host_res[dev];
+    if (!h.side) {
+        LLS_CUDA_TRY(cudaStreamCreateWithFlags(&h.side, cudaStreamNonBlocking));
+        LLS_CUDA_TRY(cudaEventCreateWithFlags(&h.fork, cudaEventDisableTiming));
+        for (auto& e : h.ev) LLS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    r = &h;
+    return LLS_OK;
+}
+
+static void plan_chunks(int n, ColumnGate& g) {
+    g.count = 0;
+    g.ready = 0;
+    int c = 0;
+    while (c < n && g.count < kMaxChunks) {
+        g.start[g.count++] = c;
+        c = c == 0 ? 64 : (c > n / 2 ? n : 2 * c);
+        if (c > n) c = n;
+    }
+    g.start[g.count] = n;
+}
+
+struct HostSolveCall {
+    SolveCall s;                        // the device solve on the workspace's copies of A, b, x
+    const float* Ah; int ldah;
+    const double* bh; double* xh;
+};
+
+static void host_layout(WsArena& ar, int m, int n, int& lda, float*& A, double*& b, double*& x) {
+    lda = (int)align_up((size_t)m, 64);
+    A = ar.take<float>((size_t)lda * n);
+    b = ar.take<double>((size_t)m);
+    x = ar.take<double>((size_t)n);
+}
+
+static int enqueue_solve_host(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+    HostSolveCall& h = *(HostSolveCall*)p;
+    SolveCall& c = h.s;
+    const int m = c.m, n = c.n;
+    HostRes* r = nullptr;
+    LLS_TRY(host_res(r));
+    ColumnGate g;
+    plan_chunks(n, g);
+    for (int k = 0; k < g.count; ++k) g.ev[k] = r->ev[k];
+    LLS_CUDA_TRY(cudaEventRecord(r->fork, st));
+    LLS_CUDA_TRY(cudaStreamWaitEvent(r->side, r->fork, 0));
+    float* Ad = const_cast<float*>(c.A);
+    LLS_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(c.b), h.bh, sizeof(double) * (size_t)m,
+                                 cudaMemcpyHostToDevice, r->side));
+    for (int k = 0; k < g.count; ++k) {
+        const int c0 = g.start[k], cols = g.start[k + 1] - c0;
+        LLS_CUDA_TRY(cudaMemcpy2DAsync(Ad + (size_t)c0 * c.lda, sizeof(float) * (size_t)c.lda,
+                                       h.Ah + (size_t)c0 * h.ldah, sizeof(float) * (size_t)h.ldah,
+                                       sizeof(float) * (size_t)m, (size_t)cols, cudaMemcpyHostToDevice, r->side));
+        LLS_CUDA_TRY(cudaMemcpy2DAsync(c.w.W + (size_t)c0 * c.w.ldw, sizeof(float) * (size_t)c.w.ldw,
+                                       Ad + (size_t)c0 * c.lda, sizeof(float) * (size_t)c.lda,
+                                       sizeof(float) * (size_t)m, (size_t)cols, cudaMemcpyDeviceToDevice, r->side));
+        LLS_CUDA_TRY(cudaEventRecord(g.ev[k], r->side));
+    }
+    LLS_TRY(solve_body(c, st, ev, capturing, &g));   // joins every chunk before A's norm and the Krylov phase
+    LLS_CUDA_TRY(cudaMemcpyAsync(h.xh, c.x, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    return LLS_OK;
+}
+
+static bool page_locked(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    if (n < 1 || m < n || !valid_opts(o)) return 0;
+    WsArena ar(nullptr, SIZE_MAX);
+    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb;
+    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb);
+    int lda; float* A; double *b, *x;
+    host_layout(ar, m, n, lda, A, b, x);
+    return ar.off;
+}
+
+int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
+                   size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream) {
+    lls_options o;
+    resolve(opts, o);
+    if (info) memset(info, 0, sizeof(*info));
+    if (n < 1 || m < n || lda < m || !A || !b || !x || !ws) return LLS_ERR_ARG;
+    if (!valid_opts(o)) return LLS_ERR_ARG;
+    if (!page_locked(A) || !page_locked(b) || !page_locked(x)) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, ws_bytes);
+    HostSolveCall h;
+    SolveCall& c = h.s;
+    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb);
+    int ldad; float* Ad; double *bd, *xd;
+    host_layout(ar, m, n, ldad, Ad, bd, xd);
+    if (!ar.ok) return LLS_ERR_WORKSPACE;
+    c.m = m; c.n = n; c.lda = ldad; c.ldr = 0; c.A = Ad; c.b = bd; c.x = xd; c.R_out = nullptr; c.o = o;
+    h.Ah = A; h.ldah = lda; h.bh = b; h.xh = x;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.op = 4; key.device = current_device();
+    key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda;
+    key.ptrs[0] = A; key.ptrs[1] = b; key.ptrs[2] = x; key.ptrs[3] = ws;
+    key.ws_bytes = ws_bytes; key.opts = o;
+
+    cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (info) {
+        for (int i = 0; i < 3; ++i) LLS_CUDA_TRY(cudaEventCreate(&own[i]));
+        for (int i = 0; i < 3; ++i) ev[i] = own[i];
+    }
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        trace_mark(stream);
+        rc = run_graphed(key, stream, enqueue_solve_host, &h, info ? ev : nullptr);
+        trace_flush();
+    }
+    if (rc == LLS_OK && info) rc = finish_info(c.w, ev, info, stream);
+    for (auto& e : own) if (e) cudaEventDestroy(e);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------------------

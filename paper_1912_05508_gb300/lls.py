@@ -28,6 +28,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_solve_batched_workspace_size", "lls_solve_batched",
            "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr",
            "lls_panel_block_qr_workspace_size", "lls_panel_block_qr",
+           "lls_solve_host_workspace_size", "lls_solve_host",
            "lls_householder_workspace_size", "lls_householder_solve")
 
 
@@ -80,6 +81,10 @@ def load(path: str = LIB_PATH):
     lib.lls_solve.argtypes = [i, i, vp, i, vp, vp, vp, i, vp, sz, C.POINTER(lls_options),
                               C.POINTER(lls_info), vp]
     lib.lls_solve.restype = i
+    lib.lls_solve_host_workspace_size.argtypes = [i, i, C.POINTER(lls_options)]
+    lib.lls_solve_host_workspace_size.restype = sz
+    lib.lls_solve_host.argtypes = [i, i, vp, i, vp, vp, vp, sz, C.POINTER(lls_options), C.POINTER(lls_info), vp]
+    lib.lls_solve_host.restype = i
     lib.lls_lowp_projection_workspace_size.argtypes = [i, i, i]
     lib.lls_lowp_projection_workspace_size.restype = sz
     lib.lls_lowp_projection.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp, sz, vp]
@@ -172,6 +177,16 @@ def lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream) 
     return load().lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes,
                             C.byref(opts) if opts is not None else None,
                             C.byref(info) if info is not None else None, stream)
+
+
+def lls_solve_host_workspace_size(m, n, opts=None) -> int:
+    return load().lls_solve_host_workspace_size(m, n, C.byref(opts) if opts is not None else None)
+
+
+def lls_solve_host(m, n, A, lda, b, x, ws, ws_bytes, opts, info, stream) -> int:
+    return load().lls_solve_host(m, n, A, lda, b, x, ws, ws_bytes,
+                                 C.byref(opts) if opts is not None else None,
+                                 C.byref(info) if info is not None else None, stream)
 
 
 def lls_lowp_projection_workspace_size(m, w1, w2) -> int:
