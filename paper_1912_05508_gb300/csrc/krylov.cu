@@ -38,7 +38,8 @@ namespace lls {
 constexpr int kKThreads = 256;
 constexpr int kKWarps = kKThreads / 32;
 constexpr int kRowTile = 1024;    // rows per A t work item (four rows per thread)
-constexpr int kColChunk = 64;     // columns per A t work item
+constexpr int kColChunkMin = 48;  // columns per A t work item: chosen per launch in [48, 96]
+constexpr int kColChunkMax = 96;  // so that the items fill whole waves of the grid
 constexpr int kRowChunk = 1024;   // rows per A^T r work item (staged in shared memory); 4096
                                   // items at m = 32768, n = 4096 fill 9 waves of 456 CTAs
 constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
@@ -62,6 +63,7 @@ struct KArgs {
     double tol;
     int max_iter, target, x_zero;
     int nrt, nck, nrc, ncg;
+    int colchunk;                // columns per A t work item
     double *v1part, *v2part;     // fused engine: per-CTA partial A^T q and A^T r, [grid][n]
     int aligned16;               // A and lda allow 16-byte copies of 4-row column segments
     const float4* At;            // row-block copy of A: At[blk * n + j] = A[4 blk .. 4 blk + 3, j], or null
@@ -249,7 +251,7 @@ __device__ void a_times_partials(const KArgs& a) {
         const int rt = it % a.nrt, cc = it / a.nrt;
         const int i0 = rt * kRowTile + 4 * threadIdx.x;
         if (i0 >= a.m) continue;
-        const int j0 = cc * kColChunk, j1 = min(a.n, j0 + kColChunk);
+        const int j0 = cc * a.colchunk, j1 = min(a.n, j0 + a.colchunk);
         const bool full = a.aligned16 && i0 + 4 <= a.m;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
         if (full) {
@@ -1101,17 +1103,38 @@ adjoint_kernel(AdjArgs aa) {
 
 // ---------------------------------------------------------------------------------------
 struct KLayout {
-    int nrt, nck, nrc, ncg;
+    int nrt, nck, nrc, ncg, colchunk;
     size_t off_r, off_q, off_t, off_p, off_s, off_u, off_d, off_qpart, off_upart, off_v1, off_v2, off_bpart,
         off_bar, off_rdf, off_tdf, off_udf, off_pdf, off_tile, total;
 };
 
 // The one-pass engine streams A from a copy in 4-row blocks (tiled = true): block blk is the
 // contiguous run At[blk * n .. blk * n + n) of 16-byte segments (A[4 blk .. 4 blk + 3, j]).
+// Width of the A t work items: a grid barrier follows the pass, so its time is the number of
+// waves of items times the item's time, and the width that minimises waves x width wins
+// (at m = 32768, n = 4096 on 456 CTAs: 72 columns, 1824 items in exactly 4 waves, where 64
+// columns gave 2048 items in 4.5 waves).
+static int pick_col_chunk(int m, int n, int grid) {
+    const long long nrt = ceil_div(m, kRowTile);
+    int best = 64;
+    long long best_cost = -1;
+    for (int c = kColChunkMin; c <= kColChunkMax; c += 8) {
+        const long long items = nrt * ceil_div(n, c);
+        const long long waves = (items + grid - 1) / grid;
+        const long long cost = waves * (c < n ? c : n);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && c > best)) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
 static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     KLayout L;
     L.nrt = ceil_div(m, kRowTile);
-    L.nck = ceil_div(n, kColChunk);
+    L.colchunk = pick_col_chunk(m, n, grid < 1 ? 1 : grid);
+    L.nck = ceil_div(n, L.colchunk);
     L.nrc = ceil_div(m, kRowChunk);
     L.ncg = ceil_div(n, kColGroup);
     size_t o = 0;
@@ -1123,7 +1146,7 @@ static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     L.off_s = take(8ull * n);
     L.off_u = take(8ull * n);
     L.off_d = take(8ull * n);
-    L.off_qpart = take(8ull * m * L.nck);
+    L.off_qpart = take(8ull * m * ceil_div(n, kColChunkMin));   // room for the narrowest width (most partials)
     L.off_upart = take(8ull * n * L.nrc);
     L.off_v1 = take(8ull * n * grid);
     L.off_v2 = take(8ull * n * grid);
@@ -1247,7 +1270,7 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     a.bar = (unsigned*)(base + L.off_bar);
     a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
     a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
-    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
+    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg; a.colchunk = L.colchunk;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kKThreads), args, smem, st));
@@ -1329,7 +1352,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.bar = (unsigned*)(base + L.off_bar);
     a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
     a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
-    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg;
+    a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg; a.colchunk = L.colchunk;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&aa};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)adjoint_kernel, dim3(grid), dim3(kKThreads), args, smem, st));
