@@ -173,7 +173,12 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
     const int gw = blockIdx.x * kKWarps + (threadIdx.x >> 5), nw = gridDim.x * kKWarps;
     const bool vec = (n & 3) == 0 && ((uintptr_t)X & 15) == 0;
     double sq = 0.0;
-    for (int c = gw; c < n; c += nw) {
+    // columns by decreasing length, the odd rounds in reverse warp order: the warps whose first
+    // column is longest take the shortest (or no) second one
+    for (int k = 0; (long long)k * nw < n; ++k) {
+        const int p = k * nw + ((k & 1) ? nw - 1 - gw : gw);
+        if (p >= n) continue;
+        const int c = upper ? n - 1 - p : p;
         const int lo = upper ? 0 : c, hi = upper ? c + 1 : n;
         const float* col = X + (size_t)c * n;
         float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
@@ -290,24 +295,32 @@ __device__ void a_times_partials(const KArgs& a) {
 
 // upart[rc][j] = sum_{i in row chunk rc} A[i, j] * v_i for v (length m) in global memory.
 // v's chunk is staged in shared memory; each lane reads 4 consecutive rows per step.
+// Each CTA takes a contiguous range of the items in row-chunk-major order (ranges differ in
+// length by at most one), so it stages a row chunk of v once for all its items in that chunk.
 __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
                                   const float2* __restrict__ vdf = nullptr) {
     const int items = a.nrc * a.ncg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int it = blockIdx.x; it < items; it += gridDim.x) {
-        const int rc = it % a.nrc, cg = it / a.nrc;
+    const int it0 = (int)((long long)blockIdx.x * items / gridDim.x);
+    const int it1 = (int)((long long)(blockIdx.x + 1) * items / gridDim.x);
+    int staged = -1;
+    for (int it = it0; it < it1; ++it) {
+        const int rc = it / a.ncg, cg = it % a.ncg;
         const int r0 = rc * kRowChunk, rows = min(a.m - r0, kRowChunk);
-        __syncthreads();
-        if (vdf) {
-            for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
-        } else {
-            for (int i = threadIdx.x; i < rows; i += kKThreads) {
-                float hi, lo;
-                split_df(__ldcg(v + r0 + i), hi, lo);
-                k_dsm[i] = make_float2(hi, lo);
+        if (rc != staged) {                       // uniform across the CTA
+            __syncthreads();
+            if (vdf) {
+                for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
+            } else {
+                for (int i = threadIdx.x; i < rows; i += kKThreads) {
+                    float hi, lo;
+                    split_df(__ldcg(v + r0 + i), hi, lo);
+                    k_dsm[i] = make_float2(hi, lo);
+                }
             }
+            __syncthreads();
+            staged = rc;
         }
-        __syncthreads();
         const bool full = a.aligned16 && rows == kRowChunk;
         for (int jj = 0; jj < kColGroup / kKWarps; ++jj) {
             const int j = cg * kColGroup + warp * (kColGroup / kKWarps) + jj;
