@@ -166,7 +166,7 @@ NCU_TRAFFIC = {"panel": None,
                "block": 4336640 + 0,
                "tc_projection": 335482624 + 23355136,
                "tc_update": 415756288 + 224454400,
-               "cgls": 24802414592 + 402266880}
+               "cgls": None}
 
 
 def max_over_ranks(value, world_size, device):
