@@ -166,7 +166,7 @@ NCU_TRAFFIC = {"panel": None,
                "block": 4336640 + 0,
                "tc_projection": 335482624 + 23355136,
                "tc_update": 415756288 + 224454400,
-               "cgls": None}
+               "cgls": 24629498624 + 364217344}
 
 
 def max_over_ranks(value, world_size, device):
