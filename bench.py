@@ -338,6 +338,33 @@ def householder_baseline(A, b, x_ref, stream, dev, reps=2):
     return out
 
 
+def library_lstsq_context(A, b, x_ref, stream):
+    """Context only, not a baseline of this library: torch.linalg.lstsq (cuSOLVER's QR-based
+    gels) in FP32 and FP64 on the same GPU and inputs, one timed call after a warm-up. Any
+    failure is reported in the line instead of ending the benchmark."""
+    import torch
+    out = {"label": "library, context only (torch.linalg.lstsq, cuSOLVER gels)"}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        try:
+            with torch.cuda.stream(stream):
+                Ax = A.to(dt)
+                bx = b.to(dt)[:, None]
+                torch.linalg.lstsq(Ax, bx)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x = torch.linalg.lstsq(Ax, bx).solution[:, 0]
+                e1.record(stream)
+                torch.cuda.synchronize()
+            rel = float(torch.linalg.norm(x.double() - x_ref) / torch.linalg.norm(x_ref))
+            out[name] = {"ms": e0.elapsed_time(e1), "rel_diff_vs_mixed_precision_x": rel}
+            del Ax, bx, x
+        except Exception as exc:  # noqa: BLE001 - context only
+            out[name] = {"error": str(exc).splitlines()[0][:200]}
+        torch.cuda.empty_cache()
+    return out
+
+
 def make_inputs(args, m, n, rank, dev):
     """Generate the problem on the device; keep a host copy in /tmp so a rerun of the same
     command (e.g. under a profiler, where torch's linear-algebra plugin may not load) reuses it."""
@@ -460,6 +487,7 @@ def main():
 
     x_ref = x.clone()
     hh = householder_baseline(A, b, x_ref, stream, dev) if not args.no_householder else None
+    libctx = library_lstsq_context(A, b, x_ref, stream) if not args.no_householder else None
 
     last = infos[-1]
     kry_ms = statistics.mean(i["krylov_ms"] for i in infos)
@@ -507,6 +535,7 @@ def main():
                    "steps_ms": [round(v, 3) for v in e2e_ms],
                    "api": "lls_solve_host (page-locked host A, b, x; upload overlapped with the QR)"},
            "householder": hh,
+           "library_context": libctx,
            "speedup_vs_householder_fp64": (hh["fp64"]["ms"] / ms) if hh else None,
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
            "clocks": clocks}
