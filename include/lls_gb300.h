@@ -288,6 +288,18 @@ int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void*
                        int ldr, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * lls_selftest_wait_timeout: exercises the failure path of the library's bounded device
+ * waits (no counterpart in the paper). It launches a two-CTA cooperative kernel whose grid
+ * barrier expects three arrivals, so the barrier can never complete; each wait gives up after
+ * its time limit (about 2 s), sets the device error word and returns. Nothing faults, and the
+ * context stays usable.
+ *  ws: at least 256 bytes of device memory, 256-B aligned (the barrier words and error word).
+ * Synchronizes `stream`. Returns LLS_ERR_TIMEOUT when the wait ran out as designed, LLS_OK if
+ * the barrier completed (a defect), LLS_ERR_ARG or LLS_ERR_CUDA otherwise.
+ * -------------------------------------------------------------------------- */
+int lls_selftest_wait_timeout(void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Plain Householder least squares (Alg. 1, Sec. 3.2.2): the comparison solver the
  * mixed-precision method is measured against, in FP64 (prec = LLS_PREC_FP64) or FP32
  * (LLS_PREC_FP32) arithmetic throughout. Blocked Householder QR of [A, b] in compact-WY

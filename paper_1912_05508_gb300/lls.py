@@ -28,7 +28,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_solve_batched_workspace_size", "lls_solve_batched",
            "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr",
            "lls_panel_block_qr_workspace_size", "lls_panel_block_qr",
-           "lls_solve_host_workspace_size", "lls_solve_host",
+           "lls_solve_host_workspace_size", "lls_solve_host", "lls_selftest_wait_timeout",
            "lls_householder_workspace_size", "lls_householder_solve")
 
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.lls_solve_host_workspace_size.restype = sz
     lib.lls_solve_host.argtypes = [i, i, vp, i, vp, vp, vp, sz, C.POINTER(lls_options), C.POINTER(lls_info), vp]
     lib.lls_solve_host.restype = i
+    lib.lls_selftest_wait_timeout.argtypes = [vp, sz, vp]
+    lib.lls_selftest_wait_timeout.restype = i
     lib.lls_lowp_projection_workspace_size.argtypes = [i, i, i]
     lib.lls_lowp_projection_workspace_size.restype = sz
     lib.lls_lowp_projection.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp, sz, vp]
@@ -177,6 +179,10 @@ def lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream) 
     return load().lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes,
                             C.byref(opts) if opts is not None else None,
                             C.byref(info) if info is not None else None, stream)
+
+
+def lls_selftest_wait_timeout(ws, ws_bytes, stream) -> int:
+    return load().lls_selftest_wait_timeout(ws, ws_bytes, stream)
 
 
 def lls_solve_host_workspace_size(m, n, opts=None) -> int:
