@@ -489,7 +489,9 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
 // second panel in registers:
 //   1. panel of columns [c0, c0 + w1) (panel_body): Q1 rows in registers, Q1l = round(Q1) in
 //      shared memory (the copy the panel also stores to Wh);
-//   2. FP16: column maxima of |A2| per CTA -> grid barrier -> e_j; A2l = round(A2 2^e_j);
+//   2. FP16: the CTA's column maxima of |A2| folded into device words (atomicMax on the bit
+//      patterns) -> grid barrier -> e_j; A2l = round(A2 2^e_j); CTA 0 clears the words
+//      after the next barrier;
 //   3. the CTA's partial Q1l^T A2l (warp MMAs, FP32 accumulation, fixed-order warp sum)
 //      -> grid barrier -> every CTA sums the P0 partials in the same fixed order, so all hold
 //      the same R12 = sum 2^-e_j (CTA 0 writes it to R), f_j and R12l = round(R12 2^f_j);
