@@ -1,0 +1,44 @@
+"""Host logic of bench.py that decides whether a benchmark line is valid: the summary of the
+nvidia-smi clock samples taken during the timed region (the median SM clock under load, the
+maximum clock, and the throttle reasons that were active)."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+_spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+bench = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(bench)
+
+IDLE = "Not Active"
+
+
+def line(sm, mx, hw=IDLE, hwt=IDLE, swt=IDLE, cap=IDLE, power="850.25"):
+    return f"0, {sm}, {mx}, {power}, 0x0000000000000000, {hw}, {hwt}, {swt}, {cap}\n"
+
+
+def test_steady_clocks_no_reasons():
+    s = bench.summarize_clocks([line(2070, 2070)] * 3)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+
+def test_idle_samples_do_not_pull_the_median_down():
+    s = bench.summarize_clocks([line(345, 2070), line(2070, 2070), line(2055, 2070), line(2070, 2070)])
+    assert s["sm_mhz"] == 2070.0 and s["samples"] == 4
+
+
+def test_reasons_are_collected_by_name():
+    s = bench.summarize_clocks([line(1980, 2070, cap="Active"), line(1900, 2070, hwt="Active"), line(2070, 2070)])
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_stuck_low_shows_in_the_median():
+    # a leftover clock lock: every sample well below the maximum, no reason active
+    s = bench.summarize_clocks([line(1005, 2070)] * 5)
+    assert s["sm_mhz"] == 1005.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == []
+
+
+def test_unavailable_fields_and_empty_output():
+    s = bench.summarize_clocks([line("[N/A]", "[N/A]"), line(2070, 2070)])
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert bench.summarize_clocks([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    assert bench.summarize_clocks(["garbage\n"])["reasons"] == ["no samples"]
