@@ -13,7 +13,11 @@ Each step here:
   3. halves the step until ||r_i(theta_i + t delta_i)|| decreases (at most ``max_halvings``
      times), which keeps Gauss-Newton monotone on problems whose residuals are not small.
 A problem stops when its relative step ||t delta|| <= xtol (1 + ||theta||) or when the
-Gauss-Newton decrease ||J delta||^2 falls below ftol ||r||^2.
+Gauss-Newton decrease ||J delta||^2 falls below ftol ||r||^2 (reasons "xtol", "ftol": converged).
+It also stops, without counting as converged, when its linear solve fails ("solve_failed"),
+when no halving of the step decreases the cost although the linear model predicts a decrease
+above rounding level (more than 1e-8 of the cost; "no_decrease"), or at max_iter ("max_iter").
+A stall whose predicted decrease is at rounding level counts as converged ("rounding").
 
 The linear solver takes the Jacobian in FP32 (the paper's setting for A), so the iteration's
 fixed point satisfies J~^T r = 0 for the rounded Jacobian J~: it matches the FP64 minimiser
@@ -32,13 +36,14 @@ def gauss_newton_batched(fun, thetas, max_iter=50, xtol=1e-10, ftol=1e-20, max_h
         (FP64 device tensors of length n_i), the residuals (FP64, length m_i) and Jacobians
         (FP32 or FP64 (m_i, n_i)); called for the unconverged problems only.
     thetas: list of FP64 device tensors (initial guesses).
-    Returns (thetas, infos) with per-problem dicts: iters, cost (||r||^2 / 2), converged.
+    Returns (thetas, infos) with per-problem dicts: iters, cost (||r||^2 / 2), converged and
+    reason (see the module docstring).
     """
     torch = lls._torch()
     thetas = [t.clone().to(torch.float64) for t in thetas]
     batch = len(thetas)
     iters = [0] * batch
-    done = [False] * batch
+    reason = ["max_iter"] * batch
     active = list(range(batch))
     rs, Js = fun(active, [thetas[i] for i in active])
     res = {i: r for i, r in zip(active, rs)}
@@ -53,7 +58,7 @@ def gauss_newton_batched(fun, thetas, max_iter=50, xtol=1e-10, ftol=1e-20, max_h
         for k, i in enumerate(active):
             iters[i] += 1
             if infos[k]["status"] not in (0, 1):
-                done[i] = True
+                reason[i] = "solve_failed"
                 continue
             d = deltas[k]
             r0 = res[i]
@@ -69,18 +74,21 @@ def gauss_newton_batched(fun, thetas, max_iter=50, xtol=1e-10, ftol=1e-20, max_h
                     accepted = (trial, rt[0], Jt[0])
                     break
                 t *= 0.5
-            if accepted is None:
-                done[i] = True                     # no decrease along the Gauss-Newton direction
+            if accepted is None:                   # no decrease along the Gauss-Newton direction
+                reason[i] = "rounding" if pred <= 1e-8 * max(f0, 1e-300) else "no_decrease"
                 continue
             step = float(torch.linalg.norm(t * d))
             thetas[i], res[i], jac[i] = accepted
-            if step <= xtol * (1.0 + float(torch.linalg.norm(thetas[i]))) or pred <= ftol * max(f0, 1e-300):
-                done[i] = True
+            if step <= xtol * (1.0 + float(torch.linalg.norm(thetas[i]))):
+                reason[i] = "xtol"
+            elif pred <= ftol * max(f0, 1e-300):
+                reason[i] = "ftol"
             else:
                 nxt.append(i)
         active = nxt
     infos = []
     for i in range(batch):
         r = res[i]
-        infos.append({"iters": iters[i], "cost": 0.5 * float(r @ r), "converged": done[i]})
+        infos.append({"iters": iters[i], "cost": 0.5 * float(r @ r),
+                      "converged": reason[i] in ("xtol", "ftol", "rounding"), "reason": reason[i]})
     return thetas, infos
