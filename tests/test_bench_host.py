@@ -42,3 +42,25 @@ def test_unavailable_fields_and_empty_output():
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
     assert bench.summarize_clocks([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
     assert bench.summarize_clocks(["garbage\n"])["reasons"] == ["no samples"]
+
+
+def test_sampler_runs_the_tool_and_summarizes(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi on PATH that prints samples until it is terminated
+    tool = tmp_path / "nvidia-smi"
+    tool.write_text("#!/bin/sh\nwhile true; do echo '0, 2070, 2070, 700.0, 0x0, Not Active, Not Active, "
+                    "Not Active, Active'; sleep 0.05; done\n")
+    tool.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    s = bench.ClockSampler(0)
+    s.start()
+    import time
+    time.sleep(0.3)
+    out = s.stop()
+    assert out["sm_mhz"] == 2070.0 and out["reasons"] == ["sw_power_cap"] and out["samples"] >= 2
+
+
+def test_sampler_without_the_tool(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
