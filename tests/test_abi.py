@@ -63,6 +63,28 @@ def test_workspace_queries_and_argument_errors(lib):
     assert lls.qr_factor(100, 10, 256, 100, None, 0, 256, 10, 256, 1024, o, None) == -4
 
 
+def test_host_solve_block_and_selftest_entry_points(lib):
+    o = lls.make_options()
+    # the host-operand solve needs the device solve's workspace plus copies of A, b and x
+    m, n = 1000, 100
+    assert lls.lls_solve_host_workspace_size(m, n, o) >= lls.lls_solve_workspace_size(m, n, o) + m * n * 4 + (m + n) * 8
+    assert lls.lls_solve_host_workspace_size(10, 20, o) == 0
+    info = lls.lls_info()
+    assert lls.lls_solve_host(m, n, None, m, None, None, 256, 1 << 20, o, info, None) == -1
+    assert lls.lls_solve_host(m, n, 256, m - 1, 256, 256, 256, 1 << 20, o, info, None) == -1
+    # the lowest-node block: sizes and arguments
+    assert lls.lls_panel_block_qr_workspace_size(4000, 16, 16) > 0
+    assert lls.lls_panel_block_qr_workspace_size(20, 16, 16) == 0          # m < w1 + w2
+    assert lls.lls_panel_block_qr(4000, 16, 16, 0, None, 4000, None, 4000, None, 32, 256, 1 << 20, None) == -1
+    assert lls.lls_panel_block_qr(4000, 16, 16, 0, 256, 4000, 256, 4000, 256, 31, 256, 1 << 20, None) == -1
+    assert lls.lls_panel_block_qr(4000, 16, 16, lls.PREC["fp32"], 256, 4000, 256, 4000, 256, 32, 256, 1 << 20,
+                                  None) == -1
+    # the wait self-test: workspace checks before any device work
+    assert lls.lls_selftest_wait_timeout(None, 256, None) == -1
+    assert lls.lls_selftest_wait_timeout(256, 128, None) == -1
+    assert lls.lls_selftest_wait_timeout(257, 1024, None) == -1
+
+
 def test_panel_leaf_option(lib):
     # the options struct carries the panel leaf (0 CGS2, 1 MGS of Alg. 4); other values are
     # argument errors, and the default is CGS2
