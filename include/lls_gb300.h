@@ -160,6 +160,10 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
  * Errors: as lls_solve; LLS_ERR_ARG also when A, b or x is not page-locked host memory.
  * -------------------------------------------------------------------------- */
 size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts);
+/* The column chunks of lls_solve_host's upload for n columns: writes start[0..count] (chunk k
+ * covers columns [start[k], start[k+1]), start[0] = 0, start[count] = n) and returns count, or
+ * LLS_ERR_ARG (n < 1, start NULL, max_entries < count + 1). Host only. */
+int lls_upload_chunks(int n, int* start, int max_entries);
 int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
                    size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream);
 

@@ -680,6 +680,15 @@ static int enqueue_solve_host(void* p, cudaStream_t st, cudaEvent_t* ev, bool ca
     return LLS_OK;
 }
 
+int lls_upload_chunks(int n, int* start, int max_entries) {
+    if (n < 1 || !start || max_entries < 2) return LLS_ERR_ARG;
+    ColumnGate g;
+    plan_chunks(n, g);
+    if (g.count + 1 > max_entries) return LLS_ERR_ARG;
+    for (int k = 0; k <= g.count; ++k) start[k] = g.start[k];
+    return g.count;
+}
+
 static bool page_locked(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

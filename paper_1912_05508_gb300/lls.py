@@ -29,6 +29,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_lowp_projection_noalloc", "lls_panel_qr_workspace_size", "lls_panel_qr",
            "lls_panel_block_qr_workspace_size", "lls_panel_block_qr",
            "lls_solve_host_workspace_size", "lls_solve_host", "lls_selftest_wait_timeout",
+           "lls_upload_chunks",
            "lls_householder_workspace_size", "lls_householder_solve")
 
 
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.lls_solve_host.restype = i
     lib.lls_selftest_wait_timeout.argtypes = [vp, sz, vp]
     lib.lls_selftest_wait_timeout.restype = i
+    lib.lls_upload_chunks.argtypes = [i, C.POINTER(C.c_int), i]
+    lib.lls_upload_chunks.restype = i
     lib.lls_lowp_projection_workspace_size.argtypes = [i, i, i]
     lib.lls_lowp_projection_workspace_size.restype = sz
     lib.lls_lowp_projection.argtypes = [i, i, i, i, vp, vp, i, vp, vp, i, vp, i, vp, vp, sz, vp]
@@ -179,6 +182,15 @@ def lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream) 
     return load().lls_solve(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes,
                             C.byref(opts) if opts is not None else None,
                             C.byref(info) if info is not None else None, stream)
+
+
+def lls_upload_chunks(n):
+    """Column boundaries of lls_solve_host's upload chunks (a list starting at 0, ending at n)."""
+    buf = (C.c_int * 64)()
+    count = load().lls_upload_chunks(n, buf, 64)
+    if count < 0:
+        raise LLSError(count, "lls_upload_chunks")
+    return list(buf[:count + 1])
 
 
 def lls_selftest_wait_timeout(ws, ws_bytes, stream) -> int:

@@ -92,3 +92,22 @@ def test_panel_leaf_option(lib):
     assert lls.qr_factor_workspace_size(1000, 64, lls.make_options(panel_leaf="mgs")) > 0
     assert lls.qr_factor_workspace_size(1000, 64, lls.make_options(panel_leaf=2)) == 0
     assert lls.lls_solve_workspace_size(1000, 64, lls.make_options(panel_leaf=-1)) == 0
+
+
+@pytest.mark.parametrize("n", [1, 40, 64, 65, 128, 700, 4096, 5000, 16384, 2 ** 31 - 1])
+def test_upload_chunks_partition_the_columns(lib, n):
+    # the host-operand solve uploads A in these chunks: contiguous, covering [0, n), the first
+    # 64 columns wide and then doubling, so the factorization waits only for the first chunk
+    s = lls.lls_upload_chunks(n)
+    assert s[0] == 0 and s[-1] == n and all(a < b for a, b in zip(s, s[1:]))
+    assert len(s) - 1 <= 32
+    assert s[1] == min(64, n)
+    for k in range(2, len(s) - 1):
+        assert s[k] == 2 * s[k - 1]
+
+
+def test_upload_chunks_argument_errors(lib):
+    buf = (C.c_int * 64)()
+    assert lib.lls_upload_chunks(0, buf, 64) == -1
+    assert lib.lls_upload_chunks(4096, None, 64) == -1
+    assert lib.lls_upload_chunks(4096, buf, 3) == -1          # 7 chunks need 8 entries
