@@ -232,6 +232,10 @@ int lls_backward(int batch, const int* m, const int* n, const float* const* A, c
  * lls_lowp_update:
  *   A2 [in/out] m x w2 FP32 (lda >= m): A2 -= (Q1l R12l)[:, j] * 2^-f[j].
  *   ws          >= 256 bytes of 256-B aligned scratch (device error word).
+ * Both calls are asynchronous, so a failure on the device cannot be returned: if a bounded
+ * device wait gives up (about 2 s), the affected outputs are written as NaN instead (the whole
+ * of R12 and R12l with f = 0 for the projection; the affected 128-row tiles of A2 for the
+ * update), and the error word in ws holds LLS_ERR_TIMEOUT's device code.
  * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED (alignment), LLS_ERR_CUDA.
  * -------------------------------------------------------------------------- */
 size_t lls_lowp_projection_workspace_size(int m, int w1, int w2);
@@ -337,7 +341,10 @@ int lls_householder_solve(int m, int n, int prec, const float* A, int lda, const
  *   w1 = w2 = 128 fits; m = 32768 with w1 = w2 = 256 does not).
  * Set-up: the first call on each device, with that device current, looks up the array's
  *   device address (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture begins.
+ *   stream capture begins. cudaDeviceReset discards the array with the device's context and
+ *   leaves the cached address stale: do not call this entry point after resetting the device.
+ * Failure: as for lls_lowp_projection, a device wait that gives up leaves R12 and R12l as NaN
+ *   (f = 0); the error word itself is inside the library's array and is not visible.
  * Sharing: all calls in the process use the same array, which keeps the last call's
  *   contents; each call clears the error word itself on the given stream. Calls whose work
  *   overlaps on the GPU (different streams without ordering, several host threads) race on

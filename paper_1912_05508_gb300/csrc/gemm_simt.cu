@@ -101,13 +101,15 @@ int sgemm(bool ta, bool tb, int M, int N, int K, float alpha, const float* A, in
 // Split-K reduction and epilogue of the projection R12 = Q1^T A2 (the projection step of Alg. 2):
 // R12[i, j] = (sum_s part[s][i, j]) * 2^-e_j in a fixed order, stored in FP32; then the
 // column exponent f_j of R12 and R12l = round(R12 * 2^f_j) for the update product.
-// One CTA per column j.
+// One CTA per column j. When the product kernel before it gave up a bounded wait (err set),
+// its partial sums are incomplete: the column is then written as NaN (R12, R12l) with f_j = 0,
+// so the failure shows in the caller's outputs and in anything computed from them.
 // ---------------------------------------------------------------------------------------
 template <typename TL>
 __global__ void __launch_bounds__(256)
 proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
                    const int* __restrict__ e, const int* __restrict__ sq, float* __restrict__ R12, int ldr,
-                   TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int kind) {
+                   TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int kind, const int* __restrict__ err) {
     // Threads split as (row slot i0 < rp) x (split group g < G): group g sums splits
     // g, g + G, ... (four independent loads per trip); the groups are then added in order
     // g = 0, 1, ..., so the result does not depend on timing.
@@ -115,6 +117,14 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
     __shared__ float s_red[8];
     __shared__ int s_f;
     const int j = blockIdx.x;
+    if (err && *(volatile const int*)err != DEV_OK) {
+        for (int i = threadIdx.x; i < w1; i += 256) {
+            R12[(size_t)i + (size_t)j * ldr] = __int_as_float(0x7fc00000);
+            if (R12l) R12l[(size_t)i + (size_t)j * ldrl] = LowPrec<TL>::from_float(__int_as_float(0x7fc00000));
+        }
+        if (threadIdx.x == 0 && f) f[j] = 0;
+        return;
+    }
     const float se = e ? pow2f(-e[j]) : 1.f;
     const size_t plane = (size_t)w1 * w2;
     int rp = 1;
@@ -171,18 +181,19 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
 }
 
 int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, const int* sq, float* R12, int ldr,
-                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st) {
+                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st, const int* err) {
     if (lowp == 0)
-        proj_reduce_kernel<__half><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, nullptr, R12, ldr, (__half*)R12l, ldrl, f, 1);
+        proj_reduce_kernel<__half><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, nullptr, R12, ldr, (__half*)R12l, ldrl, f, 1,
+                                                       err);
     else if (lowp == 1)
         proj_reduce_kernel<__nv_bfloat16><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, nullptr, R12, ldr,
-                                                              (__nv_bfloat16*)R12l, ldrl, f, 0);
+                                                              (__nv_bfloat16*)R12l, ldrl, f, 0, err);
     else if (lowp == 2)
         proj_reduce_kernel<__nv_fp8_e4m3><<<w2, 256, 0, st>>>(part, splits, w1, w2, e, sq, R12, ldr,
-                                                              (__nv_fp8_e4m3*)R12l, ldrl, f, 2);
+                                                              (__nv_fp8_e4m3*)R12l, ldrl, f, 2, err);
     else
         proj_reduce_kernel<float><<<w2, 256, 0, st>>>(part, splits, w1, w2, nullptr, nullptr, R12, ldr, (float*)nullptr,
-                                                      0, f, 0);
+                                                      0, f, 0, err);
     LLS_LAUNCH_CHECK("proj_reduce", st);
     return LLS_OK;
 }
@@ -206,7 +217,7 @@ int simt_projection_f32(const float* Q1, const float* A2, int ldw, int m, int w1
     gemm_simt_kernel<float, float, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         w1, w2, m, kc, Q1, ldw, A2, ldw, part, 0, 1.f, 0.f, nullptr);
     LLS_LAUNCH_CHECK("simt_proj_f32", st);
-    return proj_reduce(part, splits, w1, w2, nullptr, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st);
+    return proj_reduce(part, splits, w1, w2, nullptr, nullptr, R12, ldr, nullptr, 0, nullptr, 3, st, nullptr);
 }
 
 int simt_update_f32(const float* Q1, int ldw, const float* R12, int ldr, float* A2, int m, int w1,
@@ -230,7 +241,7 @@ static int simt_lowp_projection(const ProjCall& c, cudaStream_t st) {
     gemm_simt_kernel<TL, TL, true, false, EPI_PARTIAL><<<grid, kSThreads, 0, st>>>(
         c.w1, c.w2, c.m, kc, (const TL*)c.Q1l, c.ldh, (const TL*)c.A2l, c.ldh, c.part, 0, 1.f, 0.f, nullptr);
     LLS_LAUNCH_CHECK("simt_upd_f32", st);
-    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st, nullptr);
 }
 
 template <typename TL>

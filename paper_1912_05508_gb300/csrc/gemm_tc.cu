@@ -28,7 +28,7 @@
 namespace lls {
 
 int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, const int* sq, float* R12, int ldr,
-                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st);
+                void* R12l, int ldrl, int* f, int lowp, cudaStream_t st, const int* err);
 
 constexpr int kTcThreads = 128;
 constexpr int kTcBM = 128;
@@ -316,6 +316,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                            globaltimer_ns() - t0 < kSpinLimitNs) {
                     }
             }
+            if (EPI == TC_EPI_UPDATE) {
+                // the tile's update is unknown: write it as NaN, so the failure shows in A2
+                const int i = m0 + warp * 32 + lane;
+                if (i < a.M)
+                    for (int j = n0; j < n0 + BN && j < a.N; ++j)
+                        a.out[(size_t)i + (size_t)j * a.ldo] = __int_as_float(0x7fc00000);
+            }
         }
     }
     tc_fence_before();
@@ -444,7 +451,7 @@ int gemm_projection(const ProjCall& c, cudaStream_t st) {
     dim3 grid(ceil_div(c.w1, kTcBM), ceil_div(c.w2, bn), splits);
     if (c.lowp == 2) LLS_TRY((launch_bn<false, TC_EPI_PARTIAL, true>(bn, tA, tB, a, grid, st)));
     else LLS_TRY((launch_bn<false, TC_EPI_PARTIAL>(bn, tA, tB, a, grid, st)));
-    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st);
+    return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st, c.err);
 }
 
 int gemm_update(const UpdCall& c, cudaStream_t st) {

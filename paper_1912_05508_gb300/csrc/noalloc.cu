@@ -29,7 +29,9 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // The name g_noalloc_scratch in host code is only a host-side stand-in for the array; the
 // device address differs per device and must be asked for with that device current. This is
-// done on the first call on each device and cached.
+// done on the first call on each device and cached for the life of the process. A
+// cudaDeviceReset discards the device's context and with it the array, so the cached address
+// is then stale: the entry point is not to be used after a reset of that device.
 int scratch_address(void** out) {
     int dev = 0;
     LLS_CUDA_TRY(cudaGetDevice(&dev));
@@ -66,8 +68,11 @@ extern "C" int lls_lowp_projection_noalloc(int m, int w1, int w2, int prec, cons
     pc.part = ar.take<float>(partials);
     pc.err = ar.take<int>(16);
     if (!ar.ok) return LLS_ERR_TOO_LARGE;
-    // The array keeps whatever the previous call left. The partial sums are fully written by
-    // the product kernel before they are read; the error word must start at zero.
+    // The array keeps whatever the previous call left. The error word must start at zero. The
+    // partial sums are fully written by the product kernel before the reduction reads them,
+    // except when a bounded wait of the product gives up: it then leaves its partials
+    // unwritten and sets the error word, and the reduction, seeing the word, writes R12 and
+    // R12l as NaN (f = 0) instead of summing what an earlier call left there.
     LLS_CUDA_TRY(cudaMemsetAsync(pc.err, 0, sizeof(int) * 16, stream));
     pc.Q1l = Q1l; pc.A2l = A2l; pc.ldh = ldh; pc.m = m; pc.w1 = w1; pc.w2 = w2; pc.e = e;
     pc.R12 = R12; pc.ldr = ldr; pc.R12l = R12l; pc.ldrl = ldrl; pc.f = f;

@@ -15,6 +15,7 @@ import torch
 
 from oracle import metrics, rgsqrf
 from paper_1912_05508_gb300 import lls
+from parity import r_entry_err
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +64,7 @@ def test_panel_matches_oracle_tsqr(prec, m, b, kappa):
     assert metrics.orthogonality(Q) <= 8 * b * U32
     Qo, Ro = rgsqrf.tsqr(A64, leaf_rows=1024)
     assert np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro) <= 4 * np.sqrt(b) * kappa * U32 + 4 * b * U32
+    assert r_entry_err(Rg, Ro) <= 4 * np.sqrt(b) * kappa * U32 + 4 * b * U32
     if prec != "fp32":
         assert torch.equal(Wh, W.to(TDT[prec]))
 
@@ -126,6 +128,7 @@ def test_block_matches_oracle_recursion(prec, m, w1, w2):
     u = ULOW[prec]
     assert np.array_equal(np.tril(Rg, -1), np.zeros_like(Rg))
     assert np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro) <= 8 * u
+    assert r_entry_err(Rg, Ro) <= 4 * u
     assert metrics.qr_factorization_error(A, Q, Rg) <= 4 * u
     assert metrics.orthogonality(Q, "2") <= 4 * u * kappa * (w1 + w2) ** 0.5
     # the product-precision copy is Q rounded to nearest even

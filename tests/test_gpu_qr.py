@@ -17,6 +17,7 @@ import torch
 
 from oracle import direct, metrics, rgsqrf
 from paper_1912_05508_gb300 import lls, synth
+from parity import r_entry_err
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,7 @@ def test_lowprec_matches_oracle_recursion(prec, m, n, pw):
     Qo, Ro = rgsqrf.rgsqrf(A, pw, prec, leaf_rows=256)
     u = ULOW[prec]
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    assert r_entry_err(R, Ro) <= 4 * u
     fe = metrics.qr_factorization_error(A, Q, R)
     assert fe <= 4 * u
     assert metrics.orthogonality(Q, "2") <= 4 * u * kappa * n ** 0.5
@@ -82,6 +84,7 @@ def test_two_panel_blocks_match_oracle(prec, m, n):
     Qo, Ro = rgsqrf.rgsqrf(A, 16, prec, leaf_rows=256)
     u = ULOW[prec]
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    assert r_entry_err(R, Ro) <= 4 * u
     fe = metrics.qr_factorization_error(A, Q, R)
     assert fe <= 4 * u
     assert metrics.orthogonality(Q, "2") <= 4 * u * kappa * n ** 0.5
@@ -116,6 +119,7 @@ def test_column_scaling_handles_wide_column_range():
     colrel = np.linalg.norm(E, axis=0) / np.linalg.norm(A.astype(np.float64), axis=0)
     assert colrel.max() <= 16 * ULOW["fp16"]
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * ULOW["fp16"]
+    assert r_entry_err(R, Ro) <= 4 * ULOW["fp16"]
 
 
 @pytest.mark.parametrize("pw", [16, 32])
@@ -131,6 +135,7 @@ def test_column_scaling_in_every_node_width(pw):
     Qo, Ro = rgsqrf.rgsqrf(A, pw, "fp16", leaf_rows=256)
     colrel = np.linalg.norm(R - Ro, axis=0) / np.linalg.norm(Ro, axis=0)
     assert colrel.max() <= 2 * ULOW["fp16"]
+    assert r_entry_err(R, Ro) <= 2 * ULOW["fp16"]
     assert metrics.orthogonality(Q, "2") <= 2 * ULOW["fp16"]
 
 
@@ -193,6 +198,7 @@ def test_mgs_panel_matches_oracle_mgs_tsqr(m, b, kappa):
     assert metrics.qr_factorization_error(A64, Q, R) <= 8 * b * U32
     assert metrics.orthogonality(Q, "2") <= 16 * b * kappa * U32
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 4 * np.sqrt(b) * kappa * U32 + 4 * b * U32
+    assert r_entry_err(R, Ro) <= 4 * np.sqrt(b) * kappa * U32 + 4 * b * U32
 
 
 def test_cgs2_panel_keeps_orthogonality_where_mgs_loses_it():
@@ -215,6 +221,7 @@ def test_mgs_leaves_in_the_recursion_match_oracle(prec):
     Qo, Ro = rgsqrf.rgsqrf(A, 16, prec, leaf_rows=256, leaf="mgs")
     u = ULOW[prec]
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 8 * u
+    assert r_entry_err(R, Ro) <= 4 * u
     assert metrics.qr_factorization_error(A, Q, R) <= 4 * u
 
 
