@@ -9,7 +9,7 @@ residual). Inputs are generated on the device in FP64 and rounded to FP32.
 
 Prints ONE JSON line (rank 0). `value` is the mean device time per solve in ms
 (lower is better); `qr_tflops` is (2 m n^2 - 2/3 n^3) / QR time. `--impl reference`
-times the CPU oracle (FP64 Householder, Alg. 1) instead, on a column sample.
+times the CPU oracle (FP64 Householder, Alg. 1) instead, on the same problem.
 
 Multi-GPU: the path solves one independent problem per GPU (replicas, no collective);
 `value` is then the max-over-ranks time per solve and `problems_per_s` counts all ranks.
@@ -41,8 +41,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--m", type=int, default=32768)
-    ap.add_argument("--n", type=int, default=4096)
+    # (torch.distributed.run would read an abbreviated "--m" as one of its own options)
+    ap.add_argument("--rows", "--m", dest="m", type=int, default=32768)
+    ap.add_argument("--cols", "--n", dest="n", type=int, default=4096)
     ap.add_argument("--kind", default="geometric")
     ap.add_argument("--kappa", type=float, default=1e3)
     ap.add_argument("--seed", type=int, default=2)
@@ -53,7 +54,6 @@ def parse_args():
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-householder", action="store_true")
-    ap.add_argument("--cpu-sample-cols", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -119,63 +119,128 @@ def summarize_clocks(lines):
             "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(A32_dev, b_dev, cols, m, n):
-    """Oracle (FP64 Householder LLS, Alg. 1) on the first `cols` columns, scaled by flops."""
-    import numpy as np
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_threads():
+    """Threads the C oracle's OpenMP loops use (OMP_NUM_THREADS, else every core)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else os.cpu_count()
+
+
+def cpu_baseline(A32_dev, b_dev, m, n):
+    """The oracle (FP64 Householder least squares, Alg. 1) on the same A and b, one full solve,
+    timed on the host's cores. No sampling and no scaling: the value is that solve's time."""
     from oracle import direct
-    A_s = A32_dev[:, :cols].cpu().numpy()
+    A = A32_dev.cpu().numpy()
     b = b_dev.cpu().numpy()
     direct.lib()
     t0 = time.perf_counter()
-    direct.lls(A_s.astype(np.float64), b)
+    direct.lls(A, b)
     dt = time.perf_counter() - t0
-    scale = qr_flops(m, n) / qr_flops(m, cols)
-    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 Householder LLS on the first {cols} of {n} columns ({m} rows), "
-                      f"{dt:.2f} s measured, scaled by the flop ratio {scale:.1f}"}
+    return {"value": dt * 1e3, "unit": "ms", "cores": oracle_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
+            "sample": f"one full FP64 Householder solve (unblocked, OpenMP over the trailing columns) of the "
+                      f"same {m}x{n} problem, A and b as the GPU solves them"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the same problem as the GPU arm
+    (the same generator, seed and sizes). Warm-up steps solve the small 1024 x 128 problem of
+    the same family (they load the library and start the threads); each timed step is one full
+    solve of the benchmark problem. Timed steps stop early once 240 s have been spent, and the
+    line reports the number actually timed."""
     rank, ws = dist_setup("gloo")
     if rank != 0:
         return
-    import numpy as np
+    import torch
     from oracle import direct
     from paper_1912_05508_gb300 import synth
-    cols = 512
-    rng = synth.rng_for(args.seed)
-    A = rng.standard_normal((args.m, cols)).astype(np.float32)
-    b = rng.standard_normal(args.m)
-    A64 = A.astype(np.float64)
+    m, n = args.m, args.n
+    if torch.cuda.is_available():
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        A_d, b_d = make_inputs(args, m, n, 0, dev)
+        A, b = A_d.cpu().numpy(), b_d.cpu().numpy()
+        del A_d, b_d
+        torch.cuda.empty_cache()
+        gen = "generated on the GPU as in the GPU arm"
+    else:
+        p = synth.svd_lls(m, n, args.kind, args.kappa, seed=args.seed)
+        A, b = p.A, p.b
+        gen = "generated on the CPU (no GPU present): same family and seed, different random stream"
+    small = synth.svd_lls(1024, 128, args.kind, args.kappa, seed=1)
+    direct.lib()
     for _ in range(args.warmup):
-        direct.lls(A64, b)
+        direct.lls(small.A, small.b)
     times = []
+    budget_s = 240.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        direct.lls(A64, b)
+        direct.lls(A, b)
         times.append(time.perf_counter() - t0)
-    scale = qr_flops(args.m, args.n) / qr_flops(args.m, cols)
-    ms = statistics.mean(times) * 1e3 * scale
-    cfg = {"workload": f"single LLS {args.m}x{args.n} FP32, {args.kind} kappa={args.kappa:g}",
-           "sample": f"{cols}-column Gaussian sample, scaled by flops x{scale:.1f}"}
+        if sum(times) > budget_s:
+            break
+    ms = statistics.mean(times) * 1e3
+    sample = (f"{len(times)} full FP64 Householder solves of the {m}x{n} problem ({gen}); warm-up: "
+              f"{args.warmup} solves of the 1024x128 problem of the same family")
+    cfg = {"workload": f"single LLS {m}x{n} FP32, {args.kind} kappa={args.kappa:g}", "m": m, "n": n,
+           "kind": args.kind, "kappa": args.kappa, "seed": args.seed, "sample": sample}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
-                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                      "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                       "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-                      "cpu_baseline": {"value": ms, "unit": "ms", "cores": os.cpu_count(),
-                                       "kind": "oracle", "sample": cfg["sample"]},
+                      "steps_ms": [round(t * 1e3, 1) for t in times],
+                      "cpu_baseline": {"value": ms, "unit": "ms", "cores": oracle_threads(), "cpu_model": cpu_model(),
+                                       "kind": "oracle", "sample": sample},
                       "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}))
 
 
-# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel as
-# it stands, from the captures summarised under profiles/; None once a kernel changes.
-# tc_projection is the product kernel alone (the split-K reduce is a separate, small launch).
-NCU_TRAFFIC = {"panel": None,
-               "block": 4336640 + 0,
-               "tc_projection": 335482624 + 23355136,
-               "tc_update": 415756288 + 224454400,
-               "cgls": 24629498624 + 364217344}
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel, from
+# the captures summarised under profiles/, each with the SHA-256 (first 16 hex digits) of the
+# kernel's source file at the time of the capture. A kernel whose source has changed since
+# reports null until it is captured again. tc_projection is the product kernel alone (the
+# split-K reduce is a separate, small launch).
+NCU_TRAFFIC = {"block": (4336640 + 0, "panel_flat.cu", "2d7b019878166ac2"),
+               "tc_projection": (335482624 + 23355136, "gemm_tc.cu", "7aff50032693834b"),
+               "tc_update": (415756288 + 224454400, "gemm_tc.cu", "7aff50032693834b"),
+               "cgls": (24629498624 + 364217344, "krylov.cu", "d7dd0203f719dbb7")}
+
+
+def source_digest(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1912_05508_gb300", "csrc", name)
+    try:
+        with open(path, "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def ncu_traffic(key):
+    """The captured DRAM bytes per launch of a kernel, or None when there is no capture of the
+    kernel as its source stands."""
+    rec = NCU_TRAFFIC.get(key)
+    if rec is None:
+        return None
+    nbytes, src, digest = rec
+    return nbytes if source_digest(src) == digest else None
 
 
 def max_over_ranks(value, world_size, device):
@@ -311,7 +376,7 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
                     "unit": "TFLOP/s", "us_per_launch": t * 1e3, "algorithmic_flops_per_launch": fl}
     for k, v in out.items():
         v["frac"] = v["achieved"] / v["peak"]
-        v["traffic"] = NCU_TRAFFIC.get(k)
+        v["traffic"] = ncu_traffic(k)
     return out
 
 
@@ -515,7 +580,7 @@ def main():
     kernels = kernel_rooflines(m, n, pw, args.prec, stream, dev, hbm_peak, tc_peak)
     kernels["cgls"] = {"kernel": f"{args.krylov}_kernel (persistent {args.krylov.upper()} iteration, whole Krylov phase)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                       "traffic": NCU_TRAFFIC["cgls"], "algorithmic_bytes_per_launch": kry_bytes}
+                       "traffic": ncu_traffic("cgls"), "algorithmic_bytes_per_launch": kry_bytes}
     # the block kernel (two panels and the node between them) has the largest share of the
     # solve in the ncu launch list
     roofline = dict(kernels["block"] if "block" in kernels else kernels["panel"])
@@ -549,7 +614,7 @@ def main():
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
            "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(A, b, min(args.cpu_sample_cols, n), m, n)
+        out["cpu_baseline"] = cpu_baseline(A, b, m, n)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

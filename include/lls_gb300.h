@@ -35,7 +35,8 @@ typedef enum {
     LLS_OK = 0,
     LLS_NOT_CONVERGED = 1,     /* iteration limit reached; x holds the last iterate, info filled */
     LLS_ERR_ARG = -1,          /* bad size, leading dimension, null pointer or option value */
-    LLS_ERR_SINGULAR = -2,     /* R has a zero or non-finite diagonal entry (rank deficient / inf / nan input) */
+    LLS_ERR_SINGULAR = -2,     /* R has a zero or non-finite diagonal entry (rank deficient / inf / nan in A),
+                                  or b - A x0 is not finite (inf / nan in b or in a given x0) */
     LLS_ERR_CUDA = -3,         /* a CUDA runtime or driver call failed */
     LLS_ERR_WORKSPACE = -4,    /* workspace too small or misaligned */
     LLS_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired (the kernel returned early) */
@@ -56,6 +57,14 @@ typedef enum { LLS_TARGET_FP32 = 0, LLS_TARGET_FP64 = 1 } lls_target;
 /* Krylov method: CGLS (Alg. 5) or LSQR (Paige-Saunders; named in Sec. 5). */
 typedef enum { LLS_KRYLOV_CGLS = 0, LLS_KRYLOV_LSQR = 1 } lls_krylov;
 
+/* Starting point of the Krylov iteration. Alg. 5 starts from x = 0 (LLS_X0_ZERO). LLS_X0_GIVEN
+ * starts from the x the caller passes in (a warm start, e.g. the solution of a nearby problem).
+ * LLS_X0_DIRECT starts from the direct solve with the mixed-precision factors,
+ * x0 = R^{-1} (Q^T b) (Alg. 1's last two steps on the RGSQRF Q and R; Sec. 3.2.2 and 4.2.2):
+ * its error is at the level of the low-precision products, so CGLS starts with
+ * ||A (x0 - x*)|| of about u_low ||b|| instead of ||b|| and needs fewer iterations. */
+typedef enum { LLS_X0_ZERO = 0, LLS_X0_GIVEN = 1, LLS_X0_DIRECT = 2 } lls_x0;
+
 typedef struct {
     int gemm_prec;     /* lls_gemm_prec, default LLS_PREC_FP16 */
     int target;        /* lls_target, default LLS_TARGET_FP64 */
@@ -74,6 +83,7 @@ typedef struct {
                           panel's condition number. MGS panels are built for panels whose stacked
                           leaf R factors fit one level (m <= 65536 at panel_width 16); taller panels,
                           and the batched solver, return LLS_ERR_UNSUPPORTED with it. */
+    int x0;            /* lls_x0, default LLS_X0_ZERO; the batched solver takes LLS_X0_ZERO only */
 } lls_options;
 
 typedef struct {
@@ -127,7 +137,8 @@ int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R
  *
  *  A     [in]  m x n FP32, lda >= m; the problem is defined for these FP32 values.
  *  b     [in]  m FP64.
- *  x     [out] n FP64 (the FP32 target also returns FP64).
+ *  x     [out] n FP64 (the FP32 target also returns FP64); [in] as well with
+ *              opts->x0 = LLS_X0_GIVEN, where it holds the starting point.
  *  R_out [out] n x n FP32 (ldr >= n) receives the preconditioner R, or NULL.
  *  info  [out] HOST pointer or NULL. When non-NULL the call synchronizes `stream`
  *              before returning and fills *info; when NULL the call is fully
@@ -153,7 +164,8 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
  *  A  [in]  m x n FP32 page-locked host memory, column-major, lda >= m.
  *  b  [in]  m FP64 page-locked host memory.
  *  x  [out] n FP64 page-locked host memory; valid once `stream` has synchronized (the call
- *           synchronizes itself when info is non-NULL).
+ *           synchronizes itself when info is non-NULL). [in] as well with opts->x0 =
+ *           LLS_X0_GIVEN: it is uploaded with b and is the starting point.
  *  ws       lls_solve_host_workspace_size(m, n, opts) bytes of DEVICE memory, 256-B
  *           aligned: the lls_solve workspace plus device copies of A, b and x.
  *  opts, info, stream: as lls_solve (no R_out).

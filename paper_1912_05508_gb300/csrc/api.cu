@@ -7,6 +7,7 @@
 //   update A2 <- A2 - Q1 R12 (Alg. 2)                 -> FP32 in place
 // and for every leaf (<= panel_width columns) the CAQR panel (Eq. caqr). All of it is
 // asynchronous on the caller's stream; nothing is allocated.
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <mutex>
@@ -49,6 +50,7 @@ static bool valid_opts(const lls_options& o) {
     if (o.leaf_rows != 256) return false;
     if (o.reorth != 0 && o.reorth != 1) return false;
     if (o.panel_leaf != 0 && o.panel_leaf != 1) return false;
+    if (o.x0 < LLS_X0_ZERO || o.x0 > LLS_X0_DIRECT) return false;
     return true;
 }
 
@@ -475,14 +477,17 @@ int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void*
 }
 
 static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w, float*& R,
-                       float*& Minv, float*& Mt, float*& tmp, void*& ks, size_t& ks_bytes) {
+                       float*& Minv, float*& Mt, float*& tmp, void*& ks, size_t& ks_bytes, double*& hist) {
     qr_layout(ar, m, n, o, w);
     R = ar.take<float>((size_t)n * n);
     Minv = ar.take<float>((size_t)n * n);
     Mt = ar.take<float>((size_t)n * n);
     tmp = ar.take<float>((size_t)n * n);
     ks_bytes = krylov_scratch_bytes(m, n, 0, o.krylov == LLS_KRYLOV_CGLS);
+    const size_t ds = direct_start_scratch_bytes(m, n);   // the direct start borrows the Krylov scratch
+    if (ks_bytes < ds) ks_bytes = ds;
     ks = ar.take<char>(ks_bytes);
+    hist = ar.take<double>(kHistLen);
 }
 
 size_t lls_solve_workspace_size(int m, int n, const lls_options* opts) {
@@ -490,8 +495,8 @@ size_t lls_solve_workspace_size(int m, int n, const lls_options* opts) {
     resolve(opts, o);
     if (n < 1 || m < n || !valid_opts(o)) return 0;
     WsArena ar(nullptr, SIZE_MAX);
-    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb;
-    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb);
+    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb; double* hist;
+    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb, hist);
     return ar.off;
 }
 
@@ -502,6 +507,7 @@ struct SolveCall {
     QrWs w;
     float *R, *Minv, *Mt, *tmp;
     void* ks; size_t kb;
+    double* hist;
 };
 
 // The solve on `st`; gate non-null when W fills in chunks on another stream (host input).
@@ -515,11 +521,15 @@ static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool captu
     LLS_TRY(tri_inverse(c.R, n, n, c.o.panel_width, c.Minv, c.Mt, c.tmp, c.w.err, st));
     LLS_TRY(fro_sumsq(c.A, c.lda, m, n, c.w.red, c.w.dinfo + 8, st));
     LLS_TRY(fro_sumsq(c.Minv, n, n, n, c.w.red + 4096, c.w.dinfo + 9, st));
+    if (c.o.x0 == LLS_X0_DIRECT)   // x0 = R^{-1} Q^T b from the factors; W holds Q
+        LLS_TRY(direct_start(c.w.W, c.w.ldw, m, n, c.b, c.Mt, c.x, c.ks, c.kb, st));
     if (ev) record_phase(ev[1], st, capturing);
     KrylovCall kc;
     kc.m = m; kc.n = n; kc.A = c.A; kc.lda = c.lda; kc.b = c.b; kc.x = c.x; kc.Minv = c.Minv; kc.Mt = c.Mt;
     kc.method = c.o.krylov; kc.target = c.o.target; kc.tol = c.o.tol; kc.max_iter = c.o.max_iter;
     kc.scratch = c.ks; kc.scratch_bytes = c.kb; kc.dev_err = c.w.err; kc.dev_info = c.w.dinfo;
+    kc.x_zero = c.o.x0 == LLS_X0_ZERO ? 1 : 0;
+    kc.hist = c.hist;
     LLS_TRY(krylov_solve(kc, st));
     if (ev) record_phase(ev[2], st, capturing);
     return LLS_OK;
@@ -529,14 +539,38 @@ static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturi
     return solve_body(*(SolveCall*)p, st, ev, capturing, nullptr);
 }
 
+static bool log_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("LLS_LOG");
+        return v && v[0] && v[0] != '0';
+    }();
+    return on;
+}
+
+// LLS_LOG=1: the stop quantity of every iteration (eta_est for the FP64 target, the forward
+// error estimate for the FP32 target) to stderr, one line per solve.
+static void print_history(const double* hist_dev, int iters, int m, int n, cudaStream_t stream) {
+    const int count = (iters + 1 < kHistLen ? iters + 1 : kHistLen);
+    std::vector<double> h((size_t)count);
+    if (cudaMemcpyAsync(h.data(), hist_dev, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return;
+    fprintf(stderr, "[lls log] m=%d n=%d iterations=%d stop quantity per iteration:", m, n, iters);
+    for (int k = 0; k < count; ++k) fprintf(stderr, " %d:%.3e", k, h[(size_t)k]);
+    fprintf(stderr, "\n");
+}
+
 // Reads the device info record and error word after the solve (synchronizes the stream) and
 // fills info; returns the solve's status.
-static int finish_info(const QrWs& w, cudaEvent_t* ev, lls_info* info, cudaStream_t stream) {
+static int finish_info(const QrWs& w, cudaEvent_t* ev, lls_info* info, cudaStream_t stream,
+                       const double* hist = nullptr, int m = 0, int n = 0) {
     double hinfo[16];
     int herr = 0;
     LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
     LLS_CUDA_TRY(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     LLS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (hist && log_enabled()) print_history(hist, (int)hinfo[0], m, n, stream);
     cudaEventElapsedTime(&info->qr_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&info->krylov_ms, ev[1], ev[2]);
     info->iters = (int)hinfo[0];
@@ -569,7 +603,7 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
     WsArena ar(ws, ws_bytes);
     SolveCall c;
-    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb);
+    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb, c.hist);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
     c.m = m; c.n = n; c.lda = lda; c.ldr = ldr; c.A = A; c.b = b; c.x = x; c.R_out = R_out; c.o = o;
     GraphKey key;
@@ -592,7 +626,7 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
         for (auto& e : own) if (e) cudaEventDestroy(e);
         return rc;
     }
-    rc = finish_info(c.w, ev, info, stream);
+    rc = finish_info(c.w, ev, info, stream, c.hist, m, n);
     for (auto& e : own) cudaEventDestroy(e);
     return rc;
 }
@@ -665,6 +699,8 @@ static int enqueue_solve_host(void* p, cudaStream_t st, cudaEvent_t* ev, bool ca
     float* Ad = const_cast<float*>(c.A);
     LLS_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(c.b), h.bh, sizeof(double) * (size_t)m,
                                  cudaMemcpyHostToDevice, r->side));
+    if (c.o.x0 == LLS_X0_GIVEN)   // the starting x comes from the caller's host x
+        LLS_CUDA_TRY(cudaMemcpyAsync(c.x, h.xh, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, r->side));
     for (int k = 0; k < g.count; ++k) {
         const int c0 = g.start[k], cols = g.start[k + 1] - c0;
         LLS_CUDA_TRY(cudaMemcpy2DAsync(Ad + (size_t)c0 * c.lda, sizeof(float) * (size_t)c.lda,
@@ -703,8 +739,8 @@ size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts) {
     resolve(opts, o);
     if (n < 1 || m < n || !valid_opts(o)) return 0;
     WsArena ar(nullptr, SIZE_MAX);
-    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb;
-    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb);
+    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb; double* hist;
+    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb, hist);
     int lda; float* A; double *b, *x;
     host_layout(ar, m, n, lda, A, b, x);
     return ar.off;
@@ -722,7 +758,7 @@ int lls_solve_host(int m, int n, const float* A, int lda, const double* b, doubl
     WsArena ar(ws, ws_bytes);
     HostSolveCall h;
     SolveCall& c = h.s;
-    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb);
+    lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb, c.hist);
     int ldad; float* Ad; double *bd, *xd;
     host_layout(ar, m, n, ldad, Ad, bd, xd);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
@@ -748,7 +784,7 @@ int lls_solve_host(int m, int n, const float* A, int lda, const double* b, doubl
         rc = run_graphed(key, stream, enqueue_solve_host, &h, info ? ev : nullptr);
         trace_flush();
     }
-    if (rc == LLS_OK && info) rc = finish_info(c.w, ev, info, stream);
+    if (rc == LLS_OK && info) rc = finish_info(c.w, ev, info, stream, c.hist, m, n);
     for (auto& e : own) if (e) cudaEventDestroy(e);
     return rc;
 }
@@ -865,7 +901,7 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
     if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8 || o.reorth ||
-        o.panel_leaf != 0)
+        o.panel_leaf != 0 || o.x0 != LLS_X0_ZERO)
         return LLS_ERR_UNSUPPORTED;
     if (!A || !lda || !b || !x || !ws) return LLS_ERR_ARG;
     for (int i = 0; i < batch; ++i) {

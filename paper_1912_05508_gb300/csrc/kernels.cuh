@@ -125,7 +125,10 @@ struct KrylovCall {
     void* scratch; size_t scratch_bytes;
     int* dev_err;
     double* dev_info;       // [iters, eta, fwd, res, atr, anorm, xnorm, status]
+    int x_zero = 1;         // 1: start from x = 0; 0: start from the x the vector holds
+    double* hist = nullptr; // kHistLen doubles: the stop quantity after each iteration, or null
 };
+constexpr int kHistLen = 4096;   // iterations whose stop quantity the history keeps
 // one_pass: room for the one-pass CGLS engine's row-block copy of A (used when n <= 4096).
 size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass = false);
 int krylov_solve(const KrylovCall& c, cudaStream_t st);
@@ -169,6 +172,12 @@ struct GraphKey {
 typedef int (*EnqueueFn)(void* ctx, cudaStream_t st, cudaEvent_t* ev, bool capturing);
 int run_graphed(const GraphKey& key, cudaStream_t st, EnqueueFn fn, void* ctx, cudaEvent_t* ev_out);
 void record_phase(cudaEvent_t ev, cudaStream_t st, bool capturing);
+
+// ---- direct solve with the mixed-precision factors (direct.cu) ------------------------------
+// x = M (Q^T b) with M = R^{-1} given as Mt = M^T (column-major n x n, ld n); Q m x n FP32.
+size_t direct_start_scratch_bytes(int m, int n);
+int direct_start(const float* Q, int ldq, int m, int n, const double* b, const float* Mt, double* x, void* scratch,
+                 size_t scratch_bytes, cudaStream_t st);
 
 // ---- misc (util.cu) -------------------------------------------------------------------------
 int copy_matrix(const float* src, int lds, float* dst, int ldd, int m, int n, cudaStream_t st);

@@ -70,7 +70,22 @@ struct KArgs {
     float2 *rdf, *tdf, *udf, *pdf;   // double-float copies (hi, lo) of r, t, u, p, written where the
                                      // vectors are produced so no CTA re-splits a whole vector
     int vec_floats;              // floats reserved at the start of dynamic smem for vectors
+    double* hist;                // the stop quantity after each iteration (kHistLen entries), or null
 };
+
+// The stop quantity of iteration `it` into the history (block 0, thread 0; the value is the
+// same in every CTA).
+__device__ __forceinline__ void log_hist(const KArgs& a, int it, double v) {
+    if (a.hist && blockIdx.x == 0 && threadIdx.x == 0 && it < kHistLen) a.hist[it] = v;
+}
+
+// A non-finite ||b - A x||^2 at the start (a NaN or infinity in b, or in the starting x) is
+// reported like a non-finite R: the same value in every CTA, so every CTA returns here.
+__device__ __forceinline__ bool finite_start(const KArgs& a, double rn2) {
+    if (isfinite(rn2)) return true;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.err, DEV_OK, DEV_SINGULAR);
+    return false;
+}
 
 extern __shared__ __align__(16) float2 k_dsm[];
 
@@ -623,6 +638,7 @@ cgls_kernel(KArgs a) {
         xzero = false;
         KB_SYNC();
         rn2 = grid_total(a.bpart, 0);
+        if (!finite_start(a, rn2)) return;
         // ---- u = A^T r, s = M^T u, gamma = ||s||^2 ----
         if constexpr (NC > 0) {
             double dummy = 0.0;
@@ -667,6 +683,7 @@ cgls_kernel(KArgs a) {
             fwd = xn > 0.0 ? mnorm * sn / xn : (sn == 0.0 ? 0.0 : INFINITY);
         }
         const double crit = a.target == LLS_TARGET_FP64 ? eta : fwd;
+        log_hist(a, iters, crit);
         if (crit <= a.tol) { status = 0; break; }
         if (iters >= a.max_iter || restart == kMaxRestarts) { status = 1; break; }
         for (int j = gtid; j < a.n; j += gthreads) {
@@ -762,6 +779,7 @@ cgls_kernel(KArgs a) {
             const double e1 = xn > 0.0 ? sn / (anorm * xn) : INFINITY;
             const double f1 = xn > 0.0 ? mnorm * sn / xn : INFINITY;
             KB_SYNC();
+            log_hist(a, iters, a.target == LLS_TARGET_FP64 ? e1 : f1);
             if ((a.target == LLS_TARGET_FP64 ? e1 : f1) <= a.tol) break;
         }
         // loop back: the top of the restart loop recomputes b - A x and re-tests
@@ -828,6 +846,7 @@ lsqr_kernel(KArgs a) {
         xzero = false;
         KB_SYNC();
         rn2 = grid_total(a.bpart, 0);
+        if (!finite_start(a, rn2)) return;
         double beta = sqrt(rn2);
         // ---- A^T r (scaled to A^T u below), ||x||^2 ----
         at_times_partials(a, a.r);
@@ -865,6 +884,7 @@ lsqr_kernel(KArgs a) {
             fwd = xn > 0.0 ? mnorm * sn / xn : (sn == 0.0 ? 0.0 : INFINITY);
         }
         const double crit = a.target == LLS_TARGET_FP64 ? eta : fwd;
+        log_hist(a, iters, crit);
         if (crit <= a.tol) { status = 0; break; }
         if (iters >= a.max_iter || restart == kMaxRestarts || !(alpha > 0.0)) { status = 1; break; }
         {
@@ -952,6 +972,7 @@ lsqr_kernel(KArgs a) {
             const double atr = phibar * alpha * fabs(c);
             const double e1 = xn > 0.0 ? atr / (anorm * xn) : INFINITY;
             const double f1 = xn > 0.0 ? mnorm * atr / xn : INFINITY;
+            log_hist(a, iters, a.target == LLS_TARGET_FP64 ? e1 : f1);
             if ((a.target == LLS_TARGET_FP64 ? e1 : f1) <= a.tol || !(alpha > 0.0) || !(beta > 0.0)) break;
             // t = M v, d = t - (theta / rho) d
             stage_vec(a.p, a.n);
@@ -1308,7 +1329,8 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     a.info = c.dev_info;
     a.anorm2 = c.dev_info + 8;
     a.mnorm2 = c.dev_info + 9;
-    a.tol = c.tol; a.max_iter = c.max_iter; a.target = c.target; a.x_zero = 1;
+    a.tol = c.tol; a.max_iter = c.max_iter; a.target = c.target; a.x_zero = c.x_zero;
+    a.hist = c.hist;
     a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
     char* base = (char*)c.scratch;
     if (nc > 0) {
@@ -1338,6 +1360,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.M = c.Minv; a.Mt = c.Mt;
     a.err = c.dev_err; a.info = c.dev_info; a.anorm2 = nullptr; a.mnorm2 = nullptr;
     a.tol = c.tol; a.max_iter = c.max_iter; a.target = LLS_TARGET_FP64; a.x_zero = 1;
+    a.hist = nullptr;
     a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
     a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;

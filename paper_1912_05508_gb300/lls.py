@@ -17,6 +17,7 @@ PREC = {"fp16": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp64": 4}
 TARGET = {"fp32": 0, "fp64": 1}
 KRYLOV = {"cgls": 0, "lsqr": 1}
 PANEL_LEAF = {"cgs2": 0, "mgs": 1}
+X0 = {"zero": 0, "given": 1, "direct": 2}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
           -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED",
           -7: "LLS_ERR_TOO_LARGE"}
@@ -36,7 +37,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
 class lls_options(C.Structure):
     _fields_ = [("gemm_prec", C.c_int), ("target", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("panel_width", C.c_int), ("krylov", C.c_int),
-                ("leaf_rows", C.c_int), ("reorth", C.c_int), ("panel_leaf", C.c_int)]
+                ("leaf_rows", C.c_int), ("reorth", C.c_int), ("panel_leaf", C.c_int), ("x0", C.c_int)]
 
 
 class lls_info(C.Structure):
@@ -134,7 +135,7 @@ def default_options() -> lls_options:
 
 
 def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-                 krylov="cgls", leaf_rows=256, reorth=0, panel_leaf="cgs2") -> lls_options:
+                 krylov="cgls", leaf_rows=256, reorth=0, panel_leaf="cgs2", x0="zero") -> lls_options:
     o = lls_options()
     load().lls_default_options(C.byref(o))
     o.gemm_prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -146,6 +147,7 @@ def make_options(prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=
     o.leaf_rows = int(leaf_rows)
     o.reorth = int(reorth)
     o.panel_leaf = PANEL_LEAF[panel_leaf] if isinstance(panel_leaf, str) else int(panel_leaf)
+    o.x0 = X0[x0] if isinstance(x0, str) else int(x0)
     return o
 
 
@@ -358,21 +360,27 @@ def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=
 
 
 def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0,
-          krylov="cgls", want_r=False, ws=None, stream=None, check=True, reorth=0, panel_leaf="cgs2"):
+          krylov="cgls", want_r=False, ws=None, stream=None, check=True, reorth=0, panel_leaf="cgs2",
+          x0=None):
     """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
 
+    x0: None (start from zero), "direct" (start from R^{-1} Q^T b) or a vector (warm start).
     Returns (x, info_dict[, R]). Synchronizes the stream (to fill info)."""
     torch = _torch()
     _check_colmajor(A)
     m, n = A.shape
+    mode = "zero" if x0 is None else ("direct" if isinstance(x0, str) and x0 == "direct" else "given")
     o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter,
-                     panel_width=panel_width, krylov=krylov, reorth=reorth, panel_leaf=panel_leaf)
+                     panel_width=panel_width, krylov=krylov, reorth=reorth, panel_leaf=panel_leaf, x0=mode)
     nb = lls_solve_workspace_size(m, n, o)
     if nb == 0:
         raise LLSError(-1, "lls_solve_workspace_size")
     ws = ws if ws is not None and ws.numel() >= nb else workspace(nb, A.device)
     b = b.to(device=A.device, dtype=torch.float64).contiguous()
-    x = torch.empty(n, dtype=torch.float64, device=A.device)
+    if mode == "given":
+        x = torch.as_tensor(x0).to(device=A.device, dtype=torch.float64).clone().contiguous()
+    else:
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
     R = torch.empty((n, n), dtype=torch.float32, device=A.device).t() if want_r else None
     info = lls_info()
     st = lls_solve(m, n, A.data_ptr(), A.stride(1), b.data_ptr(), x.data_ptr(),

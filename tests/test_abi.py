@@ -111,3 +111,18 @@ def test_upload_chunks_argument_errors(lib):
     assert lib.lls_upload_chunks(0, buf, 64) == -1
     assert lib.lls_upload_chunks(4096, None, 64) == -1
     assert lib.lls_upload_chunks(4096, buf, 3) == -1          # 7 chunks need 8 entries
+
+
+def test_x0_option(lib):
+    # the starting point of the Krylov iteration: 0 zero (default), 1 the caller's x, 2 the
+    # direct solve R^{-1} Q^T b; other values are argument errors, and the batched solver takes
+    # the zero start only
+    assert lls.lls_default_options().x0 == 0
+    for mode in ("zero", "given", "direct"):
+        assert lls.lls_solve_workspace_size(1000, 64, lls.make_options(x0=mode)) > 0
+    assert lls.lls_solve_workspace_size(1000, 64, lls.make_options(x0=3)) == 0
+    assert lls.lls_solve_workspace_size(1000, 64, lls.make_options(x0=-1)) == 0
+    assert lls.lls_solve_batched_workspace_size(1, [256], [16], lls.make_options(x0=3)) == 0
+    info = lls.lls_info()
+    assert lls.lls_solve(1000, 64, 256, 1000, 256, 256, None, 0, 256, 1 << 30, lls.make_options(x0=5), info,
+                         None) == -1

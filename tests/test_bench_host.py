@@ -64,3 +64,15 @@ def test_sampler_without_the_tool(tmp_path, monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_ncu_traffic_only_for_the_captured_source(monkeypatch):
+    # a recorded capture counts only while the kernel's source file hashes as it did then
+    src = "panel_flat.cu"
+    digest = bench.source_digest(src)
+    assert digest is not None and len(digest) == 16
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, src, digest))
+    assert bench.ncu_traffic("probe") == 1234
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, src, "0" * 16))
+    assert bench.ncu_traffic("probe") is None
+    assert bench.ncu_traffic("no such kernel") is None

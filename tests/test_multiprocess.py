@@ -54,7 +54,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     port = free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"]
+           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1", "--rows", "2048", "--cols", "256"]
     env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -64,3 +64,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # full solves of the requested problem, no scaling: the steps timed are the steps asked for
+    assert d["steps"] == 2 and len(d["steps_ms"]) == 2
+    assert d["config"]["m"] == 2048 and d["config"]["n"] == 256
+    assert "scaled" not in json.dumps(d)
