@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-householder", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workload configurations (small solve, spectrum sweep, large QR, "
+                         "batched, differentiable)")
     return ap.parse_args()
 
 
@@ -380,6 +383,312 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
     return out
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def cfg_small_latency(stream, dev):
+    """The paper's plain method at 1024 x 128 (geometric spectrum 1 .. 1e-3, seed 1): FP16
+    products, LSQR to the FP32 target. A latency figure: the device time per solve of 50
+    back-to-back asynchronous calls (graph replays), and the wall time of a call that also
+    fills info (one host round trip), against the plain FP64 Householder solve."""
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+    p = synth.svd_lls(1024, 128, "geometric", 1e3, seed=1)
+    A = lls.colmajor(p.A, device=dev)
+    b = torch.from_numpy(p.b).to(dev)
+    m, n = A.shape
+    o = lls.make_options(prec="fp16", target="fp32", krylov="lsqr")
+    ws = lls.workspace(lls.lls_solve_workspace_size(m, n, o), dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    sh = stream.cuda_stream
+    info = lls.lls_info()
+
+    def solve(inf):
+        st = lls.lls_solve(m, n, A.data_ptr(), m, b.data_ptr(), x.data_ptr(), None, n, ws.data_ptr(), ws.numel(),
+                           o, inf, sh)
+        assert st >= 0, st
+    for _ in range(5):
+        solve(None)
+    solve(info)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(50):
+        solve(None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / 50 * 1e3
+    t0 = time.perf_counter()
+    for _ in range(20):
+        solve(info)
+    wall_us = (time.perf_counter() - t0) / 20 * 1e6
+    xh = lls.householder_solve(A, b, prec="fp64", stream=sh)
+    hws = lls.workspace(lls.lls_householder_workspace_size(m, n, lls.PREC["fp64"]), dev)
+
+    def hh():
+        assert lls.lls_householder_solve(m, n, lls.PREC["fp64"], A.data_ptr(), m, b.data_ptr(), xh.data_ptr(),
+                                         hws.data_ptr(), hws.numel(), sh) == 0
+    hh()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        hh()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hh_us = e0.elapsed_time(e1) / 10 * 1e3
+    solve(info)
+    torch.cuda.synchronize()
+    fwd = float(torch.linalg.norm(x - xh) / torch.linalg.norm(xh))
+    return {"workload": "single LLS 1024x128 FP32, geometric kappa=1e3 (seed 1), FP16 products, LSQR to the "
+                        "FP32 target", "us_per_solve": us, "us_per_solve_with_info": wall_us,
+            "iters": info.iters, "status": info.status, "fwd_vs_householder_fp64": fwd,
+            "householder_fp64_us": hh_us, "bound": "latency (about 2.3e5 flops of Krylov work per iteration)"}
+
+
+def cfg_spectrum_sweep(stream, dev, A0, b0, with_householder=True):
+    """32768 x 4096 with three spectra (arithmetic, geometric, cluster) x kappa in {1e1, 1e3,
+    1e6} (seeds 2..10, the geometric kappa = 1e3 problem being the headline's) and FP16, BF16
+    and scaled FP8 products, each refined by CGLS to the FP64 target (eta_est <= 1e-12, at
+    most 200 iterations). Per solve: status, iterations, eta and the device time to solution
+    (the solve's own phase events, QR + Krylov), after one untimed solve; per matrix the
+    relative distance of the FP16 solution from the plain FP64 Householder solution."""
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+    m, n = A0.shape
+    sh = stream.cuda_stream
+    seeds = {}
+    k = 2
+    for kind in ("geometric", "arithmetic", "cluster"):
+        for kappa in (1e1, 1e3, 1e6):
+            if (kind, kappa) == ("geometric", 1e3):
+                seeds[(kind, kappa)] = 2
+            else:
+                k += 1
+                seeds[(kind, kappa)] = k
+    size = max(lls.lls_solve_workspace_size(m, n, lls.make_options(prec=p)) for p in ("fp16", "bf16", "fp8"))
+    ws = lls.workspace(size, dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    rows = []
+    for (kind, kappa), seed in seeds.items():
+        if seed == 2:
+            A, b = A0, b0
+        else:
+            A, b, _ = synth.svd_lls_torch(m, n, kind, kappa, seed=seed, device=dev)
+        xh = lls.householder_solve(A, b, prec="fp64", stream=sh) if with_householder else None
+        for prec in ("fp16", "bf16", "fp8"):
+            o = lls.make_options(prec=prec, target="fp64")
+            info = lls.lls_info()
+            for _ in range(2):
+                st = lls.lls_solve(m, n, A.data_ptr(), A.stride(1), b.data_ptr(), x.data_ptr(), None, n,
+                                   ws.data_ptr(), ws.numel(), o, info, sh)
+            row = {"spectrum": kind, "kappa": kappa, "seed": seed, "prec": prec, "status": int(st),
+                   "converged": st == 0, "iters": info.iters, "eta": info.eta,
+                   "ms": info.qr_ms + info.krylov_ms, "qr_ms": info.qr_ms, "krylov_ms": info.krylov_ms}
+            if xh is not None and st >= 0:
+                row["fwd_vs_householder_fp64"] = float(torch.linalg.norm(x - xh) / torch.linalg.norm(xh))
+            rows.append(row)
+        if seed != 2:
+            del A, b
+        torch.cuda.empty_cache()
+    return {"workload": f"single LLS {m}x{n} FP32, spectra x kappa, FP16/BF16/FP8 products, CGLS to the FP64 "
+                        f"target (1e-12), 200 iterations at most",
+            "time_to_solution": "ms = device time of the whole solve (QR + preconditioner + Krylov) when "
+                                "converged; not converged rows report the capped run",
+            "rows": rows}
+
+
+def cfg_large_qr(stream, dev, tc_peak):
+    """QR only (RGSQRF, FP16 products) of Gaussian matrices with column norms 10^U(-2, 2):
+    262144 x 8192 (seed 11) and 16384 x 16384 (seed 12). The time is the mean of three
+    asynchronous factorizations (graph replays) after one untimed; TFLOP/s is given
+    Householder-equivalent, (2 m n^2 - 2/3 n^3) / t, and as executed by the recursion,
+    2 m n^2 / t. The column-equilibrated backward error ||(A - QR) D^-1||_F / ||A D^-1||_F and
+    the orthogonality ||I - Q^T Q||_F / sqrt(n) are computed with FP32 products (TF32 off)."""
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+    torch.backends.cuda.matmul.allow_tf32 = False
+    sh = stream.cuda_stream
+    out = []
+    for m, n, seed in ((262144, 8192, 11), (16384, 16384, 12)):
+        A = synth.scaled_gaussian_torch(m, n, seed=seed, device=dev)
+        o = lls.make_options(prec="fp16")
+        ws = lls.workspace(lls.qr_factor_workspace_size(m, n, o), dev)
+        R = torch.empty((n, n), dtype=torch.float32, device=dev).t()
+
+        def qr(Qp=None):
+            st = lls.qr_factor(m, n, A.data_ptr(), m, Qp, m, R.data_ptr(), n, ws.data_ptr(), ws.numel(), o, sh)
+            assert st == 0, st
+        qr()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(stream)
+        for _ in range(3):
+            qr()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        Q = torch.empty((n, m), dtype=torch.float32, device=dev).t()
+        qr(Q.data_ptr())
+        torch.cuda.synchronize()
+        d = torch.linalg.norm(A, dim=0)
+        E = torch.addmm(A, Q, R, beta=1.0, alpha=-1.0)
+        berr = float(torch.linalg.norm(E / d) / torch.linalg.norm(A / d))
+        del E
+        G = Q.t() @ Q
+        G.diagonal().sub_(1.0)
+        orth = float(torch.linalg.norm(G)) / n ** 0.5
+        del G, Q
+        hh = qr_flops(m, n) / (ms * 1e-3) / 1e12
+        ex = 2.0 * m * n * n / (ms * 1e-3) / 1e12
+        out.append({"m": m, "n": n, "seed": seed, "prec": "fp16", "ms": ms, "qr_tflops_householder_equiv": hh,
+                    "qr_tflops_executed": ex, "executed_frac_of_tensor_peak": ex / tc_peak,
+                    "backward_error_col_equilibrated": berr, "orthogonality_fro_over_sqrt_n": orth})
+        del A, R, ws
+        torch.cuda.empty_cache()
+    return {"workload": "QR only, Gaussian with column norms 10^U(-2,2), FP16 products", "rows": out}
+
+
+def cfg_batched(stream, dev, hbm_peak):
+    """4096 uneven problems (m ~ U[256, 4096], n ~ U[16, 512], m >= 4 n, geometric spectra with
+    kappa = 10^U(1, 5), seed 13), FP16 products, FP32 target: one lls_solve_batched call (a
+    single persistent launch, replayed as a CUDA graph), mean of three after one untimed,
+    against the same problems solved one after another by lls_solve on the default stream
+    (launched directly). Roofline: the batch's algorithmic bytes are taken as one read and one
+    write of every A for the factorization plus two reads of A per Krylov iteration."""
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+    As, bs, kap = synth.batched_problems_torch(4096, seed=13, device=dev)
+    batch = len(As)
+    ms_ = [a.shape[0] for a in As]
+    ns_ = [a.shape[1] for a in As]
+    o = lls.make_options(prec="fp16", target="fp32", panel_width=16)
+    nb = lls.lls_solve_batched_workspace_size(batch, ms_, ns_, o)
+    ws = lls.workspace(nb, dev)
+    xs = [torch.empty(n_, dtype=torch.float64, device=dev) for n_ in ns_]
+    sh = stream.cuda_stream
+    infos = (lls.lls_info * batch)()
+    args = (batch, ms_, ns_, [a.data_ptr() for a in As], ms_, [b.data_ptr() for b in bs],
+            [x.data_ptr() for x in xs], None, None, ws.data_ptr(), ws.numel(), o)
+    worst = lls.lls_solve_batched(*args, infos, sh)
+    st = [infos[i].status for i in range(batch)]
+    iters = [infos[i].iters for i in range(batch)]
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(3):
+        assert lls.lls_solve_batched(*args, None, sh) >= 0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / 3
+    # the same problems one lls_solve call each, launched directly on the default stream
+    so = lls.make_options(prec="fp16", target="fp32")
+    sws = lls.workspace(max(lls.lls_solve_workspace_size(a, b_, so) for a, b_ in zip(ms_, ns_)), dev)
+    xo = torch.empty(max(ns_), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(batch):
+        lls.lls_solve(ms_[i], ns_[i], As[i].data_ptr(), ms_[i], bs[i].data_ptr(), xo.data_ptr(), None, ns_[i],
+                      sws.data_ptr(), sws.numel(), so, None, 0)
+    torch.cuda.synchronize()
+    ms_loop = (time.perf_counter() - t0) * 1e3
+    by = sum(4.0 * m_ * n_ * (2 + 2 * it) for m_, n_, it in zip(ms_, ns_, iters))
+    gbs = by / (ms_batch * 1e-3) / 1e9
+    out = {"workload": "4096 uneven LLS (m in [256,4096], n in [16,512], m >= 4n, geometric kappa=10^U(1,5)), "
+                       "FP16 products, FP32 target", "ms_one_launch": ms_batch, "ms_loop_of_single_solves": ms_loop,
+           "speedup_vs_loop": ms_loop / ms_batch, "worst_status": int(worst),
+           "converged": sum(1 for v in st if v == 0), "not_converged": sum(1 for v in st if v == 1),
+           "errors": sum(1 for v in st if v < 0), "mean_iters": statistics.mean(iters),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "algorithmic_bytes": by}}
+    del As, bs, xs, ws, sws
+    torch.cuda.empty_cache()
+    return out
+
+
+def cfg_differentiable(stream, dev, hbm_peak):
+    """256 problems of 4096 x 256 (geometric kappa = 1e3, seeds 1400..1655), L = sum of x^2:
+    the forward solve (lls_solve_batched, FP64 target, R kept) and the adjoint (lls_backward:
+    z = (A^T A)^-1 2x by CG preconditioned with the forward R, then dL/db = A z and the rank-2
+    dL/dA). Times are the mean of three calls after one untimed. The adjoint's roofline counts
+    its output write (dL/dA, 4 m n bytes per problem) and two reads of A per CG iteration
+    plus three for the gradient sweep."""
+    import torch
+    from paper_1912_05508_gb300 import lls, synth
+    As, bs = [], []
+    for i in range(256):
+        A, b, _ = synth.svd_lls_torch(4096, 256, "geometric", 1e3, seed=1400 + i, device=dev)
+        As.append(A)
+        bs.append(b)
+    batch = 256
+    m, n = 4096, 256
+    sh = stream.cuda_stream
+    o = lls.make_options(prec="fp16", target="fp64", panel_width=16)
+    ws = lls.workspace(lls.lls_solve_batched_workspace_size(batch, [m] * batch, [n] * batch, o), dev)
+    xs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(batch)]
+    Rs = [torch.empty((n, n), dtype=torch.float32, device=dev).t() for _ in range(batch)]
+    fargs = (batch, [m] * batch, [n] * batch, [a.data_ptr() for a in As], [m] * batch, [b.data_ptr() for b in bs],
+             [x.data_ptr() for x in xs], [r.data_ptr() for r in Rs], [n] * batch, ws.data_ptr(), ws.numel(), o)
+    infos = (lls.lls_info * batch)()
+    assert lls.lls_solve_batched(*fargs, infos, sh) == 0
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(3):
+        assert lls.lls_solve_batched(*fargs, None, sh) >= 0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 3
+    gxs = [2.0 * x for x in xs]
+    gAs = [torch.empty((n, m), dtype=torch.float32, device=dev).t() for _ in range(batch)]
+    gbs = [torch.empty(m, dtype=torch.float64, device=dev) for _ in range(batch)]
+    bo = lls.make_options(prec="fp16", target="fp64")
+    bws = lls.workspace(lls.lls_backward_workspace_size(batch, [m] * batch, [n] * batch, bo), dev)
+    bargs = (batch, [m] * batch, [n] * batch, [a.data_ptr() for a in As], [m] * batch, [b.data_ptr() for b in bs],
+             [x.data_ptr() for x in xs], [r.data_ptr() for r in Rs], [n] * batch, [g.data_ptr() for g in gxs],
+             [g.data_ptr() for g in gAs], [m] * batch, [g.data_ptr() for g in gbs], bws.data_ptr(), bws.numel(), bo, sh)
+    assert lls.lls_backward(*bargs) == 0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        assert lls.lls_backward(*bargs) == 0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bwd_ms = e0.elapsed_time(e1) / 3
+    by = batch * 4.0 * m * n * 4     # grad write + reads of A in the gradient sweep (lower bound)
+    gbs_ = by / (bwd_ms * 1e-3) / 1e9
+    out = {"workload": "256 x (4096x256) LLS, geometric kappa=1e3, L = sum x^2, forward FP64 target + adjoint",
+           "forward_ms": fwd_ms, "backward_ms": bwd_ms, "total_ms": fwd_ms + bwd_ms,
+           "forward_iters_mean": statistics.mean(infos[i].iters for i in range(batch)),
+           "backward_roofline": {"bound": "hbm", "achieved": gbs_, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs_ / hbm_peak, "algorithmic_bytes_lower_bound": by}}
+    del As, bs, xs, Rs, gAs, gbs, ws, bws
+    torch.cuda.empty_cache()
+    return out
+
+
+def other_configs(args, stream, dev, A, b, hbm_peak, tc_peak):
+    """Every workload configuration besides the headline, each timed on its own; a failure is
+    reported in its entry instead of ending the benchmark."""
+    import torch
+    out = {}
+    for key, fn in (("small_1024x128", lambda: cfg_small_latency(stream, dev)),
+                    ("spectrum_sweep_32768x4096", lambda: cfg_spectrum_sweep(stream, dev, A, b,
+                                                                             not args.no_householder)),
+                    ("large_qr", lambda: cfg_large_qr(stream, dev, tc_peak)),
+                    ("batched_4096", lambda: cfg_batched(stream, dev, hbm_peak)),
+                    ("differentiable_256x4096x256", lambda: cfg_differentiable(stream, dev, hbm_peak))):
+        t0 = time.perf_counter()
+        try:
+            out[key] = fn()
+        except Exception as exc:  # noqa: BLE001 - reported in the line
+            out[key] = {"error": f"{type(exc).__name__}: {str(exc).splitlines()[0][:300] if str(exc) else ''}"}
+        out[key]["bench_wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+    return out
+
+
 def householder_baseline(A, b, x_ref, stream, dev, reps=2):
     """The plain Householder solve (Alg. 1) in FP64 and FP32 on the same GPU and inputs:
     device time per solve (CUDA events, after one warm-up) and its distance from our x."""
@@ -613,6 +922,8 @@ def main():
            "speedup_vs_householder_fp64": (hh["fp64"]["ms"] / ms) if hh else None,
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
            "clocks": clocks}
+    if ws == 1 and not args.no_configs:
+        out["configs"] = other_configs(args, stream, dev, A, b, hbm_peak, tc_peak)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, b, m, n)
     if rank == 0:

@@ -198,3 +198,33 @@ def svd_lls_torch(m: int, n: int, kind: str = "geometric", kappa: float = 1e3, s
     del A64
     torch.cuda.empty_cache()
     return A, b, x
+
+
+def scaled_gaussian_torch(m: int, n: int, seed: int = 11, lo: float = -2.0, hi: float = 2.0, device="cuda"):
+    """Device-side ``scaled_gaussian``: N(0, 1) entries with column j scaled to norm 10**U(lo, hi),
+    as an (m, n) column-major FP32 tensor, generated 1024 columns at a time."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = torch.empty((n, m), dtype=torch.float32, device=device).t()
+    expo = torch.empty(n, dtype=torch.float64, device=device).uniform_(lo, hi, generator=g)
+    for j0 in range(0, n, 1024):
+        j1 = min(n, j0 + 1024)
+        blk = torch.randn((j1 - j0, m), generator=g, dtype=torch.float32, device=device)
+        scale = (10.0 ** expo[j0:j1]) / torch.linalg.norm(blk.double(), dim=1)
+        A[:, j0:j1] = (blk.double() * scale[:, None]).float().t()
+    return A
+
+
+def batched_problems_torch(count: int = 4096, seed: int = 13, m_range=(256, 4096), n_range=(16, 512),
+                           kappa_exp=(1.0, 5.0), device="cuda"):
+    """The uneven batch on the device: shapes from ``batched_shapes``, problem i an SVD problem
+    (``svd_lls_torch``, geometric spectrum with its kappa, seed seed * 10007 + i).
+    Returns (As, bs, kappas)."""
+    ms, ns, kap = batched_shapes(count, seed=seed, m_range=m_range, n_range=n_range, kappa_exp=kappa_exp)
+    As, bs = [], []
+    for i, (m, n, k) in enumerate(zip(ms, ns, kap)):
+        A, b, _ = svd_lls_torch(int(m), int(n), "geometric", float(k), seed=seed * 10007 + i, device=device)
+        As.append(A)
+        bs.append(b)
+    return As, bs, kap

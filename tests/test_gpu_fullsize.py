@@ -100,17 +100,7 @@ def test_spectrum_sweep_kappa_1e6_reports_honestly(kind):
 
 
 def scaled_gaussian_device(m, n, seed, lo=-2.0, hi=2.0):
-    """Gaussian entries with column j scaled to norm 10^U(lo, hi), on the device (FP32)."""
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
-    A = torch.empty((n, m), dtype=torch.float32, device="cuda").t()
-    expo = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(lo, hi, generator=g)
-    for j0 in range(0, n, 1024):
-        j1 = min(n, j0 + 1024)
-        blk = torch.randn((j1 - j0, m), generator=g, dtype=torch.float32, device="cuda")
-        scale = (10.0 ** expo[j0:j1]) / torch.linalg.norm(blk.double(), dim=1)
-        A[:, j0:j1] = (blk.double() * scale[:, None]).float().t()
-    return A
+    return synth.scaled_gaussian_torch(m, n, seed=seed, lo=lo, hi=hi)
 
 
 @pytest.mark.parametrize("m,n,check_orth", [(262144, 8192, True), (16384, 16384, False)])
@@ -142,14 +132,7 @@ def test_large_qr_backward_error(m, n, check_orth):
 
 
 def batch_on_device(count, seed, m_range, n_range, kappa_exp):
-    ms, ns, kap = synth.batched_shapes(count, seed=seed, m_range=m_range, n_range=n_range,
-                                       kappa_exp=kappa_exp)
-    As, bs = [], []
-    for i, (m, n, k) in enumerate(zip(ms, ns, kap)):
-        A, b, _ = synth.svd_lls_torch(int(m), int(n), "geometric", float(k), seed=seed * 10007 + i)
-        As.append(A)
-        bs.append(b)
-    return As, bs, kap
+    return synth.batched_problems_torch(count, seed=seed, m_range=m_range, n_range=n_range, kappa_exp=kappa_exp)
 
 
 def test_batched_uneven_4096_problems_one_launch():
