@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace lls {
 
@@ -50,116 +51,6 @@ struct TcArgs {
     const int* fexp;     // UPDATE: column exponents of R12l
     int* err;
 };
-
-// ---- PTX wrappers ----------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false (and the error word set) if the phase does not complete in time or
-// another thread already flagged an error.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        for (int i = 0; i < 64; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (*(volatile int*)err != DEV_OK) return false;
-        if (globaltimer_ns() - t0 > kSpinLimitNs) {
-            atomicCAS(err, DEV_OK, DEV_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
-// kind::f8f6f4 with E4M3 operands (format code 0 for A and B in the instruction descriptor):
-// K = 32 elements = 32 bytes per instruction, the same byte footprint as 16 FP16 elements.
-__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4 in [0,14), LBO >> 4 in [16,30),
-// SBO >> 4 in [32,46), fixed 0b01 in [46,48), base offset 0, layout type in [61,64)
-// (2 = 128-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
 
 template <int BN, bool A_MN, int EPI, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -352,27 +243,30 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D tensor map over a column-major matrix: `inner` contiguous elements per column,
-// `outer` columns `ld` elements apart, boxes of box_inner x box_outer, 128-byte swizzle.
-static int make_tmap(CUtensorMap* tm, const void* base, int lowp, uint64_t inner, uint64_t outer, uint64_t ld,
-                     uint32_t box_inner, uint32_t box_outer) {
+int tc_make_tmap(CUtensorMap* tm, const void* base, CUtensorMapDataType dt, uint64_t esz, uint64_t inner,
+                 uint64_t outer, uint64_t ld, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return LLS_ERR_CUDA;
-    const uint64_t esz = lowp == 2 ? 1 : 2;
     if (((uintptr_t)base & 15) != 0 || ((ld * esz) & 15) != 0) return LLS_ERR_UNSUPPORTED;
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {ld * esz};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    const CUtensorMapDataType dt = lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                   : (lowp == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
-    CUresult r = fn(tm, dt, 2,
-                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? LLS_OK : LLS_ERR_CUDA;
 }
 
-static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
+// 2-D tensor map over a column-major low-precision matrix with the 128-byte swizzle.
+static int make_tmap(CUtensorMap* tm, const void* base, int lowp, uint64_t inner, uint64_t outer, uint64_t ld,
+                     uint32_t box_inner, uint32_t box_outer) {
+    const CUtensorMapDataType dt = lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : (lowp == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+    return tc_make_tmap(tm, base, dt, lowp == 2 ? 1 : 2, inner, outer, ld, box_inner, box_outer,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+uint32_t tc_make_idesc(int lowp, int bn, bool a_mn) {
     const uint32_t fmt = lowp == 1 ? 1u : 0u;       // kind::f16: 0 = F16, 1 = BF16; kind::f8f6f4: 0 = E4M3
     uint32_t d = 0;
     d |= 1u << 4;                                    // D = F32
@@ -383,6 +277,8 @@ static uint32_t make_idesc(int lowp, int bn, bool a_mn) {
     d |= (uint32_t)(kTcBM >> 4) << 24;               // M / 16
     return d;
 }
+
+static uint32_t make_idesc(int lowp, int bn, bool a_mn) { return tc_make_idesc(lowp, bn, a_mn); }
 
 static int pick_bn(int n) { return n <= 64 ? 64 : 128; }
 
@@ -429,13 +325,24 @@ static void proj_split(int m, int w1, int w2, int& splits, int& ktps, int lowp =
     splits = ceil_div(kt, ktps);
 }
 
+void proj_split_persistent(int m, int w1, int w2, int& splits, int& ktps);
+bool projection_persistent_applies(int lowp, int w1, int w2);
+int gemm_projection_persistent(const ProjCall& c, cudaStream_t st);
+int gemm_update_persistent(const UpdCall& c, cudaStream_t st);
+
+// Partial sums of the projection: room for either kernel's K split.
 size_t proj_partial_floats(int m, int w1, int w2) {
-    int splits, ktps;
+    int splits, ktps, ps, pk;
     proj_split(m, w1, w2, splits, ktps);
-    return (size_t)splits * w1 * w2;
+    proj_split_persistent(m, w1, w2, ps, pk);
+    return (size_t)(splits > ps ? splits : ps) * w1 * w2;
 }
 
 int gemm_projection(const ProjCall& c, cudaStream_t st) {
+    if (projection_persistent_applies(c.lowp, c.w1, c.w2)) {
+        const int r = gemm_projection_persistent(c, st);
+        if (r != LLS_ERR_UNSUPPORTED) return r;
+    }
     int splits, ktps;
     proj_split(c.m, c.w1, c.w2, splits, ktps, c.lowp);
     if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
@@ -455,6 +362,10 @@ int gemm_projection(const ProjCall& c, cudaStream_t st) {
 }
 
 int gemm_update(const UpdCall& c, cudaStream_t st) {
+    {
+        const int r = gemm_update_persistent(c, st);
+        if (r != LLS_ERR_UNSUPPORTED) return r;
+    }
     const int bn = c.w2 <= 64 ? 64 : 128;
     if (c.lowp == 2) {
         // FP8: A = Q1 row-major (K-major, rows of ldq bytes), B = R12l (K-major)

@@ -31,7 +31,9 @@ def lowp_colmajor(X, prec, ld=None):
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("m,w1,w2", [(1000, 32, 32), (4096, 128, 128), (2049, 96, 200),
-                                     (300, 512, 300), (8192, 256, 520), (32768, 64, 64)])
+                                     (300, 512, 300), (8192, 256, 520), (32768, 64, 64),
+                                     # persistent kernel: ragged M and N tiles; several units per CTA
+                                     (3000, 200, 136), (4096, 2048, 2048)])
 def test_projection(prec, m, w1, w2):
     rng = np.random.default_rng(m + w1 + w2)
     Q = rng.standard_normal((m, w1)) / np.sqrt(m)
@@ -73,7 +75,10 @@ def test_projection(prec, m, w1, w2):
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("m,w1,w2", [(1000, 32, 32), (4096, 128, 128), (2049, 96, 200),
-                                     (300, 64, 300), (8192, 256, 520), (777, 512, 64)])
+                                     (300, 64, 300), (8192, 256, 520), (777, 512, 64),
+                                     # persistent kernel: ragged rows and a ragged K tile; several
+                                     # tiles per CTA, so both accumulators and the A2 chunk ring wrap
+                                     (2052, 96, 200), (4096, 512, 1024)])
 def test_update(prec, m, w1, w2):
     rng = np.random.default_rng(7 * m + w1 + w2)
     Q = rng.standard_normal((m, w1)) / np.sqrt(m)
