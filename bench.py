@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--pw", type=int, default=0, help="panel width (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-householder", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (the library's default settings, or the ones cached)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workload configurations (small solve, spectrum sweep, large QR, "
                          "batched, differentiable)")
@@ -783,9 +785,17 @@ def main():
     dev = torch.device("cuda", local)
     m, n = args.m, args.n
     A, b = make_inputs(args, m, n, rank, dev)
+    # the autotuner measures the implementation choices for this shape once (cached on disk);
+    # with panel_width 0 the solves below use its setting
+    tune = None
+    if not args.no_autotune and args.pw == 0:
+        t0 = time.perf_counter()
+        tune = lls.autotune(A, b, prec=args.prec, target=args.target, krylov=args.krylov, reorth=args.reorth,
+                            reps=2)
+        tune["wall_s"] = round(time.perf_counter() - t0, 2)
     o = lls.make_options(prec=args.prec, target=args.target, panel_width=args.pw, krylov=args.krylov,
                          reorth=args.reorth)
-    pw = args.pw if args.pw > 0 else lls.default_options().panel_width
+    pw = args.pw if args.pw > 0 else (tune["panel_width"] if tune else 16)
     nb = lls.lls_solve_workspace_size(m, n, o)
     wsbuf = lls.workspace(nb, dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
@@ -905,6 +915,7 @@ def main():
                       "m": m, "n": n, "prec": args.prec, "target": args.target, "krylov": args.krylov,
                       "reorth": args.reorth,
                       "panel_width": pw,
+                      "autotuned": tune,
                       "l2": "inputs larger than L2 (A is %d MiB)" % (m * n * 4 >> 20),
                       "parallelism": f"replicas x{ws}"},
            "qr_ms": qr_ms, "qr_tflops": qr_flops(m, n) / (qr_ms * 1e-3) / 1e12,

@@ -72,7 +72,9 @@ typedef struct {
                           FP64: eta_est = ||R^-T A^T r|| / (||A||_F ||x||) <= 1e-12
                           FP32: fwd_est = ||R^-1||_F ||R^-T A^T r|| / ||x|| <= 1e-6 */
     int max_iter;      /* iteration cap, default 200 (the paper's cap, Sec. 4.2.3) */
-    int panel_width;   /* recursion leaf width b (columns per panel), 0 = default 16 (the paper uses 32, Sec. 3.1.3); 1..32 */
+    int panel_width;   /* recursion leaf width b (columns per panel), 1..32; 0 = auto: the setting
+                          recorded by lls_autotune for the shape, else 16 (the paper uses 32,
+                          Sec. 3.1.3) */
     int krylov;        /* lls_krylov, default CGLS */
     int leaf_rows;     /* reserved, 0 or 256 (the GPU panel's CAQR row blocks are 1024 rows, Sec. 3.1.3) */
     int reorth;        /* 1: re-orthogonalize (Sec. 4.2.1): factor Q once more, Q1 = Q2 R2, and return
@@ -306,6 +308,62 @@ int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, f
 size_t lls_panel_block_qr_workspace_size(int m, int w1, int w2);
 int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
                        int ldr, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuning. The paper picks its panel size by hand for its GPU (Sec. 3.1.3, 256 x 32 blocks
+ * on a V100); here the implementation choices are measured per problem shape on the GPU in use
+ * and the fastest is recorded. A recorded setting is used by every later call on the same
+ * device with the same shape and the same gemm_prec, target, krylov, reorth and panel_leaf
+ * whose opts->panel_width is 0 ("auto"; a NULL opts counts as auto). Calls with an explicit
+ * panel_width use the library's defaults for the other choices. None of the choices changes the
+ * definition of the arithmetic: every kernel keeps its rounding points and summation order.
+ * The table lives in the process; lls_tuning_get / lls_tuning_set let a caller save it and
+ * restore it (the Python binding keeps a JSON cache this way).
+ *
+ * lls_tuning (one recorded setting):
+ *   panel_width          leaf width b of the recursion (8, 16 or 32);
+ *   node_mode            0: the lowest nodes with both of their panels, and the narrow nodes
+ *                        (w1 <= 32), each as one launch; 1: narrow nodes as one launch, panels
+ *                        separate; 2: every node as four launches (cast, projection, reduction,
+ *                        update);
+ *   gemm_kernel          products of the wide nodes: 0 persistent (one CTA per SM looping over
+ *                        tiles, two accumulators), 1 one output tile per CTA, 2 the persistent
+ *                        update with the one-tile-per-CTA projection;
+ *   batched_ctas_per_sm  batched solver: CTAs per SM (0 = as many as fit);
+ *   ms                   the measured device time of one call with this setting.
+ *
+ * lls_autotune: times lls_solve on the caller's problem (A m x n FP32 lda >= m, b m FP64, x n
+ *   FP64 output, all device memory) for panel widths 8 / 16 / 32, then the node launch modes,
+ *   then the product kernel (coordinate search; each candidate: one untimed call, then the
+ *   fastest of `reps`), records the fastest for (m, n, opts) and returns it in *best. opts as
+ *   for lls_solve (opts->panel_width is ignored; x0 = LLS_X0_GIVEN is rejected). ws: at least
+ *   lls_autotune_workspace_size(m, n, opts) bytes. Synchronizes `stream`. x receives the last
+ *   trial's solution.
+ * lls_autotune_batched: the same for lls_solve_batched over its CTAs per SM (1 to 4, capped by
+ *   what fits); arguments as lls_solve_batched (no R_out), the setting is recorded for the key
+ *   (kind 1, m = batch, n = the largest n_i).
+ * lls_tuning_set / lls_tuning_get: record / read the setting of a key; kind 0 = lls_solve,
+ *   lls_solve_host and qr_factor on m x n; kind 1 = lls_solve_batched (m = batch, n = the
+ *   largest n_i). get returns 1 when a setting is recorded, 0 when not. lls_tuning_clear
+ *   forgets every recorded setting.
+ * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED (no candidate ran), LLS_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+typedef struct {
+    int panel_width;
+    int node_mode;
+    int gemm_kernel;
+    int batched_ctas_per_sm;
+    float ms;
+} lls_tuning;
+size_t lls_autotune_workspace_size(int m, int n, const lls_options* opts);
+int lls_autotune(int m, int n, const float* A, int lda, const double* b, double* x, void* ws, size_t ws_bytes,
+                 const lls_options* opts, int reps, lls_tuning* best, cudaStream_t stream);
+int lls_autotune_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                         const double* const* b, double* const* x, void* ws, size_t ws_bytes,
+                         const lls_options* opts, int reps, lls_tuning* best, cudaStream_t stream);
+int lls_tuning_set(int kind, int m, int n, const lls_options* opts, const lls_tuning* t);
+int lls_tuning_get(int kind, int m, int n, const lls_options* opts, lls_tuning* t);
+void lls_tuning_clear(void);
 
 /* ---------------------------------------------------------------------------
  * lls_selftest_wait_timeout: exercises the failure path of the library's bounded device

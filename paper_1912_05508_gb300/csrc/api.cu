@@ -13,6 +13,7 @@
 #include <mutex>
 #include <string.h>
 
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -53,6 +54,58 @@ static bool valid_opts(const lls_options& o) {
     if (o.x0 < LLS_X0_ZERO || o.x0 > LLS_X0_DIRECT) return false;
     return true;
 }
+
+// ---- tuned settings: recorded by lls_autotune / lls_tuning_set, used when the caller leaves
+// panel_width at 0 ("auto") -----------------------------------------------------------------
+struct TuneKey {
+    int v[9];
+    bool operator<(const TuneKey& o) const { return memcmp(v, o.v, sizeof(v)) < 0; }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, lls_tuning> g_tune;
+
+static TuneKey tune_key(int kind, int m, int n, const lls_options& o) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    TuneKey k;
+    const int v[9] = {dev, kind, m, n, o.gemm_prec, o.target, o.krylov, o.reorth, o.panel_leaf};
+    memcpy(k.v, v, sizeof(v));
+    return k;
+}
+
+static bool tuned_lookup(int kind, int m, int n, const lls_options& o, lls_tuning& t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(kind, m, n, o));
+    if (it == g_tune.end()) return false;
+    t = it->second;
+    return true;
+}
+
+static bool auto_width(const lls_options* opts) { return !opts || opts->panel_width <= 0; }
+
+// Options and implementation choices of a call: the caller's options with defaults filled in;
+// with panel_width 0, the settings recorded for this shape if there are any.
+static void resolve_settings(const lls_options* opts, int kind, int m, int n, lls_options& o, Knobs& k) {
+    resolve(opts, o);
+    k = default_knobs();
+    if (!auto_width(opts)) return;
+    lls_tuning t;
+    if (!tuned_lookup(kind, m, n, o, t)) return;
+    if (kind == 0 && t.panel_width >= 1 && t.panel_width <= 32) {
+        lls_options c = o;
+        c.panel_width = t.panel_width;
+        if (valid_opts(c)) o.panel_width = t.panel_width;
+    }
+    if (t.node_mode >= 0 && t.node_mode <= 2) k.node_mode = t.node_mode;
+    if (t.gemm_kernel >= 0 && t.gemm_kernel <= 2) k.gemm_kernel = t.gemm_kernel;
+    if (t.batched_ctas_per_sm >= 0) k.batched_ctas = t.batched_ctas_per_sm;
+}
+
+// Panel widths an "auto" call may end up with; its workspace is sized for the largest need.
+static const int kTuneWidths[3] = {8, 16, 32};
 
 // Largest split-K partial buffer over all internal nodes of the recursion.
 static size_t max_partial(int m, int c0, int w, int pw, bool lowp) {
@@ -132,6 +185,7 @@ struct ColumnGate {
 
 struct QrCtx {
     int m, n, pw, lowp, leaf;
+    Knobs k;
     QrWs w;
     float* R; int ldr;
     cudaStream_t st;
@@ -148,21 +202,21 @@ static int gate_upto(QrCtx& c, int col_end) {
     return LLS_OK;
 }
 
-// LLS_NODE=split keeps narrow nodes on the four-kernel path, LLS_NODE=node runs them as one
-// launch each but keeps the lowest nodes' panels separate (for comparisons).
-static bool use_fused_nodes() {
-    static const bool on = [] {
+// The defaults of the implementation choices (Knobs). LLS_NODE=split keeps every node on the
+// four-kernel path, LLS_NODE=node runs narrow nodes as one launch each but keeps the lowest
+// nodes' panels separate, LLS_GEMM=cta runs the wide nodes' products one output tile per CTA
+// (all for comparisons).
+Knobs default_knobs() {
+    static const Knobs k = [] {
+        Knobs d;
         const char* v = getenv("LLS_NODE");
-        return !(v && v[0] == 's');
+        if (v && v[0] == 's') d.node_mode = 2;
+        else if (v && v[0] == 'n') d.node_mode = 1;
+        const char* g = getenv("LLS_GEMM");
+        if (g && g[0] == 'c') d.gemm_kernel = 1;
+        return d;
     }();
-    return on;
-}
-static bool use_fused_blocks() {
-    static const bool on = [] {
-        const char* v = getenv("LLS_NODE");
-        return !(v && (v[0] == 's' || v[0] == 'n'));
-    }();
-    return on;
+    return k;
 }
 
 static int qr_rec(QrCtx& c, int c0, int w) {
@@ -183,7 +237,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         return LLS_OK;
     }
     const int w1 = split_point(w, c.pw), w2 = w - w1;
-    if (w1 == c.pw && w2 <= c.pw && (c.lowp == 0 || c.lowp == 1) && c.leaf == 0 && use_fused_blocks()) {
+    if (w1 == c.pw && w2 <= c.pw && (c.lowp == 0 || c.lowp == 1) && c.leaf == 0 && c.k.node_mode == 0) {
         // both halves are panels: left panel, node and right panel in one launch
         LLS_TRY(gate_upto(c, c0 + w));
         BlockCall bc;
@@ -205,7 +259,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
     } else {
         const size_t esz = c.lowp == 2 ? 1 : 2;
         const char* Whb = (const char*)c.w.Wh;
-        if (use_fused_nodes()) {
+        if (c.k.node_mode <= 1) {
             NodeCall nc;
             nc.W = c.w.W; nc.ldw = c.w.ldw; nc.Wh = c.w.Wh; nc.ldh = c.w.ldh;
             nc.m = c.m; nc.c0 = c0; nc.w1 = w1; nc.w2 = w2; nc.lowp = c.lowp;
@@ -226,10 +280,12 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         pc.ldrl = (int)align_up((size_t)w1, c.lowp == 2 ? 16 : 8);      // 16-byte rows for TMA
         pc.sq = c.lowp == 2 ? c.w.sQ + c0 : nullptr;
         pc.part = c.w.part; pc.part_floats = c.w.part_floats; pc.lowp = c.lowp; pc.err = c.w.err;
+        pc.gemm_kernel = c.k.gemm_kernel;
         LLS_TRY(gemm_projection(pc, c.st));
         UpdCall uc;
         uc.Q1l = pc.Q1l; uc.ldh = c.w.ldh; uc.R12l = c.w.R12l; uc.ldrl = pc.ldrl; uc.f = c.w.f; uc.err = c.w.err;
         uc.A2 = A2; uc.ldw = c.w.ldw; uc.m = c.m; uc.w1 = w1; uc.w2 = w2; uc.lowp = c.lowp;
+        uc.gemm_kernel = c.k.gemm_kernel;
         if (c.lowp == 2) { uc.QT = c.w.QT + c0; uc.ldq = c.w.ldq; }
         LLS_TRY(gemm_update(uc, c.st));
     }
@@ -238,7 +294,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 
 // gate: null when A is copied into W here; otherwise W fills in chunks on another stream.
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
-                  QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr) {
+                  const Knobs& k, QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * ((size_t)n + 2), st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
@@ -246,6 +302,7 @@ static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, cons
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
     QrCtx c;
     c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec); c.leaf = o.panel_leaf;
+    c.k = k;
     c.w = w; c.R = R; c.ldr = ldr; c.st = st; c.gate = gate;
     LLS_TRY(qr_rec(c, 0, n));
     LLS_TRY(gate_upto(c, n));
@@ -283,7 +340,7 @@ void lls_default_options(lls_options* o) {
     o->target = LLS_TARGET_FP64;
     o->tol = 0.0;
     o->max_iter = 200;
-    o->panel_width = 16;
+    o->panel_width = 0;        // auto: the recorded setting for the shape, else 16
     o->krylov = LLS_KRYLOV_CGLS;
     o->leaf_rows = 256;
 }
@@ -303,26 +360,40 @@ const char* lls_status_string(int s) {
     }
 }
 
-size_t qr_factor_workspace_size(int m, int n, const lls_options* opts) {
-    lls_options o;
-    resolve(opts, o);
-    if (n < 1 || m < n || !valid_opts(o)) return 0;
+static size_t qr_ws_bytes(int m, int n, const lls_options& o) {
     WsArena ar(nullptr, SIZE_MAX);
     QrWs w;
     qr_layout(ar, m, n, o, w);
     return ar.off;
 }
 
+size_t qr_factor_workspace_size(int m, int n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    if (n < 1 || m < n || !valid_opts(o)) return 0;
+    if (!auto_width(opts)) return qr_ws_bytes(m, n, o);
+    size_t mx = 0;
+    for (int pw : kTuneWidths) {
+        lls_options c = o;
+        c.panel_width = pw;
+        if (!valid_opts(c)) continue;
+        const size_t b = qr_ws_bytes(m, n, c);
+        if (b > mx) mx = b;
+    }
+    return mx;
+}
+
 struct QrCall {
     int m, n, lda, ldq, ldr;
     const float* A; float* Q; float* R;
     lls_options o;
+    Knobs k;
     QrWs w;
 };
 
 static int enqueue_qr(void* p, cudaStream_t st, cudaEvent_t*, bool) {
     QrCall& c = *(QrCall*)p;
-    LLS_TRY(run_qr(c.m, c.n, c.A, c.lda, c.R, c.ldr, c.o, c.w, st));
+    LLS_TRY(run_qr(c.m, c.n, c.A, c.lda, c.R, c.ldr, c.o, c.k, c.w, st));
     if (c.Q) LLS_TRY(copy_matrix(c.w.W, c.w.ldw, c.Q, c.ldq, c.m, c.n, st));
     return LLS_OK;
 }
@@ -336,7 +407,8 @@ static int current_device() {
 int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
               void* ws, size_t ws_bytes, const lls_options* opts, cudaStream_t stream) {
     lls_options o;
-    resolve(opts, o);
+    Knobs k;
+    resolve_settings(opts, 0, m, n, o, k);
     if (n < 1 || m < n || lda < m || ldr < n || !A || !R || !ws) return LLS_ERR_ARG;
     if (Q && ldq < m) return LLS_ERR_ARG;
     if (!valid_opts(o)) return LLS_ERR_ARG;
@@ -345,13 +417,13 @@ int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R
     QrCall c;
     qr_layout(ar, m, n, o, c.w);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
-    c.m = m; c.n = n; c.lda = lda; c.ldq = ldq; c.ldr = ldr; c.A = A; c.Q = Q; c.R = R; c.o = o;
+    c.m = m; c.n = n; c.lda = lda; c.ldq = ldq; c.ldr = ldr; c.A = A; c.Q = Q; c.R = R; c.o = o; c.k = k;
     GraphKey key;
     memset(&key, 0, sizeof(key));
     key.op = 1; key.device = current_device();
     key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda; key.ints[3] = Q ? ldq : 0; key.ints[4] = ldr;
     key.ptrs[0] = A; key.ptrs[1] = Q; key.ptrs[2] = R; key.ptrs[3] = ws;
-    key.ws_bytes = ws_bytes; key.opts = o;
+    key.ws_bytes = ws_bytes; key.opts = o; key.knobs = k;
     trace_mark(stream);
     LLS_TRY(run_graphed(key, stream, enqueue_qr, &c, nullptr));
     trace_flush();
@@ -490,20 +562,39 @@ static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w,
     hist = ar.take<double>(kHistLen);
 }
 
-size_t lls_solve_workspace_size(int m, int n, const lls_options* opts) {
-    lls_options o;
-    resolve(opts, o);
-    if (n < 1 || m < n || !valid_opts(o)) return 0;
+static size_t solve_ws_bytes(int m, int n, const lls_options& o) {
     WsArena ar(nullptr, SIZE_MAX);
     QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb; double* hist;
     lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb, hist);
     return ar.off;
 }
 
+// The workspace of a solve: for "auto" options, enough for every panel width a tuning may pick.
+static size_t solve_ws_bytes_auto(int m, int n, const lls_options* opts, const lls_options& o) {
+    if (!auto_width(opts)) return solve_ws_bytes(m, n, o);
+    size_t mx = 0;
+    for (int pw : kTuneWidths) {
+        lls_options c = o;
+        c.panel_width = pw;
+        if (!valid_opts(c)) continue;
+        const size_t b = solve_ws_bytes(m, n, c);
+        if (b > mx) mx = b;
+    }
+    return mx;
+}
+
+size_t lls_solve_workspace_size(int m, int n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    if (n < 1 || m < n || !valid_opts(o)) return 0;
+    return solve_ws_bytes_auto(m, n, opts, o);
+}
+
 struct SolveCall {
     int m, n, lda, ldr;
     const float* A; const double* b; double* x; float* R_out;
     lls_options o;
+    Knobs k;
     QrWs w;
     float *R, *Minv, *Mt, *tmp;
     void* ks; size_t kb;
@@ -515,7 +606,7 @@ static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool captu
     const int m = c.m, n = c.n;
     if (ev) record_phase(ev[0], st, capturing);
     LLS_CUDA_TRY(cudaMemsetAsync(c.w.dinfo, 0, sizeof(double) * 16, st));
-    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.w, st, gate));
+    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.k, c.w, st, gate));
     if (c.R_out) LLS_TRY(copy_matrix(c.R, n, c.R_out, c.ldr, n, n, st));
     LLS_TRY(check_diag(c.R, n, n, c.w.err, st));
     LLS_TRY(tri_inverse(c.R, n, n, c.o.panel_width, c.Minv, c.Mt, c.tmp, c.w.err, st));
@@ -590,11 +681,10 @@ static int finish_info(const QrWs& w, cudaEvent_t* ev, lls_info* info, cudaStrea
     return st;
 }
 
-int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
-              int ldr, void* ws, size_t ws_bytes, const lls_options* opts, lls_info* info,
-              cudaStream_t stream) {
-    lls_options o;
-    resolve(opts, o);
+// lls_solve with resolved options and implementation choices (also the autotuner's trial).
+static int solve_core(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out, int ldr,
+                      void* ws, size_t ws_bytes, const lls_options& o, const Knobs& k, lls_info* info,
+                      cudaStream_t stream) {
     if (info) memset(info, 0, sizeof(*info));
     if (n < 1 || m < n || lda < m || !A || !b || !x || !ws) return LLS_ERR_ARG;
     if (R_out && ldr < n) return LLS_ERR_ARG;
@@ -605,13 +695,13 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     SolveCall c;
     lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb, c.hist);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
-    c.m = m; c.n = n; c.lda = lda; c.ldr = ldr; c.A = A; c.b = b; c.x = x; c.R_out = R_out; c.o = o;
+    c.m = m; c.n = n; c.lda = lda; c.ldr = ldr; c.A = A; c.b = b; c.x = x; c.R_out = R_out; c.o = o; c.k = k;
     GraphKey key;
     memset(&key, 0, sizeof(key));
     key.op = 2; key.device = current_device();
     key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda; key.ints[3] = R_out ? ldr : 0;
     key.ptrs[0] = A; key.ptrs[1] = b; key.ptrs[2] = x; key.ptrs[3] = R_out; key.ptrs[4] = ws;
-    key.ws_bytes = ws_bytes; key.opts = o;
+    key.ws_bytes = ws_bytes; key.opts = o; key.knobs = k;
 
     cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -629,6 +719,15 @@ int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x,
     rc = finish_info(c.w, ev, info, stream, c.hist, m, n);
     for (auto& e : own) cudaEventDestroy(e);
     return rc;
+}
+
+int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
+              int ldr, void* ws, size_t ws_bytes, const lls_options* opts, lls_info* info,
+              cudaStream_t stream) {
+    lls_options o;
+    Knobs k;
+    resolve_settings(opts, 0, m, n, o, k);
+    return solve_core(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, o, k, info, stream);
 }
 
 
@@ -739,8 +838,7 @@ size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts) {
     resolve(opts, o);
     if (n < 1 || m < n || !valid_opts(o)) return 0;
     WsArena ar(nullptr, SIZE_MAX);
-    QrWs w; float *R, *Mi, *Mt, *tmp; void* ks; size_t kb; double* hist;
-    lls_layout(ar, m, n, o, w, R, Mi, Mt, tmp, ks, kb, hist);
+    ar.off = align_up(solve_ws_bytes_auto(m, n, opts, o), 256);
     int lda; float* A; double *b, *x;
     host_layout(ar, m, n, lda, A, b, x);
     return ar.off;
@@ -749,27 +847,33 @@ size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts) {
 int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
                    size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream) {
     lls_options o;
-    resolve(opts, o);
+    Knobs k;
+    resolve_settings(opts, 0, m, n, o, k);
     if (info) memset(info, 0, sizeof(*info));
     if (n < 1 || m < n || lda < m || !A || !b || !x || !ws) return LLS_ERR_ARG;
     if (!valid_opts(o)) return LLS_ERR_ARG;
     if (!page_locked(A) || !page_locked(b) || !page_locked(x)) return LLS_ERR_ARG;
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
-    WsArena ar(ws, ws_bytes);
+    // the device solve's share of the workspace is the one an "auto" call sizes
+    const size_t solve_share = align_up(solve_ws_bytes_auto(m, n, opts, o), 256);
+    if (ws_bytes < solve_share) return LLS_ERR_WORKSPACE;
+    WsArena ar(ws, solve_share);
     HostSolveCall h;
     SolveCall& c = h.s;
     lls_layout(ar, m, n, o, c.w, c.R, c.Minv, c.Mt, c.tmp, c.ks, c.kb, c.hist);
-    int ldad; float* Ad; double *bd, *xd;
-    host_layout(ar, m, n, ldad, Ad, bd, xd);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
-    c.m = m; c.n = n; c.lda = ldad; c.ldr = 0; c.A = Ad; c.b = bd; c.x = xd; c.R_out = nullptr; c.o = o;
+    WsArena ar2((char*)ws + solve_share, ws_bytes - solve_share);
+    int ldad; float* Ad; double *bd, *xd;
+    host_layout(ar2, m, n, ldad, Ad, bd, xd);
+    if (!ar2.ok) return LLS_ERR_WORKSPACE;
+    c.m = m; c.n = n; c.lda = ldad; c.ldr = 0; c.A = Ad; c.b = bd; c.x = xd; c.R_out = nullptr; c.o = o; c.k = k;
     h.Ah = A; h.ldah = lda; h.bh = b; h.xh = x;
     GraphKey key;
     memset(&key, 0, sizeof(key));
     key.op = 4; key.device = current_device();
     key.ints[0] = m; key.ints[1] = n; key.ints[2] = lda;
     key.ptrs[0] = A; key.ptrs[1] = b; key.ptrs[2] = x; key.ptrs[3] = ws;
-    key.ws_bytes = ws_bytes; key.opts = o;
+    key.ws_bytes = ws_bytes; key.opts = o; key.knobs = k;
 
     cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -871,13 +975,13 @@ int lls_backward(int batch, const int* m, const int* n, const float* const* A, c
 // Batched solve: many independent problems, one persistent launch (batched.cu).
 // ---------------------------------------------------------------------------------------
 struct BatchExec {
-    int batch; const int* m; const int* n; void* ws; lls_options o;
+    int batch; const int* m; const int* n; void* ws; lls_options o; Knobs k;
 };
 
 static int enqueue_batched(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
     BatchExec& c = *(BatchExec*)p;
     if (ev) record_phase(ev[0], st, capturing);
-    LLS_TRY(batched_execute(c.batch, c.m, c.n, c.ws, c.o, st));
+    LLS_TRY(batched_execute(c.batch, c.m, c.n, c.ws, c.o, c.k.batched_ctas, st));
     if (ev) { record_phase(ev[1], st, capturing); record_phase(ev[2], st, capturing); }
     return LLS_OK;
 }
@@ -892,12 +996,10 @@ size_t lls_solve_batched_workspace_size(int batch, const int* m, const int* n, c
     return batched_workspace_bytes(batch, m, n);
 }
 
-int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
-                      const double* const* b, double* const* x, float* const* R_out, const int* ldr,
-                      void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
-                      cudaStream_t stream) {
-    lls_options o;
-    resolve(opts, o);
+static int batched_core(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                        const double* const* b, double* const* x, float* const* R_out, const int* ldr,
+                        void* ws, size_t ws_bytes, const lls_options& o, const Knobs& k, lls_info* infos,
+                        cudaStream_t stream) {
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return LLS_ERR_ARG;
     if (o.krylov != LLS_KRYLOV_CGLS || o.gemm_prec == LLS_PREC_FP32 || o.gemm_prec == LLS_PREC_FP8 || o.reorth ||
@@ -914,13 +1016,13 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
     trace_mark(stream);
     LLS_TRY(batched_upload(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, stream));
     BatchExec c;
-    c.batch = batch; c.m = m; c.n = n; c.ws = ws; c.o = o;
+    c.batch = batch; c.m = m; c.n = n; c.ws = ws; c.o = o; c.k = k;
     GraphKey key;
     memset(&key, 0, sizeof(key));
     key.op = 3; key.device = current_device();
     key.ints[0] = batch;
     key.ptrs[0] = ws;
-    key.ws_bytes = ws_bytes; key.opts = o;
+    key.ws_bytes = ws_bytes; key.opts = o; key.knobs = k;
     cudaEvent_t own[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (infos) {
@@ -953,6 +1055,161 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
         else if (f.status > 0 && worst == LLS_OK) worst = f.status;
     }
     return worst;
+}
+
+static int batch_nmax(int batch, const int* n) {
+    int mx = 0;
+    for (int i = 0; n && i < batch; ++i) mx = n[i] > mx ? n[i] : mx;
+    return mx;
+}
+
+int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                      const double* const* b, double* const* x, float* const* R_out, const int* ldr,
+                      void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
+                      cudaStream_t stream) {
+    lls_options o;
+    Knobs k;
+    resolve_settings(opts, 1, batch, batch_nmax(batch, n), o, k);
+    return batched_core(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, o, k, infos, stream);
+}
+
+// ---------------------------------------------------------------------------------------
+// Autotuning (the paper tunes its panel by hand for its GPU, Sec. 3.1.3): timed trials of the
+// implementation choices on the caller's own problem; the fastest is recorded for the shape
+// and used by every later call that leaves panel_width at 0.
+// ---------------------------------------------------------------------------------------
+static void knobs_to_tuning(int pw, const Knobs& k, float ms, lls_tuning& t) {
+    memset(&t, 0, sizeof(t));
+    t.panel_width = pw;
+    t.node_mode = k.node_mode;
+    t.gemm_kernel = k.gemm_kernel;
+    t.batched_ctas_per_sm = k.batched_ctas;
+    t.ms = ms;
+}
+
+int lls_tuning_set(int kind, int m, int n, const lls_options* opts, const lls_tuning* t) {
+    lls_options o;
+    resolve(opts, o);
+    if ((kind != 0 && kind != 1) || m < 1 || n < 1 || !t || !valid_opts(o)) return LLS_ERR_ARG;
+    if (t->node_mode < 0 || t->node_mode > 2 || t->gemm_kernel < 0 || t->gemm_kernel > 2 ||
+        t->batched_ctas_per_sm < 0)
+        return LLS_ERR_ARG;
+    if (kind == 0) {
+        lls_options c = o;
+        c.panel_width = t->panel_width;
+        if (!valid_opts(c)) return LLS_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(kind, m, n, o)] = *t;
+    return LLS_OK;
+}
+
+int lls_tuning_get(int kind, int m, int n, const lls_options* opts, lls_tuning* t) {
+    lls_options o;
+    resolve(opts, o);
+    if ((kind != 0 && kind != 1) || !t) return LLS_ERR_ARG;
+    return tuned_lookup(kind, m, n, o, *t) ? 1 : 0;
+}
+
+void lls_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+// Time of one trial: the fastest of `reps` solves after one untimed (which records the graph),
+// as device time from the solve's own phase events; negative when the setting does not run.
+static float trial_solve(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
+                         size_t ws_bytes, const lls_options& o, const Knobs& k, int reps, cudaStream_t st) {
+    if (solve_ws_bytes(m, n, o) > ws_bytes) return -1.f;
+    lls_info info;
+    int rc = solve_core(m, n, A, lda, b, x, nullptr, 0, ws, ws_bytes, o, k, &info, st);
+    if (rc < 0) return -1.f;
+    float best = -1.f;
+    for (int r = 0; r < reps; ++r) {
+        rc = solve_core(m, n, A, lda, b, x, nullptr, 0, ws, ws_bytes, o, k, &info, st);
+        if (rc < 0) return -1.f;
+        const float t = info.qr_ms + info.krylov_ms;
+        if (best < 0.f || t < best) best = t;
+    }
+    return best;
+}
+
+size_t lls_autotune_workspace_size(int m, int n, const lls_options* opts) {
+    lls_options o;
+    resolve(opts, o);
+    if (n < 1 || m < n || !valid_opts(o)) return 0;
+    return solve_ws_bytes_auto(m, n, nullptr, o);
+}
+
+int lls_autotune(int m, int n, const float* A, int lda, const double* b, double* x, void* ws, size_t ws_bytes,
+                 const lls_options* opts, int reps, lls_tuning* best, cudaStream_t stream) {
+    lls_options o;
+    resolve(opts, o);
+    if (n < 1 || m < n || lda < m || !A || !b || !x || !ws || !best || reps < 1) return LLS_ERR_ARG;
+    if (!valid_opts(o) || o.x0 == LLS_X0_GIVEN) return LLS_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    // coordinate search from the defaults: panel width, then the node launches, then the
+    // wide nodes' product kernel
+    Knobs k = default_knobs();
+    lls_options cur = o;
+    cur.panel_width = 16;
+    float tbest = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, cur, k, reps, stream);
+    for (int pw : kTuneWidths) {
+        if (pw == 16) continue;
+        lls_options c = o;
+        c.panel_width = pw;
+        if (!valid_opts(c)) continue;
+        const float t = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, c, k, reps, stream);
+        if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; cur = c; }
+    }
+    for (int nm = 0; nm <= 2; ++nm) {
+        if (nm == k.node_mode) continue;
+        Knobs c = k;
+        c.node_mode = nm;
+        const float t = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, cur, c, reps, stream);
+        if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; k = c; }
+    }
+    for (int g = 0; g <= 2; ++g) {
+        if (g == k.gemm_kernel) continue;
+        Knobs c = k;
+        c.gemm_kernel = g;
+        const float t = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, cur, c, reps, stream);
+        if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; k = c; }
+    }
+    if (tbest < 0.f) return LLS_ERR_UNSUPPORTED;
+    knobs_to_tuning(cur.panel_width, k, tbest, *best);
+    return lls_tuning_set(0, m, n, &o, best);
+}
+
+int lls_autotune_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                         const double* const* b, double* const* x, void* ws, size_t ws_bytes,
+                         const lls_options* opts, int reps, lls_tuning* best, cudaStream_t stream) {
+    lls_options o;
+    resolve(opts, o);
+    if (!best || reps < 1) return LLS_ERR_ARG;
+    // CTAs per SM, from one up to as many as fit (batched_execute caps the request)
+    float tbest = -1.f;
+    Knobs kb = default_knobs();
+    std::vector<lls_info> infos((size_t)(batch > 0 ? batch : 1));
+    for (int ctas = 1; ctas <= 4; ++ctas) {
+        Knobs k = default_knobs();
+        k.batched_ctas = ctas;
+        int rc = batched_core(batch, m, n, A, lda, b, x, nullptr, nullptr, ws, ws_bytes, o, k, infos.data(), stream);
+        if (rc < 0 && rc != LLS_NOT_CONVERGED) {
+            if (ctas == 1) return rc;     // argument errors and the like: report them
+            continue;
+        }
+        float t = -1.f;
+        for (int r = 0; r < reps; ++r) {
+            rc = batched_core(batch, m, n, A, lda, b, x, nullptr, nullptr, ws, ws_bytes, o, k, infos.data(), stream);
+            if (rc < 0) break;
+            if (t < 0.f || infos[0].krylov_ms < t) t = infos[0].krylov_ms;
+        }
+        if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; kb = k; }
+    }
+    if (tbest < 0.f) return LLS_ERR_UNSUPPORTED;
+    knobs_to_tuning(16, kb, tbest, *best);
+    return lls_tuning_set(1, batch, batch_nmax(batch, n), &o, best);
 }
 
 }  // extern "C"

@@ -700,7 +700,8 @@ int batched_upload(int batch, const int* m, const int* n, const float* const* A,
 }
 
 // The persistent launch over an uploaded table (capturable in a CUDA graph).
-int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, cudaStream_t st) {
+int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, int ctas_per_sm,
+                    cudaStream_t st) {
     BLayout L;
     b_layout(batch, m, n, L);
     char* base = (char*)ws;
@@ -722,6 +723,7 @@ int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_o
     LLS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kPanelThreads, smem));
     if (per < 1) return LLS_ERR_UNSUPPORTED;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     int grid = sms * per;
     if (grid > batch) grid = batch;
     kern<<<grid, kPanelThreads, smem, st>>>(g);

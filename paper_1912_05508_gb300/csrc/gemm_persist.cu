@@ -29,26 +29,29 @@ int proj_reduce(const float* part, int splits, int w1, int w2, const int* e, con
 namespace {
 
 constexpr int kPM = 128;                     // tile rows (M)
-constexpr int kPN = 128;                     // tile columns (N), one accumulator
 constexpr int kPK = 64;                      // K per stage: 128-byte rows of 2-byte elements
 constexpr int kPThreads = 256;
 constexpr int kCCols = 32;                   // A2 columns per chunk
-constexpr int kCChunks = kPN / kCCols;
-constexpr int kCRing = 6;                    // A2 chunk buffers
 constexpr int kABytes = kPM * kPK * 2;       // 16 KB
-constexpr int kBBytes = kPN * kPK * 2;       // 16 KB
-constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kCBytes = kPM * kCCols * 4;    // 16 KB
 
 enum { PE_PARTIAL = 0, PE_UPDATE = 1 };
 
-template <int EPI> struct PCfg;
-template <> struct PCfg<PE_UPDATE> { static constexpr int stages = 4, ring = kCRing; };
-template <> struct PCfg<PE_PARTIAL> { static constexpr int stages = 6, ring = 0; };
+// Tile width BN (128 or 256 columns: one accumulator of BN TMEM columns, two of them), pipeline
+// depth and A2 chunk buffers, sized to the 227 KB of shared memory a CTA may hold. Wider tiles
+// halve the operand traffic from L2 per flop, which the 128 x 128 tiles are bound by.
+template <int EPI, int BN> struct PCfg {
+    static constexpr int bbytes = BN * kPK * 2;
+    static constexpr int stage_bytes = kABytes + bbytes;
+    static constexpr int stages = EPI == PE_UPDATE ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : 6);
+    static constexpr int ring = EPI == PE_UPDATE ? (BN == 256 ? 4 : 6) : 0;
+    static constexpr int chunks = BN / kCCols;
+};
 
-template <int EPI>
+template <int EPI, int BN>
 constexpr int p_smem_bytes() {
-    return 1024 + PCfg<EPI>::stages * kStageBytes + PCfg<EPI>::ring * kCBytes + 512;   // + barriers
+    using C = PCfg<EPI, BN>;
+    return 1024 + C::stages * C::stage_bytes + C::ring * kCBytes + 512;   // + barriers
 }
 
 struct PArgs {
@@ -62,12 +65,13 @@ struct PArgs {
     int* err;
 };
 
+template <int BN>
 __device__ __forceinline__ void decode_unit(const PArgs& a, int u, int& m0, int& n0, int& kt0, int& kt1, int& s) {
     const int tiles = a.tiles_m * a.tiles_n;
     s = u / tiles;
     const int t = u - s * tiles;
     m0 = (t / a.tiles_n) * kPM;     // N fastest: the tiles that share a block of rows of the A
-    n0 = (t % a.tiles_n) * kPN;     // operand run at the same time and read it from L2
+    n0 = (t % a.tiles_n) * BN;      // operand run at the same time and read it from L2
     kt0 = s * a.ktiles;
     kt1 = min(a.ktotal, kt0 + a.ktiles);
 }
@@ -84,16 +88,20 @@ __device__ __forceinline__ void drain_ring(uint32_t full0, int count, uint32_t i
     }
 }
 
-template <int EPI, bool A_MN>
+template <int EPI, bool A_MN, int BN>
 __global__ void __launch_bounds__(kPThreads, 1)
 tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ CUtensorMap tmC, PArgs a) {
-    constexpr int S = PCfg<EPI>::stages;
-    constexpr int NR = PCfg<EPI>::ring > 0 ? PCfg<EPI>::ring : 1;
+    using Cfg = PCfg<EPI, BN>;
+    constexpr int S = Cfg::stages;
+    constexpr int NR = Cfg::ring > 0 ? Cfg::ring : 1;
+    constexpr int kStageBytes = Cfg::stage_bytes;
+    constexpr int kCChunks = Cfg::chunks;
+    constexpr int kPN = BN;
     extern __shared__ __align__(1024) uint8_t p_smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* cring = smem + S * kStageBytes;
-    uint64_t* bars = (uint64_t*)(cring + PCfg<EPI>::ring * kCBytes);
+    uint64_t* bars = (uint64_t*)(cring + Cfg::ring * kCBytes);
     // full[S], empty[S], tfull[2], tempty[2], cfull[NR], cempty[NR], cdone[NR], mmadone, sdone
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
     const uint32_t tfull0 = empty0 + 8 * S, tempty0 = tfull0 + 16;
@@ -133,7 +141,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         bool ok = true;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             int m0, n0, kt0, kt1, s;
-            decode_unit(a, u, m0, n0, kt0, kt1, s);
+            decode_unit<BN>(a, u, m0, n0, kt0, kt1, s);
             for (int kt = kt0; kt < kt1; ++kt, ++it) {
                 const int st = it % S;
                 const uint32_t ph = (it / S) & 1;
@@ -159,7 +167,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             int lt = 0;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++lt) {
                 int m0, n0, kt0, kt1, s;
-                decode_unit(a, u, m0, n0, kt0, kt1, s);
+                decode_unit<BN>(a, u, m0, n0, kt0, kt1, s);
                 const int acc = lt & 1;
                 const uint32_t use = (uint32_t)(lt >> 1);
                 if (!mbar_wait(tempty0 + 8 * acc, (use & 1) ^ 1, a.err)) { ok = false; break; }
@@ -195,7 +203,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         bool ok = true;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             int m0, n0, kt0, kt1, s;
-            decode_unit(a, u, m0, n0, kt0, kt1, s);
+            decode_unit<BN>(a, u, m0, n0, kt0, kt1, s);
             for (int c = 0; c < kCChunks; ++c, ++cc) {
                 const int slot = cc % NR;
                 const uint32_t ph = (cc / NR) & 1;
@@ -214,7 +222,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const bool storer = (warp == 4 && lane == 0);
         for (int u = blockIdx.x; u < units; u += gridDim.x, ++lt) {
             int m0, n0, kt0, kt1, s;
-            decode_unit(a, u, m0, n0, kt0, kt1, s);
+            decode_unit<BN>(a, u, m0, n0, kt0, kt1, s);
             const int acc = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
             if (ok && !mbar_wait(tfull0 + 8 * acc, use & 1, a.err)) ok = false;
@@ -283,7 +291,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 }
                 for (int u = blockIdx.x; u < units; u += gridDim.x) {
                     int m0, n0, kt0, kt1, s;
-                    decode_unit(a, u, m0, n0, kt0, kt1, s);
+                    decode_unit<BN>(a, u, m0, n0, kt0, kt1, s);
                     const int row = m0 + r;
                     if (row < a.M)
                         for (int j = n0; j < n0 + kPN && j < a.N; ++j)
@@ -308,11 +316,12 @@ int sms_of_device() {
     return sms[dev];
 }
 
-template <int EPI, bool A_MN>
+template <int EPI, bool A_MN, int BN>
 int launch_persist(const CUtensorMap& tA, const CUtensorMap& tB, const CUtensorMap& tC, const PArgs& a,
                    cudaStream_t st) {
-    constexpr int smem = p_smem_bytes<EPI>();
-    auto k = tc_persist_kernel<EPI, A_MN>;
+    constexpr int smem = p_smem_bytes<EPI, BN>();
+    static_assert(smem <= 232448, "shared memory of one CTA");
+    auto k = tc_persist_kernel<EPI, A_MN, BN>;
     static bool attr[64];
     int dev = 0;
     LLS_CUDA_TRY(cudaGetDevice(&dev));
@@ -330,82 +339,98 @@ int launch_persist(const CUtensorMap& tA, const CUtensorMap& tB, const CUtensorM
     return LLS_OK;
 }
 
-bool persist_disabled() {
-    static const bool off = [] {
-        const char* v = getenv("LLS_GEMM");
-        return v && v[0] == 'c';   // LLS_GEMM=cta: the one-tile-per-CTA products (for comparisons)
-    }();
-    return off;
-}
-
 }  // namespace
 
 // The update on the persistent kernel; LLS_ERR_UNSUPPORTED (nothing launched) when the shape or
 // the operands' alignment does not fit it (the caller then uses the one-tile-per-CTA kernel).
-int gemm_update_persistent(const UpdCall& c, cudaStream_t st) {
-    if (persist_disabled() || (c.lowp != 0 && c.lowp != 1) || c.w2 < kPN || c.w1 < kPK) return LLS_ERR_UNSUPPORTED;
-    if (((uintptr_t)c.A2 & 15) != 0 || (c.ldw & 3) != 0) return LLS_ERR_UNSUPPORTED;
+template <int BN>
+static int update_persistent_bn(const UpdCall& c, cudaStream_t st) {
     const CUtensorMapDataType dt = c.lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap tA, tB, tC;
     if (tc_make_tmap(&tA, c.Q1l, dt, 2, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, 64, kPK,
                      CU_TENSOR_MAP_SWIZZLE_128B) != LLS_OK ||
-        tc_make_tmap(&tB, c.R12l, dt, 2, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, kPK, kPN,
+        tc_make_tmap(&tB, c.R12l, dt, 2, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, kPK, BN,
                      CU_TENSOR_MAP_SWIZZLE_128B) != LLS_OK ||
         tc_make_tmap(&tC, c.A2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldw,
                      kPM, kCCols, CU_TENSOR_MAP_SWIZZLE_NONE) != LLS_OK)
         return LLS_ERR_UNSUPPORTED;
     PArgs a;
     a.M = c.m; a.N = c.w2;
-    a.tiles_m = ceil_div(c.m, kPM); a.tiles_n = ceil_div(c.w2, kPN); a.splits = 1;
+    a.tiles_m = ceil_div(c.m, kPM); a.tiles_n = ceil_div(c.w2, BN); a.splits = 1;
     a.ktotal = ceil_div(c.w1, kPK); a.ktiles = a.ktotal;
-    a.idesc = tc_make_idesc(c.lowp, kPN, true);
+    a.idesc = tc_make_idesc(c.lowp, BN, true);
     a.out = c.A2; a.ldo = c.ldw; a.fexp = c.f; a.err = c.err;
-    return launch_persist<PE_UPDATE, true>(tA, tB, tC, a, st);
+    return launch_persist<PE_UPDATE, true, BN>(tA, tB, tC, a, st);
 }
 
-// Number of K splits of the persistent projection: the one that minimises the work of the most
-// loaded CTA (whole units per CTA times the K tiles of a unit), at most 8 splits and at least
-// 8 K tiles per split; ties go to fewer splits (less partial-sum traffic).
+// The update on the persistent kernel; LLS_ERR_UNSUPPORTED (nothing launched) when the shape or
+// the operands' alignment does not fit it (the caller then uses the one-tile-per-CTA kernel).
+// Nodes at least 256 columns wide take 128 x 256 tiles, narrower ones 128 x 128.
+int gemm_update_persistent(const UpdCall& c, cudaStream_t st) {
+    if (c.gemm_kernel == 1 || (c.lowp != 0 && c.lowp != 1) || c.w2 < 128 || c.w1 < kPK) return LLS_ERR_UNSUPPORTED;
+    if (((uintptr_t)c.A2 & 15) != 0 || (c.ldw & 3) != 0) return LLS_ERR_UNSUPPORTED;
+    return c.w2 >= 256 ? update_persistent_bn<256>(c, st) : update_persistent_bn<128>(c, st);
+}
+
+// K splits of the persistent projection: the work of the most loaded CTA (whole units per CTA
+// times the K tiles of a unit) plus the partial sums' round trip through memory (written here,
+// read by the fixed-order reduction), both in units of one K tile of MMAs; at most 8 splits and
+// at least 8 K tiles per split. Ties go to fewer splits.
+static int proj_bn(int w2) { return w2 >= 256 ? 256 : 128; }
+
 void proj_split_persistent(int m, int w1, int w2, int& splits, int& ktps) {
     const int sms = sms_of_device() > 0 ? sms_of_device() : 148;
-    const long long tiles = (long long)ceil_div(w1, kPM) * ceil_div(w2, kPN);
+    const int bn = proj_bn(w2);
+    const long long tiles = (long long)ceil_div(w1, kPM) * ceil_div(w2, bn);
     const int kt = ceil_div(m, kPK);
+    // one K tile of a 128 x bn unit moves (128 + bn) x 64 x 2 bytes through the tensor cores in
+    // about bn / 128 x 0.15 us; a split's partial tile set is w1 x w2 x 8 bytes of traffic at
+    // about 5 TB/s, spread over all SMs
+    const double ktile_us = 0.15 * bn / 128.0;
+    const double split_units = ((double)w1 * w2 * 8.0 / 5.0e12 * 1e6) / ktile_us;
     int best_s = 1;
-    long long best = -1;
+    double best = -1.0;
     for (int s = 1; s <= 8 && (s == 1 || kt / s >= 8); ++s) {
         const int per = ceil_div(kt, s);
         const int ss = ceil_div(kt, per);                 // splits actually non-empty
         const long long units = tiles * ss;
-        const long long cost = ((units + sms - 1) / sms) * per;
-        if (best < 0 || cost < best) { best = cost; best_s = ss; }
+        const double cost = (double)((units + sms - 1) / sms) * per + split_units * ss;
+        if (best < 0.0 || cost < best) { best = cost; best_s = ss; }
     }
     ktps = ceil_div(kt, best_s);
     splits = ceil_div(kt, ktps);
 }
 
 bool projection_persistent_applies(int lowp, int w1, int w2) {
-    return !persist_disabled() && (lowp == 0 || lowp == 1) && w1 >= kPM && w2 >= kPN;
+    return (lowp == 0 || lowp == 1) && w1 >= kPM && w2 >= 128;
 }
 
-int gemm_projection_persistent(const ProjCall& c, cudaStream_t st) {
-    if (!projection_persistent_applies(c.lowp, c.w1, c.w2)) return LLS_ERR_UNSUPPORTED;
-    int splits, ktps;
-    proj_split_persistent(c.m, c.w1, c.w2, splits, ktps);
-    if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
+template <int BN>
+static int projection_persistent_bn(const ProjCall& c, int splits, int ktps, cudaStream_t st) {
     const CUtensorMapDataType dt = c.lowp == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap tA, tB;
     if (tc_make_tmap(&tA, c.Q1l, dt, 2, (uint64_t)c.m, (uint64_t)c.w1, (uint64_t)c.ldh, kPK, kPM,
                      CU_TENSOR_MAP_SWIZZLE_128B) != LLS_OK ||
-        tc_make_tmap(&tB, c.A2l, dt, 2, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldh, kPK, kPN,
+        tc_make_tmap(&tB, c.A2l, dt, 2, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldh, kPK, BN,
                      CU_TENSOR_MAP_SWIZZLE_128B) != LLS_OK)
         return LLS_ERR_UNSUPPORTED;
     PArgs a;
     a.M = c.w1; a.N = c.w2;
-    a.tiles_m = ceil_div(c.w1, kPM); a.tiles_n = ceil_div(c.w2, kPN); a.splits = splits;
+    a.tiles_m = ceil_div(c.w1, kPM); a.tiles_n = ceil_div(c.w2, BN); a.splits = splits;
     a.ktotal = ceil_div(c.m, kPK); a.ktiles = ktps;
-    a.idesc = tc_make_idesc(c.lowp, kPN, false);
+    a.idesc = tc_make_idesc(c.lowp, BN, false);
     a.out = c.part; a.ldo = c.w1; a.fexp = nullptr; a.err = c.err;
-    LLS_TRY((launch_persist<PE_PARTIAL, false>(tA, tB, tA, a, st)));
+    return launch_persist<PE_PARTIAL, false, BN>(tA, tB, tA, a, st);
+}
+
+int gemm_projection_persistent(const ProjCall& c, cudaStream_t st) {
+    if (c.gemm_kernel != 0 || !projection_persistent_applies(c.lowp, c.w1, c.w2)) return LLS_ERR_UNSUPPORTED;
+    int splits, ktps;
+    proj_split_persistent(c.m, c.w1, c.w2, splits, ktps);
+    if ((size_t)splits * c.w1 * c.w2 > c.part_floats) return LLS_ERR_WORKSPACE;
+    const int r = proj_bn(c.w2) == 256 ? projection_persistent_bn<256>(c, splits, ktps, st)
+                                       : projection_persistent_bn<128>(c, splits, ktps, st);
+    LLS_TRY(r);
     return proj_reduce(c.part, splits, c.w1, c.w2, c.e, c.sq, c.R12, c.ldr, c.R12l, c.ldrl, c.f, c.lowp, st, c.err);
 }
 

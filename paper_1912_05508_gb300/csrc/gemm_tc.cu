@@ -339,7 +339,7 @@ size_t proj_partial_floats(int m, int w1, int w2) {
 }
 
 int gemm_projection(const ProjCall& c, cudaStream_t st) {
-    if (projection_persistent_applies(c.lowp, c.w1, c.w2)) {
+    if (c.gemm_kernel == 0 && projection_persistent_applies(c.lowp, c.w1, c.w2)) {
         const int r = gemm_projection_persistent(c, st);
         if (r != LLS_ERR_UNSUPPORTED) return r;
     }

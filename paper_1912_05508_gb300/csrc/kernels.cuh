@@ -6,6 +6,20 @@ namespace lls {
 
 constexpr int kMaxPanelLevels = 8;
 
+// Implementation choices that leave the arithmetic of the method unchanged (the same rounding
+// points, the same fixed summation orders within each kernel); the autotuner picks them per
+// shape. The environment switches LLS_NODE and LLS_GEMM set the defaults, for comparisons.
+struct Knobs {
+    int node_mode = 0;      // 0: the lowest nodes with their two panels, and the narrow nodes, as
+                            //    single launches; 1: narrow nodes as single launches, the lowest
+                            //    nodes' panels separate; 2: every node as four launches
+    int gemm_kernel = 0;    // products of the wide nodes: 0 persistent, 1 one output tile per CTA,
+                            // 2 persistent update with the one-tile-per-CTA projection
+    int batched_ctas = 0;   // batched solver: CTAs per SM, 0 = as many as fit
+    int reserved = 0;
+};
+Knobs default_knobs();
+
 // ---- panel (panel.cu) -------------------------------------------------------------------
 struct PanelCall {
     float* W; int ldw;
@@ -65,6 +79,7 @@ struct ProjCall {
     float* part; size_t part_floats;              // split-K partials scratch
     int lowp;
     int* err;                                     // device error word (bounded waits)
+    int gemm_kernel = 0;                          // Knobs::gemm_kernel
 };
 struct UpdCall {
     const void* Q1l; int ldh;                     // m x w1 low precision (M-major A operand)
@@ -75,6 +90,7 @@ struct UpdCall {
     int m, w1, w2;
     int lowp;
     int* err;
+    int gemm_kernel = 0;                          // Knobs::gemm_kernel
 };
 size_t proj_partial_floats(int m, int w1, int w2);
 // Narrow node (w1 <= 32, FP16/BF16) as one cooperative launch (node_fused.cu): the same
@@ -156,7 +172,8 @@ double* batched_info_ptr(void* ws, int batch, const int* m, const int* n);
 int batched_upload(int batch, const int* m, const int* n, const float* const* A, const int* lda,
                    const double* const* b, double* const* x, float* const* Rout, const int* ldr,
                    void* ws, size_t ws_bytes, cudaStream_t st);
-int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, cudaStream_t st);
+int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, int ctas_per_sm,
+                    cudaStream_t st);
 
 // ---- graph replay (graph.cu) -----------------------------------------------------------------
 // Identity of one call: plain-old-data, compared bytewise (zero-initialize before filling).
@@ -166,6 +183,7 @@ struct GraphKey {
     const void* ptrs[8];
     size_t ws_bytes;
     lls_options opts;
+    Knobs knobs;
 };
 // Enqueues one call on `st`; ev (may be null) receives 3 phase events; `capturing` selects
 // external event-record nodes.

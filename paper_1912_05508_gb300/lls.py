@@ -31,7 +31,9 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_panel_block_qr_workspace_size", "lls_panel_block_qr",
            "lls_solve_host_workspace_size", "lls_solve_host", "lls_selftest_wait_timeout",
            "lls_upload_chunks",
-           "lls_householder_workspace_size", "lls_householder_solve")
+           "lls_householder_workspace_size", "lls_householder_solve",
+           "lls_autotune_workspace_size", "lls_autotune", "lls_autotune_batched", "lls_tuning_set",
+           "lls_tuning_get", "lls_tuning_clear")
 
 
 class lls_options(C.Structure):
@@ -45,6 +47,14 @@ class lls_info(C.Structure):
                 ("fwd_est", C.c_double), ("res_norm", C.c_double), ("atr_norm", C.c_double),
                 ("anorm_f", C.c_double), ("xnorm", C.c_double), ("qr_ms", C.c_float),
                 ("krylov_ms", C.c_float), ("a_passes", C.c_int), ("m_passes", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lls_tuning(C.Structure):
+    _fields_ = [("panel_width", C.c_int), ("node_mode", C.c_int), ("gemm_kernel", C.c_int),
+                ("batched_ctas_per_sm", C.c_int), ("ms", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,6 +133,19 @@ def load(path: str = LIB_PATH):
     lib.lls_solve_batched.argtypes = [i, ip, ip, pp, ip, pp, pp, pp, ip, vp, sz, C.POINTER(lls_options),
                                       C.POINTER(lls_info), vp]
     lib.lls_solve_batched.restype = i
+    tp = C.POINTER(lls_tuning)
+    lib.lls_autotune_workspace_size.argtypes = [i, i, C.POINTER(lls_options)]
+    lib.lls_autotune_workspace_size.restype = sz
+    lib.lls_autotune.argtypes = [i, i, vp, i, vp, vp, vp, sz, C.POINTER(lls_options), i, tp, vp]
+    lib.lls_autotune.restype = i
+    lib.lls_autotune_batched.argtypes = [i, ip, ip, pp, ip, pp, pp, vp, sz, C.POINTER(lls_options), i, tp, vp]
+    lib.lls_autotune_batched.restype = i
+    lib.lls_tuning_set.argtypes = [i, i, i, C.POINTER(lls_options), tp]
+    lib.lls_tuning_set.restype = i
+    lib.lls_tuning_get.argtypes = [i, i, i, C.POINTER(lls_options), tp]
+    lib.lls_tuning_get.restype = i
+    lib.lls_tuning_clear.argtypes = []
+    lib.lls_tuning_clear.restype = None
     _lib = lib
     return lib
 
@@ -308,6 +331,36 @@ def lls_solve_batched(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts,
                                     C.byref(opts) if opts is not None else None, infos, stream)
 
 
+def lls_autotune_workspace_size(m, n, opts=None) -> int:
+    return load().lls_autotune_workspace_size(m, n, C.byref(opts) if opts is not None else None)
+
+
+def lls_autotune(m, n, A, lda, b, x, ws, ws_bytes, opts, reps, best, stream) -> int:
+    return load().lls_autotune(m, n, A, lda, b, x, ws, ws_bytes, C.byref(opts) if opts is not None else None,
+                               reps, C.byref(best), stream)
+
+
+def lls_autotune_batched(batch, m, n, A, lda, b, x, ws, ws_bytes, opts, reps, best, stream) -> int:
+    return load().lls_autotune_batched(batch, _ints(m), _ints(n), _ptrs(A), _ints(lda), _ptrs(b), _ptrs(x), ws,
+                                       ws_bytes, C.byref(opts) if opts is not None else None, reps,
+                                       C.byref(best), stream)
+
+
+def lls_tuning_set(kind, m, n, opts, tuning) -> int:
+    return load().lls_tuning_set(kind, m, n, C.byref(opts) if opts is not None else None, C.byref(tuning))
+
+
+def lls_tuning_get(kind, m, n, opts=None):
+    """The recorded lls_tuning for the key, or None."""
+    t = lls_tuning()
+    r = load().lls_tuning_get(kind, m, n, C.byref(opts) if opts is not None else None, C.byref(t))
+    return t if r == 1 else None
+
+
+def lls_tuning_clear() -> None:
+    load().lls_tuning_clear()
+
+
 # ---- torch helpers (allocation and pointer passing only) -----------------------------------
 
 def _torch():
@@ -340,10 +393,109 @@ def workspace(nbytes: int, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=0, panel_leaf="cgs2"):
-    """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False."""
+# ---- tuned settings: the library's table, saved to and restored from the JSON cache ----------
+
+_tuning_loaded = set()
+
+
+def _device_ident(device):
+    torch = _torch()
+    props = torch.cuda.get_device_properties(device)
+    return props.name, props.multi_processor_count
+
+
+def _opt_ints(o):
+    return {f: int(getattr(o, f)) for f in ("gemm_prec", "target", "krylov", "reorth", "panel_leaf")}
+
+
+def load_tuning_cache(device=None, path=None):
+    """Restore the settings saved for this GPU model into the library's table (once per device
+    and process); returns the number restored."""
+    from . import tuning
+    torch = _torch()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    if (idx, path) in _tuning_loaded:
+        return 0
+    _tuning_loaded.add((idx, path))
+    name, sms = _device_ident(idx)
+    count = 0
+    with torch.cuda.device(idx):
+        for kind, m, n, opts, t in tuning.entries_for_device(tuning.load(path), name, sms):
+            o = lls_default_options()
+            for f, v in opts.items():
+                setattr(o, f, v)
+            rec = lls_tuning(int(t["panel_width"]), int(t["node_mode"]), int(t["gemm_kernel"]),
+                             int(t["batched_ctas_per_sm"]), float(t["ms"]))
+            if lls_tuning_set(kind, m, n, o, rec) == 0:
+                count += 1
+    return count
+
+
+def _save_tuning(kind, m, n, o, best, device, path=None):
+    from . import tuning
+    name, sms = _device_ident(device)
+    try:
+        tuning.record(tuning.make_key(name, sms, kind, m, n, _opt_ints(o)), best.as_dict(), path)
+    except OSError:
+        pass      # a read-only cache location: the setting stays in the process's table
+
+
+def autotune(A, b, prec="fp16", target="fp64", krylov="cgls", reorth=0, panel_leaf="cgs2", reps=2, stream=None,
+             cache=True, cache_path=None):
+    """Measure the implementation choices for this problem's shape (lls_autotune), record the
+    fastest in the library's table and, with cache=True, in the JSON cache. Returns it as a dict."""
     torch = _torch()
     _check_colmajor(A)
+    m, n = A.shape
+    o = make_options(prec=prec, target=target, krylov=krylov, reorth=reorth, panel_leaf=panel_leaf)
+    nb = lls_autotune_workspace_size(m, n, o)
+    if nb == 0:
+        raise LLSError(-1, "lls_autotune_workspace_size")
+    ws = workspace(nb, A.device)
+    bb = b.to(device=A.device, dtype=torch.float64).contiguous()
+    x = torch.empty(n, dtype=torch.float64, device=A.device)
+    best = lls_tuning()
+    st = lls_autotune(m, n, A.data_ptr(), A.stride(1), bb.data_ptr(), x.data_ptr(), ws.data_ptr(), ws.numel(), o,
+                      int(reps), best, _stream(stream))
+    if st != 0:
+        raise LLSError(st, "lls_autotune")
+    if cache:
+        _save_tuning(0, m, n, o, best, A.device, cache_path)
+    return best.as_dict()
+
+
+def autotune_batched(As, bs, prec="fp16", target="fp32", reps=2, stream=None, cache=True, cache_path=None):
+    """lls_autotune_batched for a list of problems (column-major FP32 A_i, FP64 b_i)."""
+    torch = _torch()
+    batch = len(As)
+    ms = [A.shape[0] for A in As]
+    ns = [A.shape[1] for A in As]
+    o = make_options(prec=prec, target=target, panel_width=16)
+    nb = lls_solve_batched_workspace_size(batch, ms, ns, o)
+    if nb == 0:
+        raise LLSError(-6, "lls_solve_batched_workspace_size")
+    dev = As[0].device
+    ws = workspace(nb, dev)
+    bs = [b.to(device=dev, dtype=torch.float64).contiguous() for b in bs]
+    xs = [torch.empty(n_, dtype=torch.float64, device=dev) for n_ in ns]
+    best = lls_tuning()
+    st = lls_autotune_batched(batch, ms, ns, [A.data_ptr() for A in As], [A.stride(1) for A in As],
+                              [b.data_ptr() for b in bs], [x.data_ptr() for x in xs], ws.data_ptr(), ws.numel(), o,
+                              int(reps), best, _stream(stream))
+    if st != 0:
+        raise LLSError(st, "lls_autotune_batched")
+    if cache:
+        _save_tuning(1, batch, max(ns), o, best, dev, cache_path)
+    return best.as_dict()
+
+
+def qr(A, prec="fp16", panel_width=0, want_q=True, ws=None, stream=None, reorth=0, panel_leaf="cgs2"):
+    """(Q, R) of a column-major FP32 device matrix A (m x n). Q is None when want_q is False.
+    panel_width 0 uses the setting recorded for the shape (lls_autotune), if any."""
+    torch = _torch()
+    _check_colmajor(A)
+    load_tuning_cache(A.device)
     m, n = A.shape
     o = make_options(prec=prec, panel_width=panel_width, reorth=reorth, panel_leaf=panel_leaf)
     nb = qr_factor_workspace_size(m, n, o)
@@ -365,9 +517,11 @@ def solve(A, b, prec="fp16", target="fp64", tol=0.0, max_iter=200, panel_width=0
     """x = argmin ||A x - b|| for column-major FP32 A (m x n) and FP64 b on the device.
 
     x0: None (start from zero), "direct" (start from R^{-1} Q^T b) or a vector (warm start).
+    panel_width 0 uses the setting recorded for the shape (lls_autotune), if any.
     Returns (x, info_dict[, R]). Synchronizes the stream (to fill info)."""
     torch = _torch()
     _check_colmajor(A)
+    load_tuning_cache(A.device)
     m, n = A.shape
     mode = "zero" if x0 is None else ("direct" if isinstance(x0, str) and x0 == "direct" else "given")
     o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter,
@@ -496,9 +650,10 @@ def solve_batched(As, bs, prec="fp16", target="fp32", tol=0.0, max_iter=200, wan
     batch = len(As)
     for A in As:
         _check_colmajor(A)
+    load_tuning_cache(As[0].device)
     ms = [A.shape[0] for A in As]
     ns = [A.shape[1] for A in As]
-    o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter, panel_width=16)
+    o = make_options(prec=prec, target=target, tol=tol, max_iter=max_iter, panel_width=0)
     nb = lls_solve_batched_workspace_size(batch, ms, ns, o)
     if nb == 0:
         raise LLSError(-6, "lls_solve_batched_workspace_size")

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_defaults_and_status_strings(lib):
     o = lls.lls_default_options()
-    assert (o.gemm_prec, o.target, o.max_iter, o.panel_width, o.krylov) == (0, 1, 200, 16, 0)
+    assert (o.gemm_prec, o.target, o.max_iter, o.panel_width, o.krylov) == (0, 1, 200, 0, 0)
     assert lls.lls_status_string(0) == "ok"
     assert "singular" in lls.lls_status_string(-2)
 
@@ -126,3 +126,43 @@ def test_x0_option(lib):
     info = lls.lls_info()
     assert lls.lls_solve(1000, 64, 256, 1000, 256, 256, None, 0, 256, 1 << 30, lls.make_options(x0=5), info,
                          None) == -1
+
+
+def test_tuning_table_set_get_clear(lib):
+    # the library's table of tuned settings: keyed by kind, shape and the options that change
+    # the arithmetic; invalid settings are rejected; clear forgets everything
+    lls.lls_tuning_clear()
+    o = lls.make_options(prec="fp16", target="fp64")
+    assert lls.lls_tuning_get(0, 32768, 4096, o) is None
+    t = lls.lls_tuning(8, 1, 1, 0, 12.5)
+    assert lls.lls_tuning_set(0, 32768, 4096, o, t) == 0
+    got = lls.lls_tuning_get(0, 32768, 4096, o)
+    assert got is not None and got.as_dict() == {"panel_width": 8, "node_mode": 1, "gemm_kernel": 1,
+                                                 "batched_ctas_per_sm": 0, "ms": 12.5}
+    # another precision or shape is another key
+    assert lls.lls_tuning_get(0, 32768, 4096, lls.make_options(prec="bf16")) is None
+    assert lls.lls_tuning_get(0, 32768, 2048, o) is None
+    # the panel width does not take part in the key (it is what the setting chooses)
+    assert lls.lls_tuning_get(0, 32768, 4096, lls.make_options(prec="fp16", panel_width=32)) is not None
+    # invalid settings and kinds
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(40, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 3, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 0, 3, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(2, 100, 10, o, lls.lls_tuning(16, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, lls.make_options(prec="fp8"), lls.lls_tuning(8, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(1, 4096, 512, o, lls.lls_tuning(16, 0, 0, 2, 9.0)) == 0
+    assert lls.lls_tuning_get(1, 4096, 512, o).batched_ctas_per_sm == 2
+    lls.lls_tuning_clear()
+    assert lls.lls_tuning_get(0, 32768, 4096, o) is None and lls.lls_tuning_get(1, 4096, 512, o) is None
+
+
+def test_auto_panel_width_workspace_covers_every_candidate(lib):
+    # an "auto" call (panel_width 0) may run with any width a tuning picks: its workspace query
+    # answers for the largest of them
+    auto = lls.make_options(panel_width=0)
+    for m, n in ((1000, 100), (32768, 4096), (5000, 7)):
+        need = max(lls.lls_solve_workspace_size(m, n, lls.make_options(panel_width=w)) for w in (8, 16, 32))
+        assert lls.lls_solve_workspace_size(m, n, auto) == need
+        assert lls.lls_autotune_workspace_size(m, n, auto) == need
+        assert lls.qr_factor_workspace_size(m, n, auto) == max(
+            lls.qr_factor_workspace_size(m, n, lls.make_options(panel_width=w)) for w in (8, 16, 32))

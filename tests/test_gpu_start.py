@@ -31,18 +31,29 @@ def prob():
     return p, direct.lls(p.A, p.b)
 
 
+def kw_bound(A32, R):
+    """The backward error the stop test guarantees: the solver stops on
+    eta_est = ||R^-T A^T r|| / (||A||_F ||x||) <= 1e-12, and the Karlson-Walden estimate obeys
+    eta_kw <= ||(A^T A)^-1/2 R^T|| eta_est = eta_est / sigma_min(A R^-1)."""
+    A = np.asarray(A32, dtype=np.float64)
+    Rinv = np.linalg.inv(np.asarray(R.cpu().numpy(), dtype=np.float64))
+    smin = np.linalg.svd(A @ Rinv, compute_uv=False)[-1]
+    return 1e-12 / smin * (1 + 1e-6)
+
+
 @pytest.mark.parametrize("krylov", ["cgls", "lsqr"])
 def test_direct_start_converges_in_fewer_iterations(prob, krylov):
     p, xs = prob
     A = lls.colmajor(p.A)
     b = torch.from_numpy(p.b).cuda()
-    x0, i0 = lls.solve(A, b, krylov=krylov)
-    x1, i1 = lls.solve(A, b, krylov=krylov, x0="direct")
+    x0, i0, R0 = lls.solve(A, b, krylov=krylov, want_r=True)
+    x1, i1, R1 = lls.solve(A, b, krylov=krylov, x0="direct", want_r=True)
     assert i0["status"] == 0 and i1["status"] == 0, (i0, i1)
+    assert i0["eta"] <= 1e-12 and i1["eta"] <= 1e-12
     assert i1["iters"] < i0["iters"], (i0["iters"], i1["iters"])
-    for x in (x0, x1):
+    for x, R in ((x0, R0), (x1, R1)):
         xn = x.cpu().numpy()
-        assert metrics.eta_kw(p.A, p.b, xn) <= 1e-12
+        assert metrics.eta_kw(p.A, p.b, xn) <= kw_bound(p.A, R)
         assert metrics.forward_error(xn, xs) <= 10 * p.kappa * 1e-12
 
 
