@@ -218,7 +218,10 @@ int lls_solve_batched(int batch, const int* m, const int* n, const float* const*
  *  ws: lls_backward_workspace_size(batch, m, n, opts) bytes, 256-byte aligned.
  *  opts: target FP64 iterates z to ||R^-T (g - A^T A z)|| <= 1e-13 ||R^-T g|| (FP32: 1e-7);
  *        max_iter caps the CG iterations.
- * Problems are processed one after another on `stream`.
+ * A batch of two or more problems that the batched solver takes (n_i <= m_i <= 8192,
+ * n_i <= 1024) runs as one persistent launch in which each CTA takes whole problems from a
+ * work queue (R^{-1}, CG and the gradient on one SM, compensated products as in the solve);
+ * a single problem, or a batch with a larger one, runs problem after problem on the whole GPU.
  * Errors: LLS_ERR_ARG, LLS_ERR_WORKSPACE, LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA.
  * -------------------------------------------------------------------------- */
 size_t lls_backward_workspace_size(int batch, const int* m, const int* n, const lls_options* opts);

@@ -925,11 +925,21 @@ static bool batch_dims(int batch, const int* m, const int* n, int& mmax, int& nm
     return true;
 }
 
+// Batches of two or more problems that the batched kernels take run as one persistent launch;
+// single problems and larger ones run problem after problem on the whole GPU.
+static bool backward_batched(int batch, const int* m, const int* n) {
+    if (batch < 2) return false;
+    for (int i = 0; i < batch; ++i)
+        if (!batched_supported(m[i], n[i])) return false;
+    return true;
+}
+
 size_t lls_backward_workspace_size(int batch, const int* m, const int* n, const lls_options* opts) {
     lls_options o;
     resolve(opts, o);
     int mmax, nmax;
     if (!batch_dims(batch, m, n, mmax, nmax) || !valid_opts(o)) return 0;
+    if (backward_batched(batch, m, n)) return batched_adjoint_workspace_bytes(batch, m, n);
     WsArena ar(nullptr, SIZE_MAX);
     BwdWs w;
     bwd_layout(ar, mmax, nmax, w);
@@ -951,18 +961,25 @@ int lls_backward(int batch, const int* m, const int* n, const float* const* A, c
         if (lda[i] < m[i] || ldr[i] < n[i] || ldga[i] < m[i]) return LLS_ERR_ARG;
     }
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
+    const double tol = o.target == LLS_TARGET_FP32 ? 1e-7 : 1e-13;
+    trace_mark(stream);
+    if (backward_batched(batch, m, n)) {
+        const int r = batched_adjoint(batch, m, n, A, lda, b, x, R, ldr, grad_x, grad_A, ldga, grad_b, ws,
+                                      ws_bytes, tol, o.max_iter, stream);
+        trace_flush();
+        return r;
+    }
     WsArena ar(ws, ws_bytes);
     BwdWs w;
     bwd_layout(ar, mmax, nmax, w);
     if (!ar.ok) return LLS_ERR_WORKSPACE;
-    trace_mark(stream);
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, stream));
     for (int i = 0; i < batch; ++i) {
         LLS_TRY(tri_inverse(R[i], ldr[i], n[i], o.panel_width, w.Minv, w.Mt, w.tmp, w.err, stream));
         AdjointCall c;
         c.m = m[i]; c.n = n[i]; c.A = A[i]; c.lda = lda[i]; c.b = b[i]; c.x = x[i]; c.g = grad_x[i];
         c.Minv = w.Minv; c.Mt = w.Mt; c.z = w.z; c.gA = grad_A[i]; c.ldga = ldga[i]; c.gb = grad_b[i];
-        c.tol = o.target == LLS_TARGET_FP32 ? 1e-7 : 1e-13;
+        c.tol = tol;
         c.max_iter = o.max_iter;
         c.scratch = w.ks; c.scratch_bytes = w.kb; c.dev_err = w.err; c.dev_info = w.dinfo;
         LLS_TRY(adjoint_solve(c, stream));

@@ -611,6 +611,126 @@ batched_lls_kernel(BArgs g) {
     }
 }
 
+// ---- the adjoint of a batch of solves, one persistent launch ------------------------------
+// Each CTA takes whole problems from the work queue and runs, for its problem, the textbook
+// sensitivity of x* = (A^T A)^{-1} A^T b (the paper has none): M = R^{-1} from the solve's R
+// (the block inverse above), z = (A^T A)^{-1} g by CG preconditioned with M M^T,
+//   res = g, u = M^T res, y = M u, rho = ||u||^2, p = y
+//   loop: q = A p, w = A^T q, alpha = rho / (p . w), z += alpha p, res -= alpha w,
+//         u = M^T res, rho' = ||u||^2, beta = rho' / rho, y = M u, p = y + beta p
+//   until ||M^T res|| <= tol ||M^T g||,
+// then r = b - A x, dL/db = A z and dL/dA = r z^T - (A z) x^T written in one sweep. The
+// products with A and M use the same compensated (double-float) dot products as the solve.
+struct AProb {
+    int m, n, lda, ldr, ldga;
+    const float* A; const double* b; const double* x; const double* g; const float* Rin;
+    float* gA; double* gb;
+    float* R; float* M; float* Mt; float* tmp;   // n x n, ld n (R: the copy of Rin)
+    double* vec;                                 // res, u, y, p, w, z (n each); q, r, az (m each)
+    double* info;                                // 16 doubles: iterations, status, ...
+};
+
+struct AArgs {
+    AProb* probs;
+    const int* order;
+    int count;
+    unsigned* queue;
+    double tol;
+    int max_iter;
+};
+
+__device__ void adjoint_cta(const AProb& Q, const AArgs& g, BSmem& sm) {
+    const int m = Q.m, n = Q.n;
+    // the building blocks above take their sizes and pointers from a BProb
+    BProb P;
+    P.m = m; P.n = n; P.lda = Q.lda; P.A = Q.A; P.R = Q.R; P.M = Q.M; P.Mt = Q.Mt; P.tmp = Q.tmp;
+    double* res = Q.vec;
+    double* u = res + n;
+    double* y = u + n;
+    double* p = y + n;
+    double* w = p + n;
+    double* z = w + n;
+    double* q = z + n;
+    double* r = q + m;
+    double* az = r + m;
+    for (size_t e = threadIdx.x; e < (size_t)n * n; e += kPanelThreads) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        Q.R[e] = i <= j ? Q.Rin[(size_t)i + (size_t)j * Q.ldr] : 0.f;
+    }
+    __syncthreads();
+    int* perr = reinterpret_cast<int*>(Q.info + 12);
+    if (threadIdx.x == 0) *perr = 0;
+    __syncthreads();
+    trinv_cta(P, sm, perr);
+    if (*(volatile int*)perr != 0) {
+        if (threadIdx.x == 0) { Q.info[0] = 0; Q.info[7] = -2; }
+        __syncthreads();
+        return;
+    }
+    for (int j = threadIdx.x; j < n; j += kPanelThreads) { res[j] = Q.g[j]; z[j] = 0.0; }
+    stage(res, n, sm);
+    double rho = cta_sum(cta_tri_gemv(Q.M, n, true, u, sm), sm);
+    const double rho0 = rho;
+    stage(u, n, sm);
+    cta_tri_gemv(Q.Mt, n, false, y, sm);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += kPanelThreads) p[j] = y[j];
+    int iters = 0, status = rho0 > 0.0 ? 1 : 0;
+    while (status != 0 && iters < g.max_iter) {
+        stage(p, n, sm);
+        cta_a_times(P, q, nullptr, sm);                 // q = A p
+        stage(q, m, sm);
+        cta_at_times(P, w, sm);                         // w = A^T q
+        __syncthreads();
+        double pw = 0.0;
+        for (int j = threadIdx.x; j < n; j += kPanelThreads) pw += p[j] * w[j];
+        pw = cta_sum(pw, sm);
+        ++iters;
+        if (!(pw > 0.0)) { status = 0; break; }
+        const double alpha = rho / pw;
+        for (int j = threadIdx.x; j < n; j += kPanelThreads) { z[j] += alpha * p[j]; res[j] -= alpha * w[j]; }
+        stage(res, n, sm);
+        const double rnew = cta_sum(cta_tri_gemv(Q.M, n, true, u, sm), sm);
+        const double beta = rnew / rho;
+        rho = rnew;
+        stage(u, n, sm);
+        cta_tri_gemv(Q.Mt, n, false, y, sm);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += kPanelThreads) p[j] = y[j] + beta * p[j];
+        if (sqrt(rho) <= g.tol * sqrt(rho0)) status = 0;
+    }
+    // r = b - A x, A z
+    stage(Q.x, n, sm);
+    cta_a_times(P, r, Q.b, sm);
+    stage(z, n, sm);
+    cta_a_times(P, az, nullptr, sm);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kPanelThreads) Q.gb[i] = az[i];
+    // dL/dA = r z^T - (A z) x^T, column by column (coalesced over rows)
+    for (int j = 0; j < n; ++j) {
+        const double zj = z[j], xj = Q.x[j];
+        float* col = Q.gA + (size_t)j * Q.ldga;
+        for (int i = threadIdx.x; i < m; i += kPanelThreads) col[i] = (float)(r[i] * zj - az[i] * xj);
+    }
+    if (threadIdx.x == 0) { Q.info[0] = iters; Q.info[7] = status; }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPanelThreads, 1)
+batched_adjoint_kernel(AArgs g) {
+    extern __shared__ __align__(16) unsigned char b_smem_raw[];
+    BSmem& sm = *reinterpret_cast<BSmem*>(b_smem_raw);
+    for (;;) {
+        if (threadIdx.x == 0) sm.next = (int)atomicAdd(g.queue, 1u);
+        __syncthreads();
+        const int k = sm.next;
+        __syncthreads();
+        if (k >= g.count) return;
+        const AProb Q = g.probs[g.order[k]];
+        adjoint_cta(Q, g, sm);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
@@ -729,6 +849,97 @@ int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_o
     kern<<<grid, kPanelThreads, smem, st>>>(g);
     LLS_LAUNCH_CHECK("batched_lls", st);
     return LLS_OK;
+}
+
+}  // namespace lls
+
+// ---- the batched adjoint: workspace, upload and launch -----------------------------------
+namespace lls {
+
+static size_t adj_prob_bytes(int m, int n) {
+    const size_t n2 = (size_t)n * n;
+    return 4 * align_up(n2 * 4, 256) + align_up(((size_t)3 * m + 6 * n) * 8, 256) + 256;
+}
+
+struct ALayout {
+    size_t table, order, queue, info, total;
+    std::vector<size_t> off;
+};
+
+static void a_layout(int batch, const int* m, const int* n, ALayout& L) {
+    size_t o = 0;
+    L.table = o; o = align_up(o + sizeof(AProb) * batch, 256);
+    L.order = o; o = align_up(o + sizeof(int) * batch, 256);
+    L.queue = o; o = align_up(o + 256, 256);
+    L.info = o; o = align_up(o + sizeof(double) * 16 * batch, 256);
+    L.off.resize(batch);
+    for (int i = 0; i < batch; ++i) { L.off[i] = o; o += adj_prob_bytes(m[i], n[i]); }
+    L.total = o;
+}
+
+size_t batched_adjoint_workspace_bytes(int batch, const int* m, const int* n) {
+    ALayout L;
+    a_layout(batch, m, n, L);
+    return L.total;
+}
+
+int batched_adjoint(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                    const double* const* b, const double* const* x, const float* const* R, const int* ldr,
+                    const double* const* grad_x, float* const* grad_A, const int* ldga, double* const* grad_b,
+                    void* ws, size_t ws_bytes, double tol, int max_iter, cudaStream_t st) {
+    ALayout L;
+    a_layout(batch, m, n, L);
+    if (L.total > ws_bytes) return LLS_ERR_WORKSPACE;
+    char* base = (char*)ws;
+    std::vector<AProb> table(batch);
+    std::vector<int> order(batch);
+    for (int i = 0; i < batch; ++i) {
+        AProb& Q = table[i];
+        const size_t n2 = (size_t)n[i] * n[i];
+        char* q = base + L.off[i];
+        auto take = [&](size_t bytes) { char* r = q; q += align_up(bytes, 256); return r; };
+        Q.m = m[i]; Q.n = n[i]; Q.lda = lda[i]; Q.ldr = ldr[i]; Q.ldga = ldga[i];
+        Q.A = A[i]; Q.b = b[i]; Q.x = x[i]; Q.g = grad_x[i]; Q.Rin = R[i];
+        Q.gA = grad_A[i]; Q.gb = grad_b[i];
+        Q.R = (float*)take(n2 * 4); Q.M = (float*)take(n2 * 4); Q.Mt = (float*)take(n2 * 4);
+        Q.tmp = (float*)take(n2 * 4);
+        Q.vec = (double*)take(((size_t)3 * m[i] + 6 * n[i]) * 8);
+        Q.info = (double*)(base + L.info) + (size_t)16 * i;
+        order[i] = i;
+    }
+    // largest first: CG costs about m n per iteration, the inverse about n^3 / 3
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (double)m[a] * n[a] * 40.0 + (double)n[a] * n[a] * n[a] > (double)m[c] * n[c] * 40.0 + (double)n[c] * n[c] * n[c];
+    });
+    LLS_CUDA_TRY(cudaMemcpyAsync(base + L.table, table.data(), sizeof(AProb) * batch, cudaMemcpyHostToDevice, st));
+    LLS_CUDA_TRY(cudaMemcpyAsync(base + L.order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, st));
+    LLS_CUDA_TRY(cudaMemsetAsync(base + L.queue, 0, 256, st));
+    LLS_CUDA_TRY(cudaMemsetAsync(base + L.info, 0, sizeof(double) * 16 * batch, st));
+    AArgs g;
+    g.probs = (AProb*)(base + L.table);
+    g.order = (const int*)(base + L.order);
+    g.count = batch;
+    g.queue = (unsigned*)(base + L.queue);
+    g.tol = tol;
+    g.max_iter = max_iter;
+    const size_t smem = sizeof(BSmem);
+    int dev = 0, sms = 0, per = 0;
+    LLS_CUDA_TRY(cudaGetDevice(&dev));
+    LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LLS_CUDA_TRY(cudaFuncSetAttribute(batched_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_adjoint_kernel, kPanelThreads, smem));
+    if (per < 1) return LLS_ERR_UNSUPPORTED;
+    int grid = sms * per;
+    if (grid > batch) grid = batch;
+    batched_adjoint_kernel<<<grid, kPanelThreads, smem, st>>>(g);
+    LLS_LAUNCH_CHECK("batched_adjoint", st);
+    return LLS_OK;
+}
+
+double* batched_adjoint_info_ptr(void* ws, int batch, const int* m, const int* n) {
+    ALayout L;
+    a_layout(batch, m, n, L);
+    return (double*)((char*)ws + L.info);
 }
 
 }  // namespace lls

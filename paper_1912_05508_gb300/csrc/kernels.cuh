@@ -174,6 +174,12 @@ int batched_upload(int batch, const int* m, const int* n, const float* const* A,
                    void* ws, size_t ws_bytes, cudaStream_t st);
 int batched_execute(int batch, const int* m, const int* n, void* ws, const lls_options& o, int ctas_per_sm,
                     cudaStream_t st);
+// The adjoint of a batch of solves in one persistent launch (each CTA whole problems).
+size_t batched_adjoint_workspace_bytes(int batch, const int* m, const int* n);
+int batched_adjoint(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                    const double* const* b, const double* const* x, const float* const* R, const int* ldr,
+                    const double* const* grad_x, float* const* grad_A, const int* ldga, double* const* grad_b,
+                    void* ws, size_t ws_bytes, double tol, int max_iter, cudaStream_t st);
 
 // ---- graph replay (graph.cu) -----------------------------------------------------------------
 // Identity of one call: plain-old-data, compared bytewise (zero-initialize before filling).

@@ -592,8 +592,9 @@ def _make_function():
     class LLSFunction(torch.autograd.Function):
         """x = argmin ||A x - b||_2 for A (m, n) or a batch (B, m, n); differentiable in A and b.
 
-        Forward: lls_solve (RGSQRF + preconditioned CGLS). Backward: lls_backward (the
-        textbook adjoint, with z = (A^T A)^{-1} g from CG preconditioned by the forward R)."""
+        Forward: lls_solve (RGSQRF + preconditioned CGLS), or lls_solve_batched for a batch (one
+        persistent launch). Backward: lls_backward (the textbook adjoint, with
+        z = (A^T A)^{-1} g from CG preconditioned by the forward R; a batch in one launch)."""
 
         @staticmethod
         def forward(ctx, A, b, opts):
@@ -601,13 +602,22 @@ def _make_function():
             As = list(A) if batched else [A]
             bs = list(b) if batched else [b]
             Acm = [colmajor(a.detach(), device=a.device) for a in As]
-            xs, Rs = [], []
-            for a_cm, bv in zip(Acm, bs):
-                x, info, R = solve(a_cm, bv.detach(), want_r=True, **opts)
-                if info["status_code"] < 0:
-                    raise LLSError(info["status_code"], "lls_solve")
-                xs.append(x)
-                Rs.append(R)
+            if batched and len(As) > 1:
+                # the whole batch in one persistent launch
+                bopts = {k: v for k, v in opts.items() if k in ("prec", "target", "tol", "max_iter")}
+                xs, infos, Rs = solve_batched(Acm, [bv.detach() for bv in bs], want_r=True,
+                                              **{"target": "fp64", **bopts})
+                for info in infos:
+                    if info["status"] < 0:
+                        raise LLSError(info["status"], "lls_solve_batched")
+            else:
+                xs, Rs = [], []
+                for a_cm, bv in zip(Acm, bs):
+                    x, info, R = solve(a_cm, bv.detach(), want_r=True, **opts)
+                    if info["status_code"] < 0:
+                        raise LLSError(info["status_code"], "lls_solve")
+                    xs.append(x)
+                    Rs.append(R)
             ctx.batched = batched
             ctx.opts = opts
             ctx.bdtype = b.dtype

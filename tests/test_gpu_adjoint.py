@@ -82,3 +82,29 @@ def test_gradient_of_general_loss_matches_finite_differences():
         xm = lls.lstsq(At, torch.from_numpy(b - e).cuda()).detach()
         fd.append(float(((xp - xm) * w).sum()) / (2 * h))
     np.testing.assert_allclose(bt.grad.cpu().numpy()[:5], fd, rtol=1e-6, atol=1e-9)
+
+
+def test_batched_adjoint_uneven_shapes_one_launch():
+    # a batch of uneven problems: the forward solve and the adjoint each run as one persistent
+    # launch (each CTA whole problems); every problem's gradient matches the closed form
+    rng = np.random.default_rng(11)
+    probs = []
+    for i in range(12):
+        n = int(rng.integers(20, 200))
+        m = int(rng.integers(4 * n, 3000))
+        probs.append(synth.svd_lls(m, n, "geometric", 10.0 ** rng.uniform(1, 3), seed=300 + i))
+    As = [lls.colmajor(q.A) for q in probs]
+    bs = [torch.from_numpy(q.b).cuda() for q in probs]
+    xs, infos, Rs = lls.solve_batched(As, bs, target="fp64", want_r=True)
+    assert all(i["status"] == 0 for i in infos)
+    gxs = [2 * x for x in xs]
+    torch.cuda.synchronize()
+    c0 = lls.lls_kernel_launch_count()
+    gAs, gbs = lls.backward(As, bs, xs, Rs, gxs)
+    torch.cuda.synchronize()
+    assert lls.lls_kernel_launch_count() - c0 == 1
+    for i, q in enumerate(probs):
+        xo = direct.lls(q.A, q.b)
+        gA, gb = adjoint.lls_grad(q.A.astype(np.float64), q.b, xo, 2 * xo)
+        assert rel(gAs[i].cpu().numpy(), gA) <= 1e-6, i
+        assert rel(gbs[i].cpu().numpy(), gb) <= 1e-6, i
