@@ -21,6 +21,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-Xptxas", "-warn-spills", "-I", INCLUDE]
+# extra preprocessor definitions for experiments (e.g. "-DLLS_CGS_GROUP_LEAF=2"); empty by default
+CFLAGS += os.environ.get("LLS_NVCC_EXTRA", "").split()
 
 
 def _sources():

@@ -164,8 +164,8 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.qbuf = ar.take<float>(qb);
     w.cnt = ar.take<unsigned>(cw);
     w.cnt_words = cw;
-    w.colmax = ar.take<unsigned>((size_t)n + 2);
-    w.nbar = w.colmax ? w.colmax + n : nullptr;
+    w.colmax = ar.take<unsigned>((size_t)n);
+    w.nbar = ar.take<unsigned>(4);      // the grid barrier's 64-bit word, 8-byte aligned
     w.err = ar.take<int>(16);
     w.dinfo = ar.take<double>(16);
     w.red = ar.take<double>(8192);
@@ -296,7 +296,8 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
                   const Knobs& k, QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
-    LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * ((size_t)n + 2), st));
+    LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * (size_t)n, st));
+    LLS_CUDA_TRY(cudaMemsetAsync(w.nbar, 0, sizeof(unsigned) * 4, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
     if (!gate) LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));

@@ -163,34 +163,38 @@ __device__ __forceinline__ float warp_max_f(float v) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Grid-wide barrier for cooperative (co-resident) launches. Sense by generation counter;
-// the wait is bounded by kSpinLimitNs, after which the error word is set and the caller
-// must return. `bar[0]` = arrival count, `bar[1]` = generation.
-// Returns false when the barrier timed out or an error was already flagged.
+// Grid-wide barrier for cooperative (co-resident) launches. bar[0..1] form one 8-byte-aligned
+// 64-bit word: the arrival count in its low half, the generation in its high half. A CTA
+// arrives with one atomic add, which also tells it the generation it waits to see change; the
+// last arrival resets the count and advances the generation with a single add of
+// 2^32 - nblocks. The count is left at zero. The wait is bounded by kSpinLimitNs, after which
+// the error word is set and the caller must return. Returns false when the barrier timed out
+// or an error was already flagged.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        unsigned g = *gen;
+        unsigned long long* word = reinterpret_cast<unsigned long long*>(bar);
         __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
+        const unsigned long long old = atomicAdd(word, 1ull);
+        const unsigned gen = (unsigned)(old >> 32);
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        if ((unsigned)(old & 0xffffffffull) == nblocks - 1) {
+            atomicAdd(word, (1ull << 32) - (unsigned long long)nblocks);
         } else {
-            unsigned long long t0 = globaltimer_ns();
-            while (*gen == g) {
+            const volatile unsigned* genp = bar + 1;
+            const unsigned long long t0 = globaltimer_ns();
+            int spins = 0;
+            while (*genp == gen) {
+                if (++spins < 64) continue;         // a first short burst of polls, then paced
                 if (*(volatile int*)err != DEV_OK) { ok = 0; break; }
                 if (globaltimer_ns() - t0 > kSpinLimitNs) {
                     atomicCAS(err, DEV_OK, DEV_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();

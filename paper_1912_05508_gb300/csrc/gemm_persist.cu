@@ -31,27 +31,29 @@ namespace {
 constexpr int kPM = 128;                     // tile rows (M)
 constexpr int kPK = 64;                      // K per stage: 128-byte rows of 2-byte elements
 constexpr int kPThreads = 256;
-constexpr int kCCols = 32;                   // A2 columns per chunk
 constexpr int kABytes = kPM * kPK * 2;       // 16 KB
-constexpr int kCBytes = kPM * kCCols * 4;    // 16 KB
 
 enum { PE_PARTIAL = 0, PE_UPDATE = 1 };
 
 // Tile width BN (128 or 256 columns: one accumulator of BN TMEM columns, two of them), pipeline
 // depth and A2 chunk buffers, sized to the 227 KB of shared memory a CTA may hold. Wider tiles
 // halve the operand traffic from L2 per flop, which the 128 x 128 tiles are bound by.
+// The wide update keeps four operand stages (three left the tensor pipe idle half the time
+// while operands arrived) and moves A2 in 16-column chunks through four buffers.
 template <int EPI, int BN> struct PCfg {
     static constexpr int bbytes = BN * kPK * 2;
     static constexpr int stage_bytes = kABytes + bbytes;
-    static constexpr int stages = EPI == PE_UPDATE ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : 6);
+    static constexpr int stages = EPI == PE_UPDATE ? 4 : (BN == 256 ? 4 : 6);
+    static constexpr int ccols = (EPI == PE_UPDATE && BN == 256) ? 16 : 32;   // A2 columns per chunk
+    static constexpr int cbytes = kPM * ccols * 4;
     static constexpr int ring = EPI == PE_UPDATE ? (BN == 256 ? 4 : 6) : 0;
-    static constexpr int chunks = BN / kCCols;
+    static constexpr int chunks = BN / ccols;
 };
 
 template <int EPI, int BN>
 constexpr int p_smem_bytes() {
     using C = PCfg<EPI, BN>;
-    return 1024 + C::stages * C::stage_bytes + C::ring * kCBytes + 512;   // + barriers
+    return 1024 + C::stages * C::stage_bytes + C::ring * C::cbytes + 512;   // + barriers
 }
 
 struct PArgs {
@@ -97,11 +99,13 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     constexpr int NR = Cfg::ring > 0 ? Cfg::ring : 1;
     constexpr int kStageBytes = Cfg::stage_bytes;
     constexpr int kCChunks = Cfg::chunks;
+    constexpr int kCCols = Cfg::ccols;
+    constexpr int kCBytes = Cfg::cbytes;
     constexpr int kPN = BN;
     extern __shared__ __align__(1024) uint8_t p_smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)p_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* cring = smem + S * kStageBytes;
-    uint64_t* bars = (uint64_t*)(cring + Cfg::ring * kCBytes);
+    uint64_t* bars = (uint64_t*)(cring + Cfg::ring * Cfg::cbytes);
     // full[S], empty[S], tfull[2], tempty[2], cfull[NR], cempty[NR], cdone[NR], mmadone, sdone
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
     const uint32_t tfull0 = empty0 + 8 * S, tempty0 = tfull0 + 16;
@@ -230,13 +234,16 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const uint32_t tbase = tmem + ((uint32_t)(32 * e) << 16) + (uint32_t)(acc * kPN);
 #pragma unroll 1
             for (int c = 0; c < kCChunks; ++c, ++cc) {
-                float v[32];
-                if (ok) tmem_ld32(tbase + (uint32_t)(c * kCCols), v);
+                float v[kCCols];
+                if (ok) {
+                    if constexpr (kCCols == 32) tmem_ld32(tbase + (uint32_t)(c * kCCols), v);
+                    else tmem_ld16(tbase + (uint32_t)(c * kCCols), v);
+                }
                 if constexpr (EPI == PE_UPDATE) {
                     const int slot = cc % NR;
                     const uint32_t ph = (cc / NR) & 1;
                     if (ok && !mbar_wait(cfull0 + 8 * slot, ph, a.err)) ok = false;
-                    float* cb = reinterpret_cast<float*>(cring + slot * kCBytes);   // [32 columns][128 rows]
+                    float* cb = reinterpret_cast<float*>(cring + slot * kCBytes);   // [chunk columns][128 rows]
                     if (ok) {
 #pragma unroll
                         for (int j = 0; j < kCCols; ++j) {
@@ -352,7 +359,7 @@ static int update_persistent_bn(const UpdCall& c, cudaStream_t st) {
         tc_make_tmap(&tB, c.R12l, dt, 2, (uint64_t)c.w1, (uint64_t)c.w2, (uint64_t)c.ldrl, kPK, BN,
                      CU_TENSOR_MAP_SWIZZLE_128B) != LLS_OK ||
         tc_make_tmap(&tC, c.A2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)c.m, (uint64_t)c.w2, (uint64_t)c.ldw,
-                     kPM, kCCols, CU_TENSOR_MAP_SWIZZLE_NONE) != LLS_OK)
+                     kPM, PCfg<PE_UPDATE, BN>::ccols, CU_TENSOR_MAP_SWIZZLE_NONE) != LLS_OK)
         return LLS_ERR_UNSUPPORTED;
     PArgs a;
     a.M = c.m; a.N = c.w2;
