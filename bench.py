@@ -788,7 +788,9 @@ def main():
     # the autotuner measures the implementation choices for this shape once (cached on disk);
     # with panel_width 0 the solves below use its setting
     tune = None
-    if not args.no_autotune and args.pw == 0:
+    if args.no_autotune:
+        lls.load_tuning_cache(dev)      # settings an earlier run measured, if any
+    elif args.pw == 0:
         t0 = time.perf_counter()
         tune = lls.autotune(A, b, prec=args.prec, target=args.target, krylov=args.krylov, reorth=args.reorth,
                             reps=2)

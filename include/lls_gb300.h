@@ -333,11 +333,14 @@ int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void*
  *                        tiles, two accumulators), 1 one output tile per CTA, 2 the persistent
  *                        update with the one-tile-per-CTA projection;
  *   batched_ctas_per_sm  batched solver: CTAs per SM (0 = as many as fit);
+ *   krylov_ctas          CTAs of the Krylov kernel (0 = one per 64 Ki elements of A, at most
+ *                        three per SM; small problems may run faster on more);
  *   ms                   the measured device time of one call with this setting.
  *
  * lls_autotune: times lls_solve on the caller's problem (A m x n FP32 lda >= m, b m FP64, x n
  *   FP64 output, all device memory) for panel widths 8 / 16 / 32, then the node launch modes,
- *   then the product kernel (coordinate search; each candidate: one untimed call, then the
+ *   then the product kernel, then (when the problem would use fewer CTAs than SMs) wider
+ *   Krylov grids (coordinate search; each candidate: one untimed call, then the
  *   fastest of `reps`), records the fastest for (m, n, opts) and returns it in *best. opts as
  *   for lls_solve (opts->panel_width is ignored; x0 = LLS_X0_GIVEN is rejected). ws: at least
  *   lls_autotune_workspace_size(m, n, opts) bytes. Synchronizes `stream`. x receives the last
@@ -356,6 +359,7 @@ typedef struct {
     int node_mode;
     int gemm_kernel;
     int batched_ctas_per_sm;
+    int krylov_ctas;
     float ms;
 } lls_tuning;
 size_t lls_autotune_workspace_size(int m, int n, const lls_options* opts);

@@ -22,6 +22,8 @@
 namespace lls {
 
 int fro_sumsq(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t st);
+int copy_fro_sumsq(const float* A, int lda, float* W, int ldw, int m, int n, double* part, double* out,
+                   cudaStream_t st);
 int simt_projection_f32(const float* Q1, const float* A2, int ldw, int m, int w1, int w2,
                         float* R12, int ldr, float* part, cudaStream_t st);
 int simt_update_f32(const float* Q1, int ldw, const float* R12, int ldr, float* A2, int m, int w1,
@@ -102,6 +104,7 @@ static void resolve_settings(const lls_options* opts, int kind, int m, int n, ll
     if (t.node_mode >= 0 && t.node_mode <= 2) k.node_mode = t.node_mode;
     if (t.gemm_kernel >= 0 && t.gemm_kernel <= 2) k.gemm_kernel = t.gemm_kernel;
     if (t.batched_ctas_per_sm >= 0) k.batched_ctas = t.batched_ctas_per_sm;
+    if (t.krylov_ctas >= 0) k.krylov_ctas = t.krylov_ctas;
 }
 
 // Panel widths an "auto" call may end up with; its workspace is sized for the largest need.
@@ -293,13 +296,17 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 }
 
 // gate: null when A is copied into W here; otherwise W fills in chunks on another stream.
+// anorm2: when non-null (and A is copied here), ||A||_F^2 is formed in the same pass as the copy.
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
-                  const Knobs& k, QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr) {
+                  const Knobs& k, QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr, double* anorm2 = nullptr) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * (size_t)n, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.nbar, 0, sizeof(unsigned) * 4, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
-    if (!gate) LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
+    if (!gate) {
+        if (anorm2) LLS_TRY(copy_fro_sumsq(A, lda, w.W, w.ldw, m, n, w.red, anorm2, st));
+        else LLS_TRY(copy_matrix(A, lda, w.W, w.ldw, m, n, st));
+    }
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * (size_t)n, (size_t)n, st));
     QrCtx c;
     c.m = m; c.n = n; c.pw = o.panel_width; c.lowp = lowp_code(o.gemm_prec); c.leaf = o.panel_leaf;
@@ -607,11 +614,13 @@ static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool captu
     const int m = c.m, n = c.n;
     if (ev) record_phase(ev[0], st, capturing);
     LLS_CUDA_TRY(cudaMemsetAsync(c.w.dinfo, 0, sizeof(double) * 16, st));
-    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.k, c.w, st, gate));
+    // without a gate A is copied into W here, and its norm comes with the copy
+    LLS_TRY(run_qr(m, n, c.A, c.lda, c.R, n, c.o, c.k, c.w, st, gate, gate ? nullptr : c.w.dinfo + 8));
     if (c.R_out) LLS_TRY(copy_matrix(c.R, n, c.R_out, c.ldr, n, n, st));
     LLS_TRY(check_diag(c.R, n, n, c.w.err, st));
     LLS_TRY(tri_inverse(c.R, n, n, c.o.panel_width, c.Minv, c.Mt, c.tmp, c.w.err, st));
-    LLS_TRY(fro_sumsq(c.A, c.lda, m, n, c.w.red, c.w.dinfo + 8, st));
+    // the host-operand solve copies A in chunks: its norm is formed here, with the same sums
+    if (gate) LLS_TRY(copy_fro_sumsq(c.A, c.lda, nullptr, 0, m, n, c.w.red, c.w.dinfo + 8, st));
     LLS_TRY(fro_sumsq(c.Minv, n, n, n, c.w.red + 4096, c.w.dinfo + 9, st));
     if (c.o.x0 == LLS_X0_DIRECT)   // x0 = R^{-1} Q^T b from the factors; W holds Q
         LLS_TRY(direct_start(c.w.W, c.w.ldw, m, n, c.b, c.Mt, c.x, c.ks, c.kb, st));
@@ -622,6 +631,7 @@ static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool captu
     kc.scratch = c.ks; kc.scratch_bytes = c.kb; kc.dev_err = c.w.err; kc.dev_info = c.w.dinfo;
     kc.x_zero = c.o.x0 == LLS_X0_ZERO ? 1 : 0;
     kc.hist = c.hist;
+    kc.ctas = c.k.krylov_ctas;
     LLS_TRY(krylov_solve(kc, st));
     if (ev) record_phase(ev[2], st, capturing);
     return LLS_OK;
@@ -1102,6 +1112,7 @@ static void knobs_to_tuning(int pw, const Knobs& k, float ms, lls_tuning& t) {
     t.node_mode = k.node_mode;
     t.gemm_kernel = k.gemm_kernel;
     t.batched_ctas_per_sm = k.batched_ctas;
+    t.krylov_ctas = k.krylov_ctas;
     t.ms = ms;
 }
 
@@ -1110,7 +1121,7 @@ int lls_tuning_set(int kind, int m, int n, const lls_options* opts, const lls_tu
     resolve(opts, o);
     if ((kind != 0 && kind != 1) || m < 1 || n < 1 || !t || !valid_opts(o)) return LLS_ERR_ARG;
     if (t->node_mode < 0 || t->node_mode > 2 || t->gemm_kernel < 0 || t->gemm_kernel > 2 ||
-        t->batched_ctas_per_sm < 0)
+        t->batched_ctas_per_sm < 0 || t->krylov_ctas < 0)
         return LLS_ERR_ARG;
     if (kind == 0) {
         lls_options c = o;
@@ -1193,6 +1204,19 @@ int lls_autotune(int m, int n, const float* A, int lda, const double* b, double*
         c.gemm_kernel = g;
         const float t = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, cur, c, reps, stream);
         if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; k = c; }
+    }
+    // small problems leave most SMs idle at the size-derived Krylov grid: try wider ones
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms > 0 && krylov_default_ctas(m, n) < sms) {
+        const int cand[4] = {16, 64, sms, 2 * sms};
+        for (int g : cand) {
+            if (g <= krylov_default_ctas(m, n)) continue;
+            Knobs c = k;
+            c.krylov_ctas = g;
+            const float t = trial_solve(m, n, A, lda, b, x, ws, ws_bytes, cur, c, reps, stream);
+            if (t >= 0.f && (tbest < 0.f || t < tbest)) { tbest = t; k = c; }
+        }
     }
     if (tbest < 0.f) return LLS_ERR_UNSUPPORTED;
     knobs_to_tuning(cur.panel_width, k, tbest, *best);

@@ -16,7 +16,7 @@ struct Knobs {
     int gemm_kernel = 0;    // products of the wide nodes: 0 persistent, 1 one output tile per CTA,
                             // 2 persistent update with the one-tile-per-CTA projection
     int batched_ctas = 0;   // batched solver: CTAs per SM, 0 = as many as fit
-    int reserved = 0;
+    int krylov_ctas = 0;    // CTAs of the Krylov kernel, 0 = from the problem size
 };
 Knobs default_knobs();
 
@@ -143,7 +143,10 @@ struct KrylovCall {
     double* dev_info;       // [iters, eta, fwd, res, atr, anorm, xnorm, status]
     int x_zero = 1;         // 1: start from x = 0; 0: start from the x the vector holds
     double* hist = nullptr; // kHistLen doubles: the stop quantity after each iteration, or null
+    int ctas = 0;           // CTAs of the persistent kernel, 0 = from the problem size
 };
+// CTAs the Krylov kernel takes for an m x n problem when not told otherwise.
+int krylov_default_ctas(int m, int n);
 constexpr int kHistLen = 4096;   // iterations whose stop quantity the history keeps
 // one_pass: room for the one-pass CGLS engine's row-block copy of A (used when n <= 4096).
 size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass = false);

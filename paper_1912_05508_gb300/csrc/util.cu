@@ -68,6 +68,63 @@ __global__ void sum_parts_kernel(const double* part, int np, double* out) {
     if (threadIdx.x == 0) *out = s;
 }
 
+// W = A (m x n) and, in the same pass over A, out = ||A||_F^2 (the copy into the work matrix
+// and the norm the stop test needs, one read of A instead of two). With W null only the norm is
+// formed, with the same partition and order of the sums. 16-byte loads and stores when both
+// matrices allow them.
+__global__ void copy_sumsq_kernel(const float* __restrict__ A, int lda, float* __restrict__ W, int ldw, int m, int n,
+                                  double* part, int vec4) {
+    // every thread takes groups of four consecutive rows, then the rows past the last group:
+    // the same sums in the same order whether the 16-byte path is taken or not
+    float hs = 0.f, hc = 0.f;
+    const int m4 = m >> 2;
+    for (int j = blockIdx.y; j < n; j += gridDim.y) {
+        const float* a = A + (size_t)j * lda;
+        float* w = W ? W + (size_t)j * ldw : nullptr;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m4; q += gridDim.x * blockDim.x) {
+            float4 v;
+            if (vec4) {
+                v = __ldg(reinterpret_cast<const float4*>(a) + q);
+                if (w) reinterpret_cast<float4*>(w)[q] = v;
+            } else {
+                v = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+                if (w) { w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w; }
+            }
+            dot2_step(hs, hc, v.x, v.x, 0.f);
+            dot2_step(hs, hc, v.y, v.y, 0.f);
+            dot2_step(hs, hc, v.z, v.z, 0.f);
+            dot2_step(hs, hc, v.w, v.w, 0.f);
+        }
+        for (int i = 4 * m4 + blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            const float v = a[i];
+            if (w) w[i] = v;
+            dot2_step(hs, hc, v, v, 0.f);
+        }
+    }
+    double s = warp_sum_d(join_df(hs, hc));
+    __shared__ double sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2];
+        part[blockIdx.x + blockIdx.y * gridDim.x] = t;
+    }
+}
+
+int copy_fro_sumsq(const float* A, int lda, float* W, int ldw, int m, int n, double* part, double* out,
+                   cudaStream_t st) {
+    if (m <= 0 || n <= 0) return LLS_OK;
+    const int vec4 = ((uintptr_t)A & 15) == 0 && (lda & 3) == 0 &&
+                     (!W || (((uintptr_t)W & 15) == 0 && (ldw & 3) == 0));
+    dim3 grid(ceil_div(m, 1024) < 8 ? ceil_div(m, 1024) : 8, n < 512 ? n : 512);
+    copy_sumsq_kernel<<<grid, 256, 0, st>>>(A, lda, W, ldw, m, n, part, vec4);
+    LLS_LAUNCH_CHECK("copy_sumsq", st);
+    sum_parts_kernel<<<1, 32, 0, st>>>(part, (int)(grid.x * grid.y), out);
+    LLS_LAUNCH_CHECK("sum_parts", st);
+    return LLS_OK;
+}
+
 // out = ||A||_F^2 (FP64, device). part: >= 64*64 doubles.
 int fro_sumsq(const float* A, int lda, int m, int n, double* part, double* out, cudaStream_t st) {
     dim3 grid(ceil_div(m, 256) < 8 ? ceil_div(m, 256) : 8, n < 512 ? n : 512);

@@ -54,7 +54,7 @@ class lls_info(C.Structure):
 
 class lls_tuning(C.Structure):
     _fields_ = [("panel_width", C.c_int), ("node_mode", C.c_int), ("gemm_kernel", C.c_int),
-                ("batched_ctas_per_sm", C.c_int), ("ms", C.c_float)]
+                ("batched_ctas_per_sm", C.c_int), ("krylov_ctas", C.c_int), ("ms", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -426,7 +426,7 @@ def load_tuning_cache(device=None, path=None):
             for f, v in opts.items():
                 setattr(o, f, v)
             rec = lls_tuning(int(t["panel_width"]), int(t["node_mode"]), int(t["gemm_kernel"]),
-                             int(t["batched_ctas_per_sm"]), float(t["ms"]))
+                             int(t["batched_ctas_per_sm"]), int(t.get("krylov_ctas", 0)), float(t["ms"]))
             if lls_tuning_set(kind, m, n, o, rec) == 0:
                 count += 1
     return count

@@ -15,7 +15,7 @@ import json
 import os
 import tempfile
 
-FIELDS = ("panel_width", "node_mode", "gemm_kernel", "batched_ctas_per_sm", "ms")
+FIELDS = ("panel_width", "node_mode", "gemm_kernel", "batched_ctas_per_sm", "krylov_ctas", "ms")
 OPT_FIELDS = ("gemm_prec", "target", "krylov", "reorth", "panel_leaf")
 
 

@@ -134,23 +134,24 @@ def test_tuning_table_set_get_clear(lib):
     lls.lls_tuning_clear()
     o = lls.make_options(prec="fp16", target="fp64")
     assert lls.lls_tuning_get(0, 32768, 4096, o) is None
-    t = lls.lls_tuning(8, 1, 1, 0, 12.5)
+    t = lls.lls_tuning(8, 1, 1, 0, 0, 12.5)
     assert lls.lls_tuning_set(0, 32768, 4096, o, t) == 0
     got = lls.lls_tuning_get(0, 32768, 4096, o)
     assert got is not None and got.as_dict() == {"panel_width": 8, "node_mode": 1, "gemm_kernel": 1,
-                                                 "batched_ctas_per_sm": 0, "ms": 12.5}
+                                                 "batched_ctas_per_sm": 0, "krylov_ctas": 0, "ms": 12.5}
     # another precision or shape is another key
     assert lls.lls_tuning_get(0, 32768, 4096, lls.make_options(prec="bf16")) is None
     assert lls.lls_tuning_get(0, 32768, 2048, o) is None
     # the panel width does not take part in the key (it is what the setting chooses)
     assert lls.lls_tuning_get(0, 32768, 4096, lls.make_options(prec="fp16", panel_width=32)) is not None
     # invalid settings and kinds
-    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(40, 0, 0, 0, 1.0)) == -1
-    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 3, 0, 0, 1.0)) == -1
-    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 0, 3, 0, 1.0)) == -1
-    assert lls.lls_tuning_set(2, 100, 10, o, lls.lls_tuning(16, 0, 0, 0, 1.0)) == -1
-    assert lls.lls_tuning_set(0, 100, 10, lls.make_options(prec="fp8"), lls.lls_tuning(8, 0, 0, 0, 1.0)) == -1
-    assert lls.lls_tuning_set(1, 4096, 512, o, lls.lls_tuning(16, 0, 0, 2, 9.0)) == 0
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(40, 0, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 3, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 0, 3, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, o, lls.lls_tuning(16, 0, 0, 0, -1, 1.0)) == -1
+    assert lls.lls_tuning_set(2, 100, 10, o, lls.lls_tuning(16, 0, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(0, 100, 10, lls.make_options(prec="fp8"), lls.lls_tuning(8, 0, 0, 0, 0, 1.0)) == -1
+    assert lls.lls_tuning_set(1, 4096, 512, o, lls.lls_tuning(16, 0, 0, 2, 0, 9.0)) == 0
     assert lls.lls_tuning_get(1, 4096, 512, o).batched_ctas_per_sm == 2
     lls.lls_tuning_clear()
     assert lls.lls_tuning_get(0, 32768, 4096, o) is None and lls.lls_tuning_get(1, 4096, 512, o) is None

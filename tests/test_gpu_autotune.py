@@ -53,7 +53,7 @@ def test_every_recorded_setting_solves_to_the_oracle(cache, pw, node_mode, gemm_
     # whatever the tuner picks, the solve is the same method: each setting reaches the target
     p = synth.svd_lls(6000, 320, "geometric", 1e3, seed=72)
     o = lls.make_options()
-    assert lls.lls_tuning_set(0, 6000, 320, o, lls.lls_tuning(pw, node_mode, gemm_kernel, 0, 1.0)) == 0
+    assert lls.lls_tuning_set(0, 6000, 320, o, lls.lls_tuning(pw, node_mode, gemm_kernel, 0, 0, 1.0)) == 0
     x, info = lls.solve(lls.colmajor(p.A), torch.from_numpy(p.b).cuda())
     assert info["status"] == 0, info
     xs = direct.lls(p.A, p.b)

@@ -6,8 +6,8 @@ import os
 from paper_1912_05508_gb300 import tuning
 
 OPTS = {"gemm_prec": 0, "target": 1, "krylov": 0, "reorth": 0, "panel_leaf": 0}
-T1 = {"panel_width": 16, "node_mode": 0, "gemm_kernel": 0, "batched_ctas_per_sm": 0, "ms": 21.5}
-T2 = {"panel_width": 8, "node_mode": 1, "gemm_kernel": 1, "batched_ctas_per_sm": 2, "ms": 3.25}
+T1 = {"panel_width": 16, "node_mode": 0, "gemm_kernel": 0, "batched_ctas_per_sm": 0, "krylov_ctas": 0, "ms": 21.5}
+T2 = {"panel_width": 8, "node_mode": 1, "gemm_kernel": 1, "batched_ctas_per_sm": 2, "krylov_ctas": 64, "ms": 3.25}
 
 
 def test_key_round_trip():
