@@ -1257,6 +1257,14 @@ size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass) {
     return k_layout(m, n, grid, one_pass && tiled_engine_allowed(n)).total;
 }
 
+// One CTA per 64 Ki elements of A (the passes' work items are 1024-row tiles); the caller
+// caps it at three CTAs per SM.
+int krylov_default_ctas(int m, int n) {
+    const long long work = (long long)m * n;
+    const long long g = (work + (1 << 16) - 1) >> 16;
+    return g < 1 ? 1 : (g > (1 << 20) ? (1 << 20) : (int)g);
+}
+
 static int fused_nc(int n) {
     const int need = ceil_div(n, kKThreads);
     if (need <= 1) return 1;
@@ -1281,8 +1289,7 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
         const int nblk = ceil_div(c.m, kRB);
         grid = ceil_div(nblk, 8);            // at least 8 row blocks per CTA
     } else {
-        const long long work = (long long)c.m * c.n;
-        grid = (int)((work + (1 << 16) - 1) >> 16);
+        grid = c.ctas > 0 ? c.ctas : krylov_default_ctas(c.m, c.n);
     }
     if (grid < 1) grid = 1;
     if (grid > maxg) grid = maxg;
