@@ -41,7 +41,8 @@ typedef enum {
     LLS_ERR_WORKSPACE = -4,    /* workspace too small or misaligned */
     LLS_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired (the kernel returned early) */
     LLS_ERR_UNSUPPORTED = -6,  /* valid but unimplemented option combination */
-    LLS_ERR_TOO_LARGE = -7     /* sizes need more scratch than a fixed-scratch entry point holds */
+    LLS_ERR_TOO_LARGE = -7,    /* sizes need more scratch than a fixed-scratch entry point holds */
+    LLS_ERR_BOUNDS = -8        /* debug build only: an index check failed and its access was skipped */
 } lls_status;
 
 /* Precision of the two tensor-core products of each recursion step (Alg. 2: projection and update).
@@ -125,7 +126,9 @@ unsigned long long lls_kernel_launch_count(void);
  *  opts     may be NULL (defaults). Only gemm_prec, panel_width and leaf_rows are used.
  * Errors: LLS_ERR_ARG (n < 1, m < n, ld too small, null A/R/ws), LLS_ERR_WORKSPACE,
  *         LLS_ERR_UNSUPPORTED, LLS_ERR_CUDA. Rank deficiency is not an error here:
- *         it shows up as a zero diagonal entry of R.
+ *         it shows up as a zero diagonal entry of R. The call does not synchronize, so a
+ *         device-side failure (a bounded wait that gave up) cannot be returned: it leaves
+ *         NaN on the whole diagonal of R instead.
  * -------------------------------------------------------------------------- */
 size_t qr_factor_workspace_size(int m, int n, const lls_options* opts);
 int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
@@ -383,6 +386,32 @@ void lls_tuning_clear(void);
  * the barrier completed (a defect), LLS_ERR_ARG or LLS_ERR_CUDA otherwise.
  * -------------------------------------------------------------------------- */
 int lls_selftest_wait_timeout(void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Debug build (no counterpart in the paper). The library also builds as
+ * liblls_gb300_debug.so, with the same ABI, where the kernels' global-memory accesses carry
+ * index checks: a failed check skips its access and records its source line. The compute
+ * entry points (qr_factor, lls_solve, lls_solve_host, lls_solve_batched, lls_backward,
+ * lls_panel_qr, lls_panel_block_qr, lls_lowp_projection, lls_lowp_update,
+ * lls_householder_solve) clear the records before the work, synchronize `stream` after it
+ * and return LLS_ERR_BOUNDS (naming the file and line on stderr) if a check failed; debug
+ * calls therefore cannot be captured into a caller's CUDA graph. The checks do not change
+ * the arithmetic: the two builds give bitwise equal results.
+ * lls_debug_build: 1 in the debug build, 0 in the release build.
+ * lls_debug_inject: arms a planted fault of the one-level CAQR panel kernels (which factor the
+ *   panels of up to 65536 rows), for tests of the failure paths, or disarms it (mode 0):
+ *   mode 1: every store of Q is addressed one panel height past the last row; the index
+ *           checks reject each such store, so none happens and Q keeps its previous contents;
+ *           the call returns LLS_ERR_BOUNDS;
+ *   mode 2: the grid barrier between the leaves and the tree waits for one CTA more than the
+ *           grid holds; each CTA's bounded wait gives up after about 2 s and sets the device
+ *           error word, and the kernels after it return at their first wait: lls_solve returns
+ *           LLS_ERR_TIMEOUT, qr_factor leaves NaN on the diagonal of R.
+ *   Nothing faults in either mode. Returns LLS_OK, LLS_ERR_ARG (mode not 0, 1 or 2),
+ *   LLS_ERR_UNSUPPORTED in the release build, LLS_ERR_CUDA if the flag could not be set.
+ * -------------------------------------------------------------------------- */
+int lls_debug_build(void);
+int lls_debug_inject(int mode);
 
 /* ---------------------------------------------------------------------------
  * Plain Householder least squares (Alg. 1, Sec. 3.2.2): the comparison solver the

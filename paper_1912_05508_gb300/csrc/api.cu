@@ -337,6 +337,15 @@ extern std::atomic<unsigned long long> g_launches;
 
 using namespace lls;
 
+// LLS_DEBUG builds: clear the translation units' index-check records before a public call
+// and read them after it; the release build compiles both to nothing.
+#define LLS_DEBUG_BEGIN(st) do { if (LLS_DEBUG) ::lls::debug_reset(st); } while (0)
+static int debug_end(int status, cudaStream_t st) {
+    if (!LLS_DEBUG) return status;
+    const int d = ::lls::debug_collect(st);
+    return d != LLS_OK ? d : status;
+}
+
 extern "C" {
 
 unsigned long long lls_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -364,6 +373,7 @@ const char* lls_status_string(int s) {
         case LLS_ERR_TIMEOUT: return "device wait timed out";
         case LLS_ERR_UNSUPPORTED: return "unsupported option combination";
         case LLS_ERR_TOO_LARGE: return "sizes exceed the fixed scratch of this entry point";
+        case LLS_ERR_BOUNDS: return "index check failed (debug build)";
         default: return "unknown status";
     }
 }
@@ -403,7 +413,7 @@ static int enqueue_qr(void* p, cudaStream_t st, cudaEvent_t*, bool) {
     QrCall& c = *(QrCall*)p;
     LLS_TRY(run_qr(c.m, c.n, c.A, c.lda, c.R, c.ldr, c.o, c.k, c.w, st));
     if (c.Q) LLS_TRY(copy_matrix(c.w.W, c.w.ldw, c.Q, c.ldq, c.m, c.n, st));
-    return LLS_OK;
+    return poison_diag_on_error(c.R, c.ldr, c.n, c.w.err, st);   // a wait that gave up: NaN diagonal
 }
 
 static int current_device() {
@@ -412,7 +422,7 @@ static int current_device() {
     return d;
 }
 
-int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
+static int qr_factor_impl(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
               void* ws, size_t ws_bytes, const lls_options* opts, cudaStream_t stream) {
     lls_options o;
     Knobs k;
@@ -443,7 +453,7 @@ size_t lls_lowp_projection_workspace_size(int m, int w1, int w2) {
     return align_up(sizeof(float) * proj_partial_floats(m, w1, w2), 256) + 256;
 }
 
-int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l, int ldh,
+static int lls_lowp_projection_impl(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l, int ldh,
                         const int* e, float* R12, int ldr, void* R12l, int ldrl, int* f, void* ws,
                         size_t ws_bytes, cudaStream_t stream) {
     if (m < 1 || w1 < 1 || w2 < 1 || ldh < m || ldr < w1 || ldrl < w1 || (ldrl & 7) != 0) return LLS_ERR_ARG;
@@ -462,7 +472,7 @@ int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const 
     return gemm_projection(pc, stream);
 }
 
-int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
+static int lls_lowp_update_impl(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
                     int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
                     cudaStream_t stream) {
     if (m < 1 || w1 < 1 || w2 < 1 || ldh < m || lda < m || ldrl < w1 || (ldrl & 7) != 0) return LLS_ERR_ARG;
@@ -499,7 +509,7 @@ size_t lls_panel_qr_workspace_size(int m, int b) {
     return ar.off;
 }
 
-int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr, void* ws,
+static int lls_panel_qr_impl(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr, void* ws,
                  size_t ws_bytes, cudaStream_t stream) {
     if (m < 1 || b < 1 || b > 32 || m < b || ldw < m || ldr < b || !W || !R || !ws) return LLS_ERR_ARG;
     if (prec != LLS_PREC_FP16 && prec != LLS_PREC_BF16 && prec != LLS_PREC_FP32) return LLS_ERR_ARG;
@@ -535,7 +545,7 @@ size_t lls_panel_block_qr_workspace_size(int m, int w1, int w2) {
     return ar.off;
 }
 
-int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
+static int lls_panel_block_qr_impl(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
                        int ldr, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (w1 < 1 || w2 < 1 || m < w1 + w2 || ldw < m || ldh < m || ldr < w1 + w2) return LLS_ERR_ARG;
     if (!W || !Wh || !R || !ws) return LLS_ERR_ARG;
@@ -732,7 +742,7 @@ static int solve_core(int m, int n, const float* A, int lda, const double* b, do
     return rc;
 }
 
-int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
+static int lls_solve_impl(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
               int ldr, void* ws, size_t ws_bytes, const lls_options* opts, lls_info* info,
               cudaStream_t stream) {
     lls_options o;
@@ -855,7 +865,7 @@ size_t lls_solve_host_workspace_size(int m, int n, const lls_options* opts) {
     return ar.off;
 }
 
-int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
+static int lls_solve_host_impl(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
                    size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream) {
     lls_options o;
     Knobs k;
@@ -957,7 +967,7 @@ size_t lls_backward_workspace_size(int batch, const int* m, const int* n, const 
     return ar.off;
 }
 
-int lls_backward(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+static int lls_backward_impl(int batch, const int* m, const int* n, const float* const* A, const int* lda,
                  const double* const* b, const double* const* x, const float* const* R, const int* ldr,
                  const double* const* grad_x, float* const* grad_A, const int* ldga,
                  double* const* grad_b, void* ws, size_t ws_bytes, const lls_options* opts,
@@ -1091,7 +1101,7 @@ static int batch_nmax(int batch, const int* n) {
     return mx;
 }
 
-int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+static int lls_solve_batched_impl(int batch, const int* m, const int* n, const float* const* A, const int* lda,
                       const double* const* b, double* const* x, float* const* R_out, const int* ldr,
                       void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
                       cudaStream_t stream) {
@@ -1252,6 +1262,82 @@ int lls_autotune_batched(int batch, const int* m, const int* n, const float* con
     if (tbest < 0.f) return LLS_ERR_UNSUPPORTED;
     knobs_to_tuning(16, kb, tbest, *best);
     return lls_tuning_set(1, batch, batch_nmax(batch, n), &o, best);
+}
+
+// ---- entry points: LLS_DEBUG builds check the index records around each call -------------
+
+int qr_factor(int m, int n, const float* A, int lda, float* Q, int ldq, float* R, int ldr,
+              void* ws, size_t ws_bytes, const lls_options* opts, cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(qr_factor_impl(m, n, A, lda, Q, ldq, R, ldr, ws, ws_bytes, opts, stream), stream);
+}
+
+int lls_lowp_projection(int m, int w1, int w2, int prec, const void* Q1l, const void* A2l, int ldh,
+                        const int* e, float* R12, int ldr, void* R12l, int ldrl, int* f, void* ws,
+                        size_t ws_bytes, cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_lowp_projection_impl(m, w1, w2, prec, Q1l, A2l, ldh, e, R12, ldr, R12l, ldrl, f, ws, ws_bytes, stream), stream);
+}
+
+int lls_lowp_update(int m, int w1, int w2, int prec, const void* Q1l, int ldh, const void* R12l,
+                    int ldrl, const int* f, float* A2, int lda, void* ws, size_t ws_bytes,
+                    cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_lowp_update_impl(m, w1, w2, prec, Q1l, ldh, R12l, ldrl, f, A2, lda, ws, ws_bytes, stream), stream);
+}
+
+int lls_panel_qr(int m, int b, int prec, float* W, int ldw, void* Wh, int ldh, float* R, int ldr, void* ws,
+                 size_t ws_bytes, cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_panel_qr_impl(m, b, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream), stream);
+}
+
+int lls_panel_block_qr(int m, int w1, int w2, int prec, float* W, int ldw, void* Wh, int ldh, float* R,
+                       int ldr, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_panel_block_qr_impl(m, w1, w2, prec, W, ldw, Wh, ldh, R, ldr, ws, ws_bytes, stream), stream);
+}
+
+int lls_solve(int m, int n, const float* A, int lda, const double* b, double* x, float* R_out,
+              int ldr, void* ws, size_t ws_bytes, const lls_options* opts, lls_info* info,
+              cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    const int st = debug_end(lls_solve_impl(m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, info, stream), stream);
+    if (st == LLS_ERR_BOUNDS && info) info->status = st;
+    return st;
+}
+
+int lls_solve_host(int m, int n, const float* A, int lda, const double* b, double* x, void* ws,
+                   size_t ws_bytes, const lls_options* opts, lls_info* info, cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    const int st = debug_end(lls_solve_host_impl(m, n, A, lda, b, x, ws, ws_bytes, opts, info, stream), stream);
+    if (st == LLS_ERR_BOUNDS && info) info->status = st;
+    return st;
+}
+
+int lls_backward(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                 const double* const* b, const double* const* x, const float* const* R, const int* ldr,
+                 const double* const* grad_x, float* const* grad_A, const int* ldga,
+                 double* const* grad_b, void* ws, size_t ws_bytes, const lls_options* opts,
+                 cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_backward_impl(batch, m, n, A, lda, b, x, R, ldr, grad_x, grad_A, ldga, grad_b, ws, ws_bytes, opts, stream), stream);
+}
+
+int lls_solve_batched(int batch, const int* m, const int* n, const float* const* A, const int* lda,
+                      const double* const* b, double* const* x, float* const* R_out, const int* ldr,
+                      void* ws, size_t ws_bytes, const lls_options* opts, lls_info* infos,
+                      cudaStream_t stream) {
+    LLS_DEBUG_BEGIN(stream);
+    return debug_end(lls_solve_batched_impl(batch, m, n, A, lda, b, x, R_out, ldr, ws, ws_bytes, opts, infos, stream), stream);
+}
+
+int lls_debug_build(void) { return LLS_DEBUG ? 1 : 0; }
+
+int lls_debug_inject(int mode) {
+    if (!LLS_DEBUG) return LLS_ERR_UNSUPPORTED;
+    if (mode < 0 || mode > 2) return LLS_ERR_ARG;
+    return panel_debug_inject(mode);
 }
 
 }  // extern "C"

@@ -113,7 +113,8 @@ __device__ void panel_cta(const BProb& P, int c0, int w, BSmem& sm) {
             const int lr = t + r * kPanelThreads;
 #pragma unroll
             for (int j = 0; j < kBPw; ++j)
-                v[r][j] = (lr < rows && j < w) ? P.W[(size_t)(s + lr) + (size_t)(c0 + j) * P.ldw] : 0.f;
+                v[r][j] = (lr < rows && j < w && LLS_INB(s + lr < m && c0 + j < P.n))
+                              ? P.W[(size_t)(s + lr) + (size_t)(c0 + j) * P.ldw] : 0.f;
         }
         __syncthreads();
         cgs2_block<kBPw>(v, w, sm.red, sm.Rs);
@@ -125,7 +126,7 @@ __device__ void panel_cta(const BProb& P, int c0, int w, BSmem& sm) {
 #pragma unroll
             for (int p = 0; p < kBPw; ++p) {
                 const int j = p - off;
-                if (j < 0) continue;
+                if (j < 0 || !LLS_INB(s + lr < m && c0 + j < P.n)) continue;
                 const size_t idx = (size_t)(s + lr) + (size_t)(c0 + j) * P.ldw;
                 P.W[idx] = v[r][p];
                 if (nb == 1) store_lp<TL>(P.Wh, idx, v[r][p]);
@@ -583,6 +584,7 @@ batched_lls_kernel(BArgs g) {
         const int k = sm.next;
         __syncthreads();
         if (k >= g.count) return;
+        if (!LLS_INB(g.order[k] >= 0 && g.order[k] < g.count)) continue;
         const BProb P = g.probs[g.order[k]];
         // W = A, low-precision rows m..ldw-1 zero (the tensor-core tiles read whole 16-row blocks)
         for (size_t e = threadIdx.x; e < (size_t)P.ldw * P.n; e += kPanelThreads) {
@@ -726,6 +728,7 @@ batched_adjoint_kernel(AArgs g) {
         const int k = sm.next;
         __syncthreads();
         if (k >= g.count) return;
+        if (!LLS_INB(g.order[k] >= 0 && g.order[k] < g.count)) continue;
         const AProb Q = g.probs[g.order[k]];
         adjoint_cta(Q, g, sm);
     }

@@ -42,6 +42,48 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // Device error word values (written by kernels that hit a bounded-wait limit or bad data).
 enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2 };
 
+// ---------------------------------------------------------------------------------------
+// Index checks of the LLS_DEBUG build (liblls_gb300_debug.so). LLS_INB(cond) guards one
+// global-memory access. In the release build it is the constant true and compiles away. In
+// the debug build a false condition records the source line of the first failed check in
+// the translation unit's debug word, and the caller skips the access; no kernel returns
+// early on a failed check, so its barriers stay matched. The public entry points clear the
+// words before a call and read them after it (a stream synchronization), returning
+// LLS_ERR_BOUNDS and naming the file and line on stderr. Debug calls cannot be captured
+// into a caller's CUDA graph.
+// ---------------------------------------------------------------------------------------
+#ifndef LLS_DEBUG
+#define LLS_DEBUG 0
+#endif
+// Reads (reset = 0: the recorded line, 0 if none) or clears (reset = 1) one unit's word.
+using DebugFetch = int (*)(cudaStream_t st, int reset);
+bool debug_register(DebugFetch f, const char* file);
+int debug_collect(cudaStream_t st);   // LLS_OK, or LLS_ERR_BOUNDS after naming the site
+void debug_reset(cudaStream_t st);
+#if LLS_DEBUG
+namespace {
+__device__ int g_debug_line;     // one per translation unit (no relocatable device code)
+__device__ __forceinline__ bool debug_check(bool ok, int line) {
+    if (!ok) atomicCAS(&g_debug_line, 0, line);
+    return ok;
+}
+int debug_fetch(cudaStream_t st, int reset) {
+    int v = 0;
+    if (reset) {
+        cudaMemcpyToSymbolAsync(g_debug_line, &v, sizeof(v), 0, cudaMemcpyHostToDevice, st);
+        return 0;
+    }
+    cudaMemcpyFromSymbolAsync(&v, g_debug_line, sizeof(v), 0, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return v;
+}
+[[maybe_unused]] const bool g_debug_registered = debug_register(debug_fetch, __BASE_FILE__);
+}  // namespace
+#define LLS_INB(cond) (::lls::debug_check((cond), __LINE__))
+#else
+#define LLS_INB(cond) true
+#endif
+
 // Maximum wait of any device-side spin before it gives up, in nanoseconds.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) qtb_partial_kernel(const float* __restric
     }
     double s = (double)s0 + (double)s1 + ((double)s2 + (double)s3);
     s = warp_sum_d(s);
-    if (lane == 0) part[(size_t)blockIdx.y * n + j] = s;
+    if (lane == 0 && LLS_INB(r0 < m && ldq >= m)) part[(size_t)blockIdx.y * n + j] = s;
 }
 
 __global__ void __launch_bounds__(256) qtb_sum_kernel(const double* __restrict__ part, int chunks, int n,

@@ -258,7 +258,9 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     if (storer) {
                         // the chunk is complete once all four warps arrived; then write it back
                         if (ok && !mbar_wait(cdone0 + 8 * slot, ph, a.err)) ok = false;
-                        if (ok) {
+                        // a TMA store must not start at a negative coordinate (one past the
+                        // edge is clipped by the unit)
+                        if (ok && LLS_INB(m0 >= 0 && m0 < a.M && n0 + c * kCCols >= 0)) {
                             tma_store_2d(&tmC, m0, n0 + c * kCCols, smem_u32(cb));
                             bulk_commit();
                         }
@@ -270,7 +272,7 @@ tc_persist_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     if (ok) {
                         const int row = m0 + r;
                         float* o = a.out + (size_t)s * a.M * a.N;
-                        if (row < a.M) {
+                        if (row < a.M && LLS_INB(s >= 0 && s < a.splits && row >= 0)) {
 #pragma unroll
                             for (int j = 0; j < kCCols; ++j) {
                                 const int col = n0 + c * kCCols + j;

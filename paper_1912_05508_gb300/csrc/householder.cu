@@ -329,7 +329,11 @@ extern "C" int lls_householder_solve(int m, int n, int prec, const float* A, int
                                      void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (n < 1 || m < n || lda < m || !A || !b || !x || !ws) return LLS_ERR_ARG;
     if (((uintptr_t)ws & 255) != 0) return LLS_ERR_WORKSPACE;
-    if (prec == LLS_PREC_FP64) return hh_solve<double>(m, n, A, lda, b, x, ws, ws_bytes, stream);
-    if (prec == LLS_PREC_FP32) return hh_solve<float>(m, n, A, lda, b, x, ws, ws_bytes, stream);
-    return LLS_ERR_ARG;
+    if (prec != LLS_PREC_FP64 && prec != LLS_PREC_FP32) return LLS_ERR_ARG;
+    if (LLS_DEBUG) lls::debug_reset(stream);
+    const int st = prec == LLS_PREC_FP64 ? hh_solve<double>(m, n, A, lda, b, x, ws, ws_bytes, stream)
+                                         : hh_solve<float>(m, n, A, lda, b, x, ws, ws_bytes, stream);
+    if (!LLS_DEBUG) return st;
+    const int d = lls::debug_collect(stream);   // the debug build's index records
+    return d != LLS_OK ? d : st;
 }

@@ -38,6 +38,9 @@ void panel_scratch_sizes(int m, size_t& rbuf_floats, size_t& qbuf_floats, size_t
 int panel_qr(const PanelCall& c, cudaStream_t st);
 // One-level-tree variant (panel_flat.cu); LLS_ERR_UNSUPPORTED when the panel needs a deeper tree.
 int panel_flat_qr(const PanelCall& c, cudaStream_t st);
+// Debug build: arms a planted fault of the CAQR panel kernels (1: out-of-range Q stores, 2: a
+// grid barrier that cannot complete) or disarms it (0).
+int panel_debug_inject(int mode);
 // Two one-level panels and the recursion node between them in one cooperative launch
 // (panel_flat.cu): columns [c0, c0 + w1) and [c0 + w1, c0 + w1 + w2), 8 < w1 <= 16,
 // 1 <= w2 <= w1, FP16 or BF16 products. LLS_ERR_UNSUPPORTED (nothing launched) otherwise.
@@ -209,6 +212,7 @@ int direct_start(const float* Q, int ldq, int m, int n, const double* b, const f
 // ---- misc (util.cu) -------------------------------------------------------------------------
 int copy_matrix(const float* src, int lds, float* dst, int ldd, int m, int n, cudaStream_t st);
 int check_diag(const float* R, int ldr, int n, int* dev_err, cudaStream_t st);
+int poison_diag_on_error(float* R, int ldr, int n, const int* dev_err, cudaStream_t st);
 int zero_lower(float* R, int ldr, int n, cudaStream_t st);
 
 }  // namespace lls

@@ -1,11 +1,13 @@
 // R-preconditioned CGLS (Alg. 5, Sec. 3.2.3) as one persistent cooperative kernel.
 //
-// Products with A: for n <= 4096 each iteration makes ONE pass over A. A is streamed in
-// 4-row blocks through a double-buffered shared-memory ring (cp.async); for each block the
-// CTA forms q = A t on those rows (block-wide reduction), then accumulates A^T q and A^T r
-// for its columns from the same shared-memory copy. After the pass, with delta = ||q||^2
-// and alpha = gamma / delta known, u = A^T r_new = A^T r - alpha A^T q. Larger n uses two
-// passes (q = A t; then u = A^T r after the r update).
+// Products with A: the default engine makes two passes over A per iteration: q = A t as
+// per-column-chunk partial sums over 1024-row tiles, then, after the r update, u = A^T r as
+// per-row-chunk partial sums over 32-column groups; every partial is summed in a fixed
+// order. An optional one-pass engine (LLS_KRYLOV=onepass, CGLS with n <= 4096) streams a
+// row-block copy of A in 4-row blocks through a double-buffered shared-memory ring
+// (cp.async); for each block the CTA forms q = A t on those rows (block-wide reduction),
+// then accumulates A^T q and A^T r for its columns from the same shared-memory copy, and
+// after the pass u = A^T r_new = A^T r - alpha A^T q.
 //
 // The loop of Alg. 5, with the slips of the printed listing read as: step length
 // alpha = gamma / delta, solution update x += alpha R^{-1} p, and the preconditioned
@@ -252,7 +254,7 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
         two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
         two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
         warp_sum_df(s0, c0);
-        if (lane == 0) {
+        if (lane == 0 && LLS_INB(c >= 0 && c < n)) {
             const double val = join_df(s0, c0);
             out[c] = val;
             if (outdf) outdf[c] = to_df(val);
@@ -272,6 +274,7 @@ __device__ void a_times_partials(const KArgs& a) {
         const int i0 = rt * kRowTile + 4 * threadIdx.x;
         if (i0 >= a.m) continue;
         const int j0 = cc * a.colchunk, j1 = min(a.n, j0 + a.colchunk);
+        if (!LLS_INB(j0 >= 0 && j1 <= a.n && a.lda >= a.m)) continue;
         const bool full = a.aligned16 && i0 + 4 <= a.m;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
         if (full) {
@@ -300,6 +303,7 @@ __device__ void a_times_partials(const KArgs& a) {
                 if (i0 + 3 < a.m) dot2_step(s3, c3, col[3], t.x, t.y);
             }
         }
+        if (!LLS_INB(cc < a.nck && i0 < a.m)) continue;
         double* out = a.qpart + (size_t)cc * a.m + i0;
         out[0] = join_df(s0, c0);
         if (i0 + 1 < a.m) out[1] = join_df(s1, c1);
@@ -336,6 +340,7 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
             __syncthreads();
             staged = rc;
         }
+        if (!LLS_INB(r0 >= 0 && r0 + rows <= a.m)) continue;
         const bool full = a.aligned16 && rows == kRowChunk;
         for (int jj = 0; jj < kColGroup / kKWarps; ++jj) {
             const int j = cg * kColGroup + warp * (kColGroup / kKWarps) + jj;
@@ -369,7 +374,7 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
             two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
             two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
             warp_sum_df(s0, c0);
-            if (lane == 0) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
+            if (lane == 0 && LLS_INB(rc < a.nrc && j < a.n)) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
         }
     }
 }

@@ -75,10 +75,11 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
     // ---- A: load this CTA's rows; column maxima of |A2| ------------------------------------
     float av[W1];
 #pragma unroll
-    for (int j = 0; j < W1; ++j) av[j] = (valid && j < w2) ? a.W[(size_t)row + (size_t)(cA + j) * a.ldw] : 0.f;
+    for (int j = 0; j < W1; ++j)
+        av[j] = (valid && j < w2 && LLS_INB(row < a.ldw)) ? a.W[(size_t)row + (size_t)(cA + j) * a.ldw] : 0.f;
 #pragma unroll
     for (int i = 0; i < W1; ++i) {
-        const TL q = (valid && i < w1) ? Wh[(size_t)row + (size_t)(a.c0 + i) * a.ldh] : zero;
+        const TL q = (valid && i < w1 && LLS_INB(row < a.ldh)) ? Wh[(size_t)row + (size_t)(a.c0 + i) * a.ldh] : zero;
         sm.Qs[i][t] = q;
         sm.QsT[t][i] = q;
     }
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             sm.red[c][warp][lane] = warp_transpose_max<kCh>(mx);
         }
         __syncthreads();
-        if (t < w2) {
+        if (t < w2 && LLS_INB(t < W1)) {
             float m = 0.f;
 #pragma unroll
             for (int q = 0; q < kNW; ++q) m = fmaxf(m, sm.red[t / kCh][q][t % kCh]);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
 #pragma unroll
             for (int q = 0; q < G; ++q) tot += sm.part_g[q * W1 + t];
             r12 = tot * pow2f(-scale_exponent(a.kind, sm.colm[j]));
-            if (t < w1) a.R[(size_t)(a.c0 + t) + (size_t)(cA + j) * a.ldr] = r12;
+            if (t < w1 && LLS_INB(a.c0 + t < a.ldr)) a.R[(size_t)(a.c0 + t) + (size_t)(cA + j) * a.ldr] = r12;
         }
         float mx = (t < w1) ? fabsf(r12) : 0.f;
         mx = warp_max_f(mx);                      // rows 0..W1-1 live in warps 0..W1/32-1
@@ -210,7 +211,8 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
     if (valid) {
 #pragma unroll
         for (int j = 0; j < W1; ++j)
-            if (j < w2) a.W[(size_t)row + (size_t)(cA + j) * a.ldw] = fmaf(-sm.Us[t][j], sm.sc[j], av[j]);
+            if (j < w2 && LLS_INB(row < a.ldw))
+                a.W[(size_t)row + (size_t)(cA + j) * a.ldw] = fmaf(-sm.Us[t][j], sm.sc[j], av[j]);
     }
 }
 

@@ -347,7 +347,18 @@ __device__ __forceinline__ void flat_leaf_range(int m, int P0, int i, int& s, in
     e = s + base + (i < extra ? 1 : 0);
 }
 
+#if LLS_DEBUG
+// Planted faults for the tests of the debug build: 1 = every store of Q is addressed one panel
+// height too low (the index checks reject it); 2 = the leaf-to-tree grid barrier waits for one
+// CTA more than the grid holds (the bounded wait gives up).
+__device__ int g_debug_inject;
+#endif
+
 __device__ __forceinline__ void flat_store_q(const FlatArgs& a, int row, int j, float q) {
+#if LLS_DEBUG
+    if (g_debug_inject == 1) row += a.m;
+#endif
+    if (!LLS_INB(row >= 0 && row < a.m && j >= 0 && j < a.b)) return;
     a.W[(size_t)row + (size_t)(a.c0 + j) * a.ldw] = q;
     const size_t h = (size_t)row + (size_t)(a.c0 + j) * a.ldh;
     if (a.lowp == 0) reinterpret_cast<__half*>(a.Wh)[h] = __float2half_rn(q);
@@ -358,6 +369,7 @@ template <int B>
 __device__ __forceinline__ void flat_write_r(const FlatArgs& a, const FlatSmem<B>& sm) {
     for (int i = threadIdx.x; i < a.b * a.b; i += kFT) {
         const int r = i % a.b, c = i / a.b;
+        if (!LLS_INB(r < B && c < B && a.c0 + r < a.ldr)) continue;
         a.R[(size_t)(a.c0 + r) + (size_t)(a.c0 + c) * a.ldr] = r <= c ? sm.Rs[r][c] : 0.f;
     }
 }
@@ -396,13 +408,19 @@ __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B],
 #pragma unroll
         for (int j = 0; j < B; ++j) Ql[(t + r * kFT) * (B + 1) + j] = v[r][j];
     float* rb = a.rbuf + (size_t)blockIdx.x * (B * B);
-    for (int i = t; i < B * B; i += kFT) rb[i] = sm.Rs[i / B][i % B];
+    if (LLS_INB((int)blockIdx.x < a.P0))
+        for (int i = t; i < B * B; i += kFT) rb[i] = sm.Rs[i / B][i % B];
     __threadfence();
     __syncthreads();
     for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
 
     // bounded grid barrier: every leaf R is in the workspace
-    if (!grid_barrier(a.bar, a.P0, a.err)) return false;
+#if LLS_DEBUG
+    const unsigned expect = a.P0 + (g_debug_inject == 2 ? 1 : 0);
+#else
+    const unsigned expect = a.P0;
+#endif
+    if (!grid_barrier(a.bar, expect, a.err)) return false;
 
     // the stacked R factors, row-index-major: thread t holds row rr = t / TPR of the R
     // factors of children (t mod TPR) + TPR r, so each warp holds one or two row indices
@@ -414,7 +432,7 @@ __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B],
     for (int r = 0; r < kRootRPT; ++r) {
         const int child = cl + TPR * r;
         const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
-        const bool live = child < a.P0 && rr < b;
+        const bool live = child < a.P0 && rr < b && LLS_INB(child >= 0 && rr >= 0 && rr < B);
 #pragma unroll
         for (int j4 = 0; j4 < B / 4; ++j4) {
             const float4 q = live ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -475,7 +493,8 @@ __device__ __forceinline__ void load_rows(const FlatArgs& a, int c0, float (&v)[
         const int lr = threadIdx.x + r * kFT;
 #pragma unroll
         for (int j = 0; j < B; ++j)
-            v[r][j] = (lr < rows && j < ncol) ? a.W[(size_t)(s + lr) + (size_t)(c0 + j) * a.ldw] : 0.f;
+            v[r][j] = (lr < rows && j < ncol && LLS_INB(s + lr >= 0 && s + lr < a.m))
+                          ? a.W[(size_t)(s + lr) + (size_t)(c0 + j) * a.ldw] : 0.f;
     }
 }
 
@@ -572,7 +591,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         const float wm = warp_transpose_max<16>(mx);
         if (lane < 16) bs.red[warp][lane] = wm;
         __syncthreads();
-        if (t < w2) {
+        if (t < w2 && LLS_INB(t < 16)) {
             float x = 0.f;
 #pragma unroll
             for (int q = 0; q < kFW; ++q) x = fmaxf(x, bs.red[q][t]);
@@ -618,7 +637,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         float x = 0.f;
 #pragma unroll
         for (int q = 0; q < kFW; ++q) x += bs.wp[q][t];   // entry (t mod 16, t / 16)
-        a.part[(size_t)blockIdx.x * 256 + t] = x;
+        if (LLS_INB((int)blockIdx.x < kBlockMaxP0 && t < 256)) a.part[(size_t)blockIdx.x * 256 + t] = x;
     }
     if (!grid_barrier(a.p1.bar, P0, a.p1.err)) return false;
     // every CTA has read the column maxima before the barrier above: CTA 0 clears them
@@ -642,7 +661,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         const bool live = i < w1 && j < w2;
         const float r12 = live ? tot * bs.einv[j] : 0.f;
         bs.r12[j][i] = r12;
-        if (blockIdx.x == 0 && live)
+        if (blockIdx.x == 0 && live && LLS_INB(a.p1.c0 + i < a.p1.ldr))
             a.p1.R[(size_t)(a.p1.c0 + i) + (size_t)(a.p1.c0 + w1 + j) * a.p1.ldr] = r12;
     }
     __syncthreads();
@@ -813,6 +832,17 @@ bool flat_disabled() {
 }
 
 }  // namespace
+
+int panel_debug_inject(int mode) {
+#if LLS_DEBUG
+    const int v = mode;
+    LLS_CUDA_TRY(cudaMemcpyToSymbol(g_debug_inject, &v, sizeof(v)));
+    return LLS_OK;
+#else
+    (void)mode;
+    return LLS_ERR_UNSUPPORTED;
+#endif
+}
 
 // Returns LLS_ERR_UNSUPPORTED (nothing launched) when the panel needs a deeper tree.
 int panel_flat_qr(const PanelCall& c, cudaStream_t st) {

@@ -1,4 +1,5 @@
-// Launch counting and optional per-kernel tracing.
+// Launch counting, optional per-kernel tracing, and the registry of the debug build's
+// per-unit index-check words.
 //
 // Every launch goes through note_launch(name, stream). With the environment variable
 // LLS_TRACE set, an event is recorded after each launch; trace_flush() (called at the end of
@@ -7,6 +8,7 @@
 // and a table is printed to stderr at process exit.
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <atomic>
 #include <map>
@@ -85,6 +87,39 @@ void trace_flush() {
         g_last[r.st] = r.ev;
     }
     g_pending.clear();
+}
+
+// ---- LLS_DEBUG index checks: one word per translation unit -------------------------------
+namespace {
+struct DebugUnit { DebugFetch fetch; const char* file; };
+std::vector<DebugUnit>& debug_units() {
+    static std::vector<DebugUnit> u;   // filled by static initializers, before any call
+    return u;
+}
+}  // namespace
+
+bool debug_register(DebugFetch f, const char* file) {
+    debug_units().push_back({f, file});
+    return true;
+}
+
+void debug_reset(cudaStream_t st) {
+    for (auto& u : debug_units()) u.fetch(st, 1);
+}
+
+int debug_collect(cudaStream_t st) {
+    int status = LLS_OK;
+    for (auto& u : debug_units()) {
+        const int line = u.fetch(st, 0);
+        if (line != 0) {
+            const char* base = strrchr(u.file, '/');
+            fprintf(stderr, "[lls debug] index check failed at %s:%d (the access was skipped)\n",
+                    base ? base + 1 : u.file, line);
+            status = LLS_ERR_BOUNDS;
+            u.fetch(st, 1);
+        }
+    }
+    return status;
 }
 
 }  // namespace lls

@@ -24,6 +24,21 @@ int check_diag(const float* R, int ldr, int n, int* dev_err, cudaStream_t st) {
     return LLS_OK;
 }
 
+// After a factorization whose device error word is set (a bounded wait gave up, so R and Q
+// are incomplete): R's diagonal becomes NaN, which the caller sees without synchronizing.
+__global__ void poison_diag_kernel(float* R, int ldr, int n, const int* err) {
+    if (*(volatile const int*)err == DEV_OK) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        R[(size_t)i + (size_t)i * ldr] = __int_as_float(0x7fc00000);
+}
+
+int poison_diag_on_error(float* R, int ldr, int n, const int* dev_err, cudaStream_t st) {
+    if (n <= 0) return LLS_OK;
+    poison_diag_kernel<<<ceil_div(n, 256) < 16 ? ceil_div(n, 256) : 16, 256, 0, st>>>(R, ldr, n, dev_err);
+    LLS_LAUNCH_CHECK("poison_diag", st);
+    return LLS_OK;
+}
+
 __global__ void zero_lower_kernel(float* R, int ldr, int n) {
     int j = blockIdx.y;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x + j + 1; i < n; i += gridDim.x * blockDim.x)
@@ -82,6 +97,7 @@ __global__ void copy_sumsq_kernel(const float* __restrict__ A, int lda, float* _
         const float* a = A + (size_t)j * lda;
         float* w = W ? W + (size_t)j * ldw : nullptr;
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m4; q += gridDim.x * blockDim.x) {
+            if (!LLS_INB(4 * q + 3 < m && (W == nullptr || ldw >= m) && lda >= m)) continue;
             float4 v;
             if (vec4) {
                 v = __ldg(reinterpret_cast<const float4*>(a) + q);

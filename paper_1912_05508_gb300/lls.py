@@ -12,6 +12,8 @@ import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblls_gb300.so")
+# LLS_DEBUG=1 in the environment selects the index-checking build (build(debug=True))
+LIB_DEBUG_PATH = os.path.join(PKG, "liblls_gb300_debug.so")
 
 PREC = {"fp16": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp64": 4}
 TARGET = {"fp32": 0, "fp64": 1}
@@ -20,7 +22,7 @@ PANEL_LEAF = {"cgs2": 0, "mgs": 1}
 X0 = {"zero": 0, "given": 1, "direct": 2}
 STATUS = {0: "LLS_OK", 1: "LLS_NOT_CONVERGED", -1: "LLS_ERR_ARG", -2: "LLS_ERR_SINGULAR",
           -3: "LLS_ERR_CUDA", -4: "LLS_ERR_WORKSPACE", -5: "LLS_ERR_TIMEOUT", -6: "LLS_ERR_UNSUPPORTED",
-          -7: "LLS_ERR_TOO_LARGE"}
+          -7: "LLS_ERR_TOO_LARGE", -8: "LLS_ERR_BOUNDS"}
 
 EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count",
            "qr_factor_workspace_size", "qr_factor", "lls_solve_workspace_size", "lls_solve",
@@ -33,7 +35,7 @@ EXPORTS = ("lls_default_options", "lls_status_string", "lls_kernel_launch_count"
            "lls_upload_chunks",
            "lls_householder_workspace_size", "lls_householder_solve",
            "lls_autotune_workspace_size", "lls_autotune", "lls_autotune_batched", "lls_tuning_set",
-           "lls_tuning_get", "lls_tuning_clear")
+           "lls_tuning_get", "lls_tuning_clear", "lls_debug_build", "lls_debug_inject")
 
 
 class lls_options(C.Structure):
@@ -69,11 +71,14 @@ class LLSError(RuntimeError):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load the compiled library (built by paper_1912_05508_gb300.build)."""
+def load(path: str | None = None):
+    """Load the compiled library (built by paper_1912_05508_gb300.build); with LLS_DEBUG=1 in
+    the environment, the index-checking debug build."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_DEBUG_PATH if os.environ.get("LLS_DEBUG", "0") not in ("", "0") else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} missing (run __graft_entry__.build())")
     lib = C.CDLL(path)
@@ -146,6 +151,10 @@ def load(path: str = LIB_PATH):
     lib.lls_tuning_get.restype = i
     lib.lls_tuning_clear.argtypes = []
     lib.lls_tuning_clear.restype = None
+    lib.lls_debug_build.argtypes = []
+    lib.lls_debug_build.restype = i
+    lib.lls_debug_inject.argtypes = [i]
+    lib.lls_debug_inject.restype = i
     _lib = lib
     return lib
 
