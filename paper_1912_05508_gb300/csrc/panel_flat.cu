@@ -8,8 +8,9 @@
 //  2. One bounded grid barrier (cooperative launch: all CTAs are resident).
 //  3. (circled 2-3) every CTA loads the P0 stacked R factors and factors the stack with the
 //     same code in the same order, so each CTA holds the tree's Q without a second exchange
-//     through memory. CTA 0 writes R. The stack is held row-index-major, so the warps whose
-//     rows of the upper-triangular factors are still zero skip a step's arithmetic.
+//     through memory. CTA 0 writes R. Each thread holds rows of one child spaced b/4 apart, so
+//     in the early steps, where the upper-triangular factors' later rows are still zero, every
+//     thread leaves those rows out of its arithmetic (compile-time row counts per group).
 //  4. (circled 4-5) each CTA multiplies its block's Q by its b x b slice of the tree's Q and
 //     stores the result: FP32 to W and, rounded to nearest even, to the product-precision
 //     copy Wh.
@@ -34,8 +35,7 @@ namespace {
 
 constexpr int kFT = 256;            // threads per CTA
 constexpr int kFW = kFT / 32;       // warps per CTA
-constexpr int kRootRPT = 4;         // stacked rows per thread in the tree factorization
-constexpr int kStackRows = kRootRPT * kFT;
+constexpr int kStackRows = 4 * kFT;   // most stacked leaf-R rows of the tree (4 per thread)
 
 struct FlatArgs {
     float* W; int ldw;
@@ -59,29 +59,22 @@ struct FlatSmem {
 // CTA-wide sums of the N (<= 64) values x[] held by every thread. Returns this warp's row of
 // `tot`, whose entries 0..N-1 hold the CTA totals. One barrier; `red` alternates between
 // two buffers, so the next call may start writing before every warp has read this one.
-// A warp whose rows are all zero (`idle`, warp-uniform) contributes zeros without shuffling.
 template <int N, int B>
-__device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<B>& sm, int& parity,
-                                                  bool idle = false) {
+__device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<B>& sm, int& parity) {
     static_assert(N >= 1 && N <= 64, "block_sum handles at most 64 values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int N0 = N < 32 ? N : 32;
     constexpr int S0 = pow2ceil(N0);
-    if (idle) {
-        sm.red[parity][0][warp][lane] = 0.f;
-        if constexpr (N > 32) sm.red[parity][1][warp][lane] = 0.f;
-    } else {
-        float c0[S0];
+    float c0[S0];
 #pragma unroll
-        for (int i = 0; i < S0; ++i) c0[i] = i < N0 ? x[i] : 0.f;
-        sm.red[parity][0][warp][lane] = warp_transpose_reduce<S0>(c0);
-        if constexpr (N > 32) {
-            constexpr int S1 = pow2ceil(N - 32);
-            float c1[S1];
+    for (int i = 0; i < S0; ++i) c0[i] = i < N0 ? x[i] : 0.f;
+    sm.red[parity][0][warp][lane] = warp_transpose_reduce<S0>(c0);
+    if constexpr (N > 32) {
+        constexpr int S1 = pow2ceil(N - 32);
+        float c1[S1];
 #pragma unroll
-            for (int i = 0; i < S1; ++i) c1[i] = 32 + i < N ? x[32 + i] : 0.f;
-            sm.red[parity][1][warp][lane] = warp_transpose_reduce<S1>(c1);
-        }
+        for (int i = 0; i < S1; ++i) c1[i] = 32 + i < N ? x[32 + i] : 0.f;
+        sm.red[parity][1][warp][lane] = warp_transpose_reduce<S1>(c1);
     }
     __syncthreads();
     float t0 = 0.f;
@@ -99,6 +92,16 @@ __device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<
     return sm.tot[warp];
 }
 
+// Rows of a register block that can be nonzero up to step KMAX. A leaf (TC = 0): all R. The
+// tree's stack (TC > 0): the thread holds row index (t mod TC) + TC r of one child's upper-
+// triangular factor, and rows with index > KMAX are zero in columns 0..KMAX and left unchanged
+// by steps 0..KMAX (their products with the current column vanish and nothing is subtracted
+// from them), so only r <= KMAX / TC take part.
+template <int R, int KMAX, int TC>
+__host__ __device__ constexpr int active_rows() {
+    return TC == 0 ? R : (KMAX / TC + 1 < R ? KMAX / TC + 1 : R);
+}
+
 // Steps K = K0 .. K0 + KG - 1 of the lagged CGS2 on the register block v (R rows per thread,
 // columns 0..B-1; before step K, columns < K hold q_0..q_{K-1}, column K holds a_K after its
 // first projection, the rest are raw). Afterwards column K holds q_K and column K+1 its first
@@ -108,22 +111,19 @@ __device__ __forceinline__ const float* block_sum(const float (&x)[N], FlatSmem<
 // group's widest step, with the columns not yet orthogonalised masked to zero, and pick the
 // current and next columns by register selects. Sharing bodies keeps the kernel's code
 // small enough for the instruction cache at a cost of at most KG - 1 extra products.
-// rr0: the smallest in-block row index held by this warp in the stacked-R layout (the root),
-// or 0 (the leaves). In the stacked upper-triangular R factors, row index K + 1 and beyond is
-// zero in q_0..q_K and in column K, so such rows contribute nothing to step K's products and
-// the step leaves them unchanged: a warp with rr0 >= K + 1 skips the step's arithmetic.
-template <int B, int R, int K0, int KG>
-__device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+// TC: see active_rows (the tree's rows that are still zero take no part in a group's steps).
+template <int B, int R, int K0, int KG, int TC>
+__device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
     constexpr int NQ = K0 + KG - 1;              // q columns any step of the group may use
     constexpr int N = 2 * NQ + 2;                // h2[NQ], nn, g[NQ], c
+    constexpr int RA = active_rows<R, K0 + KG - 1, TC>();   // rows that can be nonzero in the group
 #pragma unroll 1
     for (int s = 0; s < KG; ++s) {
         const int K = K0 + s;
         if (K >= b) return;
-        const bool idle = rr0 >= K + 1;  // rows >= K + 1: zero contributions, and unchanged by the step
         float cur[R], nx[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RA; ++r) {
             float c = v[r][K0], d = K0 + 1 < B ? v[r][K0 + 1] : 0.f;
 #pragma unroll
             for (int u = 1; u < KG; ++u) {
@@ -138,7 +138,7 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
         for (int j = 0; j < NQ; ++j) {
             float p1 = 0.f, p2 = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RA; ++r) {
                 p1 = fmaf(v[r][j], cur[r], p1);
                 p2 = fmaf(v[r][j], nx[r], p2);
             }
@@ -148,14 +148,14 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
         {
             float p1 = 0.f, p2 = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RA; ++r) {
                 p1 = fmaf(cur[r], cur[r], p1);
                 p2 = fmaf(cur[r], nx[r], p2);
             }
             x[NQ] = p1;
             x[2 * NQ + 1] = p2;
         }
-        const float* t = block_sum<N, B>(x, sm, parity, idle);
+        const float* t = block_sum<N, B>(x, sm, parity);
 
         // two interleaved chains per sum (even / odd j) halve the dependent FMA depth
         float h2[NQ > 0 ? NQ : 1], g[NQ > 0 ? NQ : 1];
@@ -171,26 +171,22 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
         const float nn = t[NQ];
         float acc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = 0.f;
-        if (!idle) {
+        for (int r = 0; r < RA; ++r) {
+            float a0 = cur[r], a1 = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float a0 = cur[r], a1 = 0.f;
-#pragma unroll
-                for (int j = 0; j < NQ; ++j) {
-                    if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
-                    else a0 = fmaf(-v[r][j], h2[j], a0);
-                }
-                acc[r] = a0 + a1;
+            for (int j = 0; j < NQ; ++j) {
+                if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
+                else a0 = fmaf(-v[r][j], h2[j], a0);
             }
+            acc[r] = a0 + a1;
         }
         float normsq = nn - hh;
         if (!(normsq >= 0.25f * nn)) {   // the second pass removed much of the norm: reduce it directly
             float d[1];
             d[0] = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) d[0] = fmaf(acc[r], acc[r], d[0]);
-            normsq = block_sum<1, B>(d, sm, parity, idle)[0];
+            for (int r = 0; r < RA; ++r) d[0] = fmaf(acc[r], acc[r], d[0]);
+            normsq = block_sum<1, B>(d, sm, parity)[0];
         }
         // R_KK and 1 / R_KK from one reciprocal square root (a few ulp; the CGS2 error bound
         // is unchanged up to the constant)
@@ -210,9 +206,8 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
                 if (next) sm.Rs[K][K + 1] = gq;
             }
         }
-        if (idle) continue;              // the warp's rows stay zero
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RA; ++r) {
             const float q = acc[r] * inv;
             float a0 = nx[r], a1 = 0.f;
 #pragma unroll
@@ -235,18 +230,18 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
 // q_0..q_{K-1} removed. One CTA-wide reduction gives ||a_K||^2 and a_K^T a_j (j > K); then
 // R_KK = ||a_K||, q_K = a_K / R_KK, R_Kj = a_K^T a_j / R_KK (= q_K^T a_j) and
 // a_j -= q_K R_Kj. Products for columns j <= K are masked to zero, so the shared group body
-// leaves them untouched. rr0 as in cgs2_group.
-template <int B, int R, int K0, int KG>
-__device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+// leaves them untouched. TC as in cgs2_group.
+template <int B, int R, int K0, int KG, int TC>
+__device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+    constexpr int RA = active_rows<R, K0 + KG - 1, TC>();
     constexpr int N = B - K0;                    // ||a_K||^2, then a_K^T a_j for j = K0+1 .. B-1
 #pragma unroll 1
     for (int s = 0; s < KG; ++s) {
         const int K = K0 + s;
         if (K >= b) return;
-        const bool idle = rr0 >= K + 1;
         float cur[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RA; ++r) {
             float c = v[r][K0];
 #pragma unroll
             for (int u = 1; u < KG; ++u) c = s == u ? v[r][K0 + u] : c;
@@ -256,7 +251,7 @@ __device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& 
         {
             float p = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) p = fmaf(cur[r], cur[r], p);
+            for (int r = 0; r < RA; ++r) p = fmaf(cur[r], cur[r], p);
             x[0] = p;
         }
 #pragma unroll
@@ -264,10 +259,10 @@ __device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& 
             const int j = K0 + i;
             float p = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) p = fmaf(v[r][j], cur[r], p);
+            for (int r = 0; r < RA; ++r) p = fmaf(v[r][j], cur[r], p);
             x[i] = j > K ? p : 0.f;
         }
-        const float* t = block_sum<N, B>(x, sm, parity, idle);
+        const float* t = block_sum<N, B>(x, sm, parity);
         const float ns = fmaxf(t[0], 0.f);
         const float inv = ns > 0.f ? rsqrtf(ns) : 0.f;
         const float nrm = ns * inv;
@@ -280,9 +275,8 @@ __device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& 
             if (lane == 0) sm.Rs[K][K] = nrm;
             if (lane > K && lane < b) sm.Rs[K][lane] = t[lane - K0] * inv;
         }
-        if (idle) continue;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RA; ++r) {
             const float q = cur[r] * inv;
 #pragma unroll
             for (int i = 1; i < N; ++i) v[r][K0 + i] = fmaf(-q, rk[i], v[r][K0 + i]);
@@ -293,22 +287,22 @@ __device__ __forceinline__ void mgs_group(float (&v)[R][B], int b, FlatSmem<B>& 
     }
 }
 
-template <int B, int R, int K0>
+template <int B, int R, int K0, int TC>
 struct MgsFlat {
     static constexpr int KG = 4;
-    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
         if (K0 >= b) return;
-        mgs_group<B, R, K0, KG>(v, b, sm, parity, rr0);
-        MgsFlat<B, R, K0 + KG>::run(v, b, sm, parity, rr0);
+        mgs_group<B, R, K0, KG, TC>(v, b, sm, parity);
+        MgsFlat<B, R, K0 + KG, TC>::run(v, b, sm, parity);
     }
 };
-template <int B, int R>
-struct MgsFlat<B, R, B> {
-    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
+template <int B, int R, int TC>
+struct MgsFlat<B, R, B, TC> {
+    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&) {}
 };
 
-// CGS2 steps per shared group body, for the leaf (2 rows per thread) and the tree stage (4 rows
-// per thread). Fewer steps per body mean fewer masked products but more code for the
+// CGS2 steps per shared group body, for blocks of 2 rows per thread (LEAF: the 512-row leaves and
+// the 512-row tree stack) and of 4 rows per thread (TREE: the 1024-row leaves and stack). Fewer steps per body mean fewer masked products but more code for the
 // instruction cache; on the 32768 x 16 panel two steps per body measured fastest (block
 // 75.8 us, against 77.8 with four and 88.4 with one).
 #ifndef LLS_CGS_GROUP_LEAF
@@ -320,25 +314,26 @@ struct MgsFlat<B, R, B> {
 template <int R>
 constexpr int cgs_group() { return R <= 2 ? LLS_CGS_GROUP_LEAF : LLS_CGS_GROUP_TREE; }
 
-template <int B, int R, int K0>
+template <int B, int R, int K0, int TC>
 struct Cgs2Flat {
     static constexpr int KG = cgs_group<R>() < B ? cgs_group<R>() : B;
-    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
+    static __device__ __forceinline__ void run(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
         if (K0 >= b) return;
-        cgs2_group<B, R, K0, KG>(v, b, sm, parity, rr0);
-        Cgs2Flat<B, R, K0 + KG>::run(v, b, sm, parity, rr0);
+        cgs2_group<B, R, K0, KG, TC>(v, b, sm, parity);
+        Cgs2Flat<B, R, K0 + KG, TC>::run(v, b, sm, parity);
     }
 };
-template <int B, int R>
-struct Cgs2Flat<B, R, B> {
-    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&, int) {}
+template <int B, int R, int TC>
+struct Cgs2Flat<B, R, B, TC> {
+    static __device__ __forceinline__ void run(float (&)[R][B], int, FlatSmem<B>&, int&) {}
 };
 
-// The leaf factorization of the panel: CGS2 (default) or MGS (Alg. 4).
-template <bool MGS, int B, int R>
-__device__ __forceinline__ void leaf_qr(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity, int rr0) {
-    if constexpr (MGS) MgsFlat<B, R, 0>::run(v, b, sm, parity, rr0);
-    else Cgs2Flat<B, R, 0>::run(v, b, sm, parity, rr0);
+// The factorization of a register block: CGS2 (default) or MGS (Alg. 4). TC = 0: a leaf (rows
+// of the panel); TC > 0: the tree's stack in the layout of panel_body (TC threads per child).
+template <bool MGS, int B, int R, int TC = 0>
+__device__ __forceinline__ void leaf_qr(float (&v)[R][B], int b, FlatSmem<B>& sm, int& parity) {
+    if constexpr (MGS) MgsFlat<B, R, 0, TC>::run(v, b, sm, parity);
+    else Cgs2Flat<B, R, 0, TC>::run(v, b, sm, parity);
 }
 
 __device__ __forceinline__ void flat_leaf_range(int m, int P0, int i, int& s, int& e) {
@@ -378,14 +373,14 @@ __device__ __forceinline__ void flat_write_r(const FlatArgs& a, const FlatSmem<B
 // leaf factorization, the one-level tree and the reconstruction. Q goes to W and Wh, R to R
 // (CTA 0). On return v holds this CTA's rows of Q (zero beyond `rows`). Returns false if a
 // bounded grid barrier gave up (the error word is set).
-template <int B, int RL, bool MGS>
+template <int B, int RL, int RR, bool MGS>
 __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B], FlatSmem<B>& sm, float* Ql, int& parity,
                            int s, int rows) {
     const int t = threadIdx.x, b = a.b;
     for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
     for (int i = t; i < B * B; i += kFT) (&sm.S[0][0])[i] = 0.f;
     __syncthreads();
-    leaf_qr<MGS, B, RL>(v, b, sm, parity, 0);
+    leaf_qr<MGS, B, RL>(v, b, sm, parity);
     __syncthreads();
 
     if (a.P0 == 1) {   // the block is the whole panel: Q and R are final
@@ -422,30 +417,36 @@ __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B],
 #endif
     if (!grid_barrier(a.bar, expect, a.err)) return false;
 
-    // the stacked R factors, row-index-major: thread t holds row rr = t / TPR of the R
-    // factors of children (t mod TPR) + TPR r, so each warp holds one or two row indices
-    // (rr0 = its first) and can skip the steps where its rows are still zero
-    constexpr int TPR = kFT / B;
-    const int rr = t / TPR, cl = t % TPR;
-    float vr[kRootRPT][B];
+    // the stacked R factors: TC = B / 4 threads per child, thread t holding rows
+    // (t mod TC) + TC r (r < RR) of child t / TC, so that in step K only the rows r <= K / TC can
+    // be nonzero (upper-triangular factors) and every thread takes part in the same share
+    constexpr int TC = B / 4;
+    static_assert(RR * TC == B && kFT / TC * B == kStackRows, "tree layout: 4 rows of each child per thread");
+    const int child = t / TC, rsub = t % TC;
+    float vr[RR][B];
+    {
+        const bool live = child < a.P0 && LLS_INB(child >= 0);
 #pragma unroll
-    for (int r = 0; r < kRootRPT; ++r) {
-        const int child = cl + TPR * r;
-        const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
-        const bool live = child < a.P0 && rr < b && LLS_INB(child >= 0 && rr >= 0 && rr < B);
+        for (int r = 0; r < RR; ++r) {
+            const int rr = rsub + TC * r;
+            const float4* src = reinterpret_cast<const float4*>(a.rbuf + (size_t)child * (B * B) + rr * B);
 #pragma unroll
-        for (int j4 = 0; j4 < B / 4; ++j4) {
-            const float4 q = live ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
+            for (int j4 = 0; j4 < B / 4; ++j4) {
+                const float4 q = (live && rr < b) ? __ldcg(src + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                vr[r][4 * j4 + 0] = q.x; vr[r][4 * j4 + 1] = q.y; vr[r][4 * j4 + 2] = q.z; vr[r][4 * j4 + 3] = q.w;
+            }
         }
     }
-    leaf_qr<MGS, B, kRootRPT>(vr, b, sm, parity, ((t >> 5) * 32) / TPR);
+    leaf_qr<MGS, B, RR, TC>(vr, b, sm, parity);
     // this block's b x b slice of the tree's Q: the rows of child blockIdx.x
+    if (child == (int)blockIdx.x) {
 #pragma unroll
-    for (int r = 0; r < kRootRPT; ++r) {
-        if (cl + TPR * r == (int)blockIdx.x && rr < b)
+        for (int r = 0; r < RR; ++r) {
+            const int rr = rsub + TC * r;
+            if (rr < b)
 #pragma unroll
-            for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
+                for (int j = 0; j < B; ++j) sm.S[rr][j] = vr[r][j];
+        }
     }
     __syncthreads();
     if (blockIdx.x == 0) flat_write_r<B>(a, sm);
@@ -498,7 +499,7 @@ __device__ __forceinline__ void load_rows(const FlatArgs& a, int c0, float (&v)[
     }
 }
 
-template <int B, int RL, bool MGS>
+template <int B, int RL, int RR, bool MGS>
 __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
     extern __shared__ __align__(128) unsigned char flat_smem[];
     FlatSmem<B>& sm = *reinterpret_cast<FlatSmem<B>*>(flat_smem);
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
     flat_leaf_range(a.m, a.P0, blockIdx.x, s, e);
     float v[RL][B];
     load_rows<B, RL>(a, a.c0, v, s, e - s, a.b);
-    panel_body<B, RL, MGS>(a, v, sm, Ql, parity, s, e - s);
+    panel_body<B, RL, RR, MGS>(a, v, sm, Ql, parity, s, e - s);
 }
 
 // ---- a block of two panels and the recursion node between them, in one launch ----------
@@ -713,7 +714,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
     return true;
 }
 
-template <typename TL, int RL>
+template <typename TL, int RL, int RR>
 __global__ void __launch_bounds__(kFT, 1) block_fused_kernel(BlockArgs a) {
     extern __shared__ __align__(128) unsigned char flat_smem[];
     FlatSmem<16>& sm = *reinterpret_cast<FlatSmem<16>*>(flat_smem);
@@ -729,7 +730,7 @@ __global__ void __launch_bounds__(kFT, 1) block_fused_kernel(BlockArgs a) {
     FlatArgs pa = a.p1;
 #pragma unroll 1
     for (int pass = 0;; ++pass) {
-        if (!panel_body<16, RL, false>(pa, v, sm, Ql, parity, s, rows)) return;   // 1. / 5.
+        if (!panel_body<16, RL, RR, false>(pa, v, sm, Ql, parity, s, rows)) return;   // 1. / 5.
         if (pass == 1) break;
         if (!block_node<TL, RL>(a, v, bs, s, rows)) return;                      // 1. - 4.
         pa = a.p2;
@@ -742,7 +743,7 @@ constexpr size_t flat_smem_bytes() {
 }
 
 // Per device: the dynamic shared memory opt-in and the co-resident CTA capacity.
-template <int B, int RL, bool MGS>
+template <int B, int RL, int RR, bool MGS>
 static int flat_prepare(int& capacity) {
     constexpr int kMaxDev = 64;
     static int cap[kMaxDev];
@@ -752,11 +753,11 @@ static int flat_prepare(int& capacity) {
     if (dev < 0 || dev >= kMaxDev) return LLS_ERR_UNSUPPORTED;
     if (!done[dev]) {
         const size_t smem = flat_smem_bytes<B, RL>();
-        LLS_CUDA_TRY(cudaFuncSetAttribute(panel_flat_kernel<B, RL, MGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LLS_CUDA_TRY(cudaFuncSetAttribute(panel_flat_kernel<B, RL, RR, MGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         int sms = 0, per = 0;
         LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_flat_kernel<B, RL, MGS>, kFT, smem));
+        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_flat_kernel<B, RL, RR, MGS>, kFT, smem));
         cap[dev] = sms * per;
         done[dev] = true;
     }
@@ -764,24 +765,24 @@ static int flat_prepare(int& capacity) {
     return LLS_OK;
 }
 
-template <int B, int RL, bool MGS>
+template <int B, int RL, int RR, bool MGS>
 static int launch_flat(FlatArgs& a, cudaStream_t st) {
     int cap = 0;
-    LLS_TRY((flat_prepare<B, RL, MGS>(cap)));
+    LLS_TRY((flat_prepare<B, RL, RR, MGS>(cap)));
     if (a.P0 > cap) return LLS_ERR_UNSUPPORTED;
     const size_t smem = flat_smem_bytes<B, RL>();
     if (a.P0 == 1) {
-        panel_flat_kernel<B, RL, MGS><<<1, kFT, smem, st>>>(a);
+        panel_flat_kernel<B, RL, RR, MGS><<<1, kFT, smem, st>>>(a);
     } else {
         void* args[] = {&a};
-        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL, MGS>, dim3(a.P0), dim3(kFT), args,
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)panel_flat_kernel<B, RL, RR, MGS>, dim3(a.P0), dim3(kFT), args,
                                                  smem, st));
     }
     LLS_LAUNCH_CHECK("panel_flat", st);
     return LLS_OK;
 }
 
-template <typename TL, int RL>
+template <typename TL, int RL, int RR>
 static int launch_block(BlockArgs& a, cudaStream_t st) {
     constexpr int kMaxDev = 64;
     static int cap[kMaxDev];
@@ -791,36 +792,61 @@ static int launch_block(BlockArgs& a, cudaStream_t st) {
     if (dev < 0 || dev >= kMaxDev) return LLS_ERR_UNSUPPORTED;
     const size_t smem = block_smem_bytes<TL, RL>();
     if (!done[dev]) {
-        LLS_CUDA_TRY(cudaFuncSetAttribute(block_fused_kernel<TL, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LLS_CUDA_TRY(cudaFuncSetAttribute(block_fused_kernel<TL, RL, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         int sms = 0, per = 0;
         LLS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, block_fused_kernel<TL, RL>, kFT, smem));
+        LLS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, block_fused_kernel<TL, RL, RR>, kFT, smem));
         cap[dev] = sms * per;
         done[dev] = true;
     }
     if (a.p1.P0 > cap[dev]) return LLS_ERR_UNSUPPORTED;
     if (a.p1.P0 == 1) {
-        block_fused_kernel<TL, RL><<<1, kFT, smem, st>>>(a);
+        block_fused_kernel<TL, RL, RR><<<1, kFT, smem, st>>>(a);
     } else {
         void* args[] = {&a};
-        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)block_fused_kernel<TL, RL>, dim3(a.p1.P0), dim3(kFT), args,
+        LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)block_fused_kernel<TL, RL, RR>, dim3(a.p1.P0), dim3(kFT), args,
                                                  smem, st));
     }
     LLS_LAUNCH_CHECK("block_fused", st);
     return LLS_OK;
 }
 
-// Rows per thread and number of CTAs of a one-level panel of m rows and bucketed width bw;
-// false when the stacked leaf R factors would not fit one block.
-static bool flat_shape(int m, int bw, int& rl, int& P0) {
+// Leaf shape of a one-level panel of m rows and bucketed width bw: rows per thread of the
+// leaves (rl), number of CTAs (P0) and stacked rows per thread of the tree (rr); false when the
+// stacked leaf R factors would not fit one 1024-row block. 512-row leaves are taken wherever
+// their stack fits: 1024-row leaves with a 512-row stack (two rows per thread in the tree) were
+// measured slower at 32768 x 16 (panel 33.2 us against 30.2).
+static bool flat_long_leaves() {
+    static const bool v = [] {
+        const char* s = getenv("LLS_FLAT");
+        return s && s[0] == 'l';   // LLS_FLAT=long: 1024-row leaves wherever the stack fits
+    }();
+    return v;
+}
+
+static bool flat_shape(int m, int bw, int& rl, int& P0, int& rr) {
     const int p2 = ceil_div(m, 2 * kFT), p4 = ceil_div(m, 4 * kFT);
+    rr = 4;
     if (m <= 2 * kFT) { rl = 2; P0 = 1; }
     else if (m <= 4 * kFT) { rl = 4; P0 = 1; }
+    else if (flat_long_leaves() && p4 * bw <= kStackRows) { rl = 4; P0 = p4; }
     else if (p2 * bw <= kStackRows) { rl = 2; P0 = p2; }
     else if (p4 * bw <= kStackRows) { rl = 4; P0 = p4; }
     else return false;
     return true;
+}
+
+template <int B, bool MGS>
+static int launch_flat_shape(FlatArgs& a, int rl, int rr, cudaStream_t st) {
+    (void)rr;
+    return rl == 2 ? launch_flat<B, 2, 4, MGS>(a, st) : launch_flat<B, 4, 4, MGS>(a, st);
+}
+
+template <typename TL>
+static int launch_block_shape(BlockArgs& a, int rl, int rr, cudaStream_t st) {
+    (void)rr;
+    return rl == 2 ? launch_block<TL, 2, 4>(a, st) : launch_block<TL, 4, 4>(a, st);
 }
 
 bool flat_disabled() {
@@ -852,14 +878,11 @@ int panel_flat_qr(const PanelCall& c, cudaStream_t st) {
     a.m = c.m; a.c0 = c.c0; a.b = c.b; a.lowp = c.lowp;
     a.rbuf = c.rbuf; a.bar = c.cnt + kFlatBarWord; a.err = c.err;
     const int bw = c.b <= 8 ? 8 : 16;   // the stack holds TPR * 4 children of B rows each
-    int rl;
-    if (!flat_shape(c.m, bw, rl, a.P0)) return LLS_ERR_UNSUPPORTED;
-    if (c.leaf == 1) {
-        if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, true>(a, st) : launch_flat<8, 4, true>(a, st);
-        return rl == 2 ? launch_flat<16, 2, true>(a, st) : launch_flat<16, 4, true>(a, st);
-    }
-    if (c.b <= 8) return rl == 2 ? launch_flat<8, 2, false>(a, st) : launch_flat<8, 4, false>(a, st);
-    return rl == 2 ? launch_flat<16, 2, false>(a, st) : launch_flat<16, 4, false>(a, st);
+    int rl, rr;
+    if (!flat_shape(c.m, bw, rl, a.P0, rr)) return LLS_ERR_UNSUPPORTED;
+    if (c.leaf == 1)
+        return c.b <= 8 ? launch_flat_shape<8, true>(a, rl, rr, st) : launch_flat_shape<16, true>(a, rl, rr, st);
+    return c.b <= 8 ? launch_flat_shape<8, false>(a, rl, rr, st) : launch_flat_shape<16, false>(a, rl, rr, st);
 }
 
 size_t block_fused_part_floats() { return (size_t)kBlockMaxP0 * 256; }
@@ -867,8 +890,8 @@ size_t block_fused_part_floats() { return (size_t)kBlockMaxP0 * 256; }
 bool block_fused_supported(const BlockCall& c) {
     if (flat_disabled() || (c.lowp != 0 && c.lowp != 1)) return false;
     if (c.w1 <= 8 || c.w1 > 16 || c.w2 < 1 || c.w2 > c.w1) return false;
-    int rl, P0;
-    return flat_shape(c.m, 16, rl, P0) && P0 <= kBlockMaxP0 && (size_t)P0 * 256 <= c.part_floats;
+    int rl, P0, rr;
+    return flat_shape(c.m, 16, rl, P0, rr) && P0 <= kBlockMaxP0 && (size_t)P0 * 256 <= c.part_floats;
 }
 
 int block_fused_qr(const BlockCall& c, cudaStream_t st) {
@@ -878,14 +901,14 @@ int block_fused_qr(const BlockCall& c, cudaStream_t st) {
     p.W = c.W; p.ldw = c.ldw; p.Wh = c.Wh; p.ldh = c.ldh; p.R = c.R; p.ldr = c.ldr;
     p.m = c.m; p.c0 = c.c0; p.b = c.w1; p.lowp = c.lowp;
     p.rbuf = c.rbuf; p.bar = c.cnt + kFlatBarWord; p.err = c.err;
-    int rl;
-    flat_shape(c.m, 16, rl, p.P0);
+    int rl, rr;
+    flat_shape(c.m, 16, rl, p.P0, rr);
     a.p2 = p;
     a.p2.c0 = c.c0 + c.w1;
     a.p2.b = c.w2;
     a.part = c.part; a.colmax = c.colmax; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;
-    if (c.lowp == 0) return rl == 2 ? launch_block<__half, 2>(a, st) : launch_block<__half, 4>(a, st);
-    return rl == 2 ? launch_block<__nv_bfloat16, 2>(a, st) : launch_block<__nv_bfloat16, 4>(a, st);
+    if (c.lowp == 0) return launch_block_shape<__half>(a, rl, rr, st);
+    return launch_block_shape<__nv_bfloat16>(a, rl, rr, st);
 }
 
 }  // namespace lls

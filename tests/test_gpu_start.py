@@ -18,6 +18,7 @@ import pytest
 import torch
 
 from oracle import direct, metrics
+from parity import kw_bound as parity_kw_bound
 from paper_1912_05508_gb300 import lls, synth
 
 pytestmark = pytest.mark.gpu
@@ -32,13 +33,7 @@ def prob():
 
 
 def kw_bound(A32, R):
-    """The backward error the stop test guarantees: the solver stops on
-    eta_est = ||R^-T A^T r|| / (||A||_F ||x||) <= 1e-12, and the Karlson-Walden estimate obeys
-    eta_kw <= ||(A^T A)^-1/2 R^T|| eta_est = eta_est / sigma_min(A R^-1)."""
-    A = np.asarray(A32, dtype=np.float64)
-    Rinv = np.linalg.inv(np.asarray(R.cpu().numpy(), dtype=np.float64))
-    smin = np.linalg.svd(A @ Rinv, compute_uv=False)[-1]
-    return 1e-12 / smin * (1 + 1e-6)
+    return parity_kw_bound(A32, R.cpu().numpy())
 
 
 @pytest.mark.parametrize("krylov", ["cgls", "lsqr"])
