@@ -133,17 +133,33 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
             cur[r] = c;
             nx[r] = d;
         }
+        // products for columns j, j + 1 in the two halves of packed FMAs (each half is the
+        // same single-rounding chain over the rows as a scalar FMA chain)
         float x[N];
 #pragma unroll
-        for (int j = 0; j < NQ; ++j) {
-            float p1 = 0.f, p2 = 0.f;
+        for (int j = 0; j < NQ; j += 2) {
+            if (j + 1 < NQ) {
+                float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int r = 0; r < RA; ++r) {
-                p1 = fmaf(v[r][j], cur[r], p1);
-                p2 = fmaf(v[r][j], nx[r], p2);
+                for (int r = 0; r < RA; ++r) {
+                    const float2 vv = make_float2(v[r][j], v[r][j + 1]);
+                    p1 = __ffma2_rn(vv, make_float2(cur[r], cur[r]), p1);
+                    p2 = __ffma2_rn(vv, make_float2(nx[r], nx[r]), p2);
+                }
+                x[j] = j < K ? p1.x : 0.f;
+                x[j + 1] = j + 1 < K ? p1.y : 0.f;
+                x[NQ + 1 + j] = j < K ? p2.x : 0.f;
+                x[NQ + 2 + j] = j + 1 < K ? p2.y : 0.f;
+            } else {
+                float p1 = 0.f, p2 = 0.f;
+#pragma unroll
+                for (int r = 0; r < RA; ++r) {
+                    p1 = fmaf(v[r][j], cur[r], p1);
+                    p2 = fmaf(v[r][j], nx[r], p2);
+                }
+                x[j] = j < K ? p1 : 0.f;
+                x[NQ + 1 + j] = j < K ? p2 : 0.f;
             }
-            x[j] = j < K ? p1 : 0.f;
-            x[NQ + 1 + j] = j < K ? p2 : 0.f;
         }
         {
             float p1 = 0.f, p2 = 0.f;
@@ -159,26 +175,30 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
 
         // two interleaved chains per sum (even / odd j) halve the dependent FMA depth
         float h2[NQ > 0 ? NQ : 1], g[NQ > 0 ? NQ : 1];
-        float hh0 = 0.f, hh1 = 0.f, hg0 = 0.f, hg1 = 0.f;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
             h2[j] = t[j];                        // zero for j >= K (masked products)
             g[j] = t[NQ + 1 + j];
-            if (j & 1) { hh1 = fmaf(h2[j], h2[j], hh1); hg1 = fmaf(h2[j], g[j], hg1); }
-            else { hh0 = fmaf(h2[j], h2[j], hh0); hg0 = fmaf(h2[j], g[j], hg0); }
         }
-        const float hh = hh0 + hh1, hg = hg0 + hg1;
+        float2 hh2 = make_float2(0.f, 0.f), hg2 = make_float2(0.f, 0.f);   // (even j, odd j)
+#pragma unroll
+        for (int j = 0; j < NQ; j += 2) {
+            const float2 hv = make_float2(h2[j], j + 1 < NQ ? h2[j + 1] : 0.f);
+            const float2 gv = make_float2(g[j], j + 1 < NQ ? g[j + 1] : 0.f);
+            hh2 = __ffma2_rn(hv, hv, hh2);
+            hg2 = __ffma2_rn(hv, gv, hg2);
+        }
+        const float hh = hh2.x + hh2.y, hg = hg2.x + hg2.y;
         const float nn = t[NQ];
         float acc[R];
 #pragma unroll
         for (int r = 0; r < RA; ++r) {
-            float a0 = cur[r], a1 = 0.f;
+            float2 a2 = make_float2(cur[r], 0.f);   // (even j, odd j) chains
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                if (j & 1) a1 = fmaf(-v[r][j], h2[j], a1);
-                else a0 = fmaf(-v[r][j], h2[j], a0);
-            }
-            acc[r] = a0 + a1;
+            for (int j = 0; j < NQ; j += 2)
+                a2 = __ffma2_rn(make_float2(-v[r][j], j + 1 < NQ ? -v[r][j + 1] : 0.f),
+                                make_float2(h2[j], j + 1 < NQ ? h2[j + 1] : 0.f), a2);
+            acc[r] = a2.x + a2.y;
         }
         float normsq = nn - hh;
         if (!(normsq >= 0.25f * nn)) {   // the second pass removed much of the norm: reduce it directly
@@ -209,13 +229,12 @@ __device__ __forceinline__ void cgs2_group(float (&v)[R][B], int b, FlatSmem<B>&
 #pragma unroll
         for (int r = 0; r < RA; ++r) {
             const float q = acc[r] * inv;
-            float a0 = nx[r], a1 = 0.f;
+            float2 a2 = make_float2(nx[r], 0.f);    // (even j, odd j) chains
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                if (j & 1) a1 = fmaf(-v[r][j], g[j], a1);
-                else a0 = fmaf(-v[r][j], g[j], a0);
-            }
-            const float a = fmaf(-q, gq, a0 + a1);
+            for (int j = 0; j < NQ; j += 2)
+                a2 = __ffma2_rn(make_float2(-v[r][j], j + 1 < NQ ? -v[r][j + 1] : 0.f),
+                                make_float2(g[j], j + 1 < NQ ? g[j + 1] : 0.f), a2);
+            const float a = fmaf(-q, gq, a2.x + a2.y);
 #pragma unroll
             for (int u = 0; u < KG; ++u) {
                 if (s == u) v[r][K0 + u] = q;
@@ -468,13 +487,13 @@ __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B],
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const float4* Sk = reinterpret_cast<const float4*>(&sm.S[k][0]);
+            const float2 qk = make_float2(q[k], q[k]);
 #pragma unroll
             for (int j4 = 0; j4 < B / 4; ++j4) {
                 const float4 s4 = Sk[j4];
-                o[4 * j4 + 0] = fmaf(q[k], s4.x, o[4 * j4 + 0]);
-                o[4 * j4 + 1] = fmaf(q[k], s4.y, o[4 * j4 + 1]);
-                o[4 * j4 + 2] = fmaf(q[k], s4.z, o[4 * j4 + 2]);
-                o[4 * j4 + 3] = fmaf(q[k], s4.w, o[4 * j4 + 3]);
+                float2 lo = __ffma2_rn(qk, make_float2(s4.x, s4.y), make_float2(o[4 * j4 + 0], o[4 * j4 + 1]));
+                float2 hi = __ffma2_rn(qk, make_float2(s4.z, s4.w), make_float2(o[4 * j4 + 2], o[4 * j4 + 3]));
+                o[4 * j4 + 0] = lo.x; o[4 * j4 + 1] = lo.y; o[4 * j4 + 2] = hi.x; o[4 * j4 + 3] = hi.y;
             }
         }
 #pragma unroll
