@@ -222,10 +222,17 @@ def run_reference(args):
 # kernel's source file at the time of the capture. A kernel whose source has changed since
 # reports null until it is captured again. tc_projection is the product kernel alone (the
 # split-K reduce is a separate, small launch).
-NCU_TRAFFIC = {"block": (4336640 + 0, "panel_flat.cu", "2d7b019878166ac2"),
-               "tc_projection": (335482624 + 23355136, "gemm_tc.cu", "7aff50032693834b"),
-               "tc_update": (415756288 + 224454400, "gemm_tc.cu", "7aff50032693834b"),
-               "cgls": (24629498624 + 364217344, "krylov.cu", "d7dd0203f719dbb7")}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture per kernel
+# (summaries under profiles/), valid only while the kernel's source is the captured one:
+# key -> (captured bytes, captured units, source file, sha256 prefix of that file). The bench
+# scales the bytes by its own units over the captured units, since every term of the traffic
+# grows in proportion: block launches of the same shape; the products' rows m (the capture
+# runs m = 16384, half the bench's top node); the Krylov phase's algorithmic bytes (the capture
+# runs 16384 x 4096 for 6 iterations: 15 passes over A and 14 triangular products).
+NCU_TRAFFIC = {"tc_projection": (134252288 + 3640064, 16384, "gemm_persist.cu", "e6322d58344b9a4e"),
+               "tc_update": (209890560 + 82324480, 16384, "gemm_persist.cu", "e6322d58344b9a4e"),
+               "cgls": (4415026000 + 64646912, 15 * 4.0 * 16384 * 4096 + 14 * 4.0 * 4096 * 4097 / 2,
+                        "krylov.cu", "3b11ff6146427a6d")}
 
 
 def source_digest(name):
@@ -238,14 +245,14 @@ def source_digest(name):
         return None
 
 
-def ncu_traffic(key):
-    """The captured DRAM bytes per launch of a kernel, or None when there is no capture of the
-    kernel as its source stands."""
+def ncu_traffic(key, units=1.0):
+    """DRAM bytes per launch of a kernel, from its capture scaled to `units` (see NCU_TRAFFIC),
+    or None when there is no capture of the kernel as its source stands."""
     rec = NCU_TRAFFIC.get(key)
     if rec is None:
         return None
-    nbytes, src, digest = rec
-    return nbytes if source_digest(src) == digest else None
+    nbytes, cunits, src, digest = rec
+    return nbytes * units / cunits if source_digest(src) == digest else None
 
 
 def max_over_ranks(value, world_size, device):
@@ -381,7 +388,7 @@ def kernel_rooflines(m, n, pw, prec, stream, dev, hbm_peak, tc_peak):
                     "unit": "TFLOP/s", "us_per_launch": t * 1e3, "algorithmic_flops_per_launch": fl}
     for k, v in out.items():
         v["frac"] = v["achieved"] / v["peak"]
-        v["traffic"] = ncu_traffic(k)
+        v["traffic"] = ncu_traffic(k, m if k.startswith("tc_") else 1.0)
     return out
 
 
@@ -901,7 +908,7 @@ def main():
     kernels = kernel_rooflines(m, n, pw, args.prec, stream, dev, hbm_peak, tc_peak)
     kernels["cgls"] = {"kernel": f"{args.krylov}_kernel (persistent {args.krylov.upper()} iteration, whole Krylov phase)", "bound": "hbm",
                        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                       "traffic": ncu_traffic("cgls"), "algorithmic_bytes_per_launch": kry_bytes}
+                       "traffic": ncu_traffic("cgls", kry_bytes), "algorithmic_bytes_per_launch": kry_bytes}
     # the block kernel (two panels and the node between them) has the largest share of the
     # solve in the ncu launch list
     roofline = dict(kernels["block"] if "block" in kernels else kernels["panel"])

@@ -46,6 +46,28 @@ def run(out):
         res[f"batch_x{i}"] = xs[i].cpu().numpy()
         res[f"batch_gA{i}"] = gAs[i].cpu().numpy()
         res[f"batch_gb{i}"] = gbs[i].cpu().numpy()
+    # the kernel-level panel and block entry points at a one-level shape of 64 leaves
+    st = torch.cuda.current_stream().cuda_stream
+    for (m, b) in [(32768, 16), (5000, 13), (9000, 8)]:
+        W = lls.colmajor(torch.randn(m, b, generator=g, dtype=torch.float64).float())
+        Wh = torch.zeros((b, m), dtype=torch.float16, device="cuda").t()
+        R = torch.zeros((b, b), dtype=torch.float32, device="cuda").t()
+        ws = lls.workspace(lls.lls_panel_qr_workspace_size(m, b)).zero_()
+        for _ in range(2):   # the second call reuses the workspace as left by the first
+            W2 = W.clone()
+            assert lls.lls_panel_qr(m, b, lls.PREC["fp16"], W2.data_ptr(), m, Wh.data_ptr(), m, R.data_ptr(), b,
+                                    ws.data_ptr(), ws.numel(), st) == 0
+        res[f"panel_Q_{m}_{b}"] = W2.cpu().numpy()
+        res[f"panel_R_{m}_{b}"] = R.cpu().numpy()
+    m = 32768
+    W = lls.colmajor(torch.randn(m, 32, generator=g, dtype=torch.float64).float())
+    Wh = torch.zeros((32, m), dtype=torch.float16, device="cuda").t()
+    R = torch.zeros((32, 32), dtype=torch.float32, device="cuda").t()
+    ws = lls.workspace(lls.lls_panel_block_qr_workspace_size(m, 16, 16)).zero_()
+    assert lls.lls_panel_block_qr(m, 16, 16, lls.PREC["fp16"], W.data_ptr(), m, Wh.data_ptr(), m, R.data_ptr(), 32,
+                                  ws.data_ptr(), ws.numel(), st) == 0
+    res["block_Q"] = W.cpu().numpy()
+    res["block_R"] = R.cpu().numpy()
     torch.cuda.synchronize()
     np.savez(out, **res)
 

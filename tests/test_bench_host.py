@@ -71,8 +71,11 @@ def test_ncu_traffic_only_for_the_captured_source(monkeypatch):
     src = "panel_flat.cu"
     digest = bench.source_digest(src)
     assert digest is not None and len(digest) == 16
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, src, digest))
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, 1.0, src, digest))
     assert bench.ncu_traffic("probe") == 1234
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, src, "0" * 16))
+    # captured on half the units the bench runs: the bytes scale in proportion
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1000, 16384, src, digest))
+    assert bench.ncu_traffic("probe", 32768) == 2000
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "probe", (1234, 1.0, src, "0" * 16))
     assert bench.ncu_traffic("probe") is None
     assert bench.ncu_traffic("no such kernel") is None
