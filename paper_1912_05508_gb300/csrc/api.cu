@@ -128,7 +128,7 @@ struct QrWs {
     uint8_t* QT; int ldq; int* sQ;   // FP8 only: row-major copy of Q and its column exponents
     float* R1; float* Rt;            // re-orthogonalization: the first pass's R, and R2 R1 (n x n)
     float* rbuf; float* qbuf; unsigned* cnt; size_t cnt_words;
-    unsigned* colmax; unsigned* nbar;   // fused narrow nodes: column maxima (n), grid barrier (2)
+    unsigned* nbar;                  // fused narrow nodes: grid barrier (2)
     int* err;
     double* dinfo;     // 16 doubles of device-side results
     double* red;       // 8192 doubles of reduction partials
@@ -167,7 +167,6 @@ static void qr_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w) 
     w.qbuf = ar.take<float>(qb);
     w.cnt = ar.take<unsigned>(cw);
     w.cnt_words = cw;
-    w.colmax = ar.take<unsigned>((size_t)n);
     w.nbar = ar.take<unsigned>(4);      // the grid barrier's 64-bit word, 8-byte aligned
     w.err = ar.take<int>(16);
     w.dinfo = ar.take<double>(16);
@@ -247,7 +246,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
         bc.W = c.w.W; bc.ldw = c.w.ldw; bc.Wh = c.w.Wh; bc.ldh = c.w.ldh; bc.R = c.R; bc.ldr = c.ldr;
         bc.m = c.m; bc.c0 = c0; bc.w1 = w1; bc.w2 = w2; bc.lowp = c.lowp;
         bc.rbuf = c.w.rbuf; bc.cnt = c.w.cnt; bc.part = c.w.part; bc.part_floats = c.w.part_floats;
-        bc.colmax = c.w.colmax + c0 + w1; bc.err = c.w.err;
+        bc.err = c.w.err;
         const int r = block_fused_qr(bc, c.st);
         if (r != LLS_ERR_UNSUPPORTED) return r;
     }
@@ -267,7 +266,7 @@ static int qr_rec(QrCtx& c, int c0, int w) {
             nc.W = c.w.W; nc.ldw = c.w.ldw; nc.Wh = c.w.Wh; nc.ldh = c.w.ldh;
             nc.m = c.m; nc.c0 = c0; nc.w1 = w1; nc.w2 = w2; nc.lowp = c.lowp;
             nc.R = c.R; nc.ldr = c.ldr; nc.part = c.w.part; nc.part_floats = c.w.part_floats;
-            nc.R12l = c.w.R12l; nc.f = c.w.f; nc.colmax = c.w.colmax; nc.bar = c.w.nbar; nc.err = c.w.err;
+            nc.R12l = c.w.R12l; nc.f = c.w.f; nc.bar = c.w.nbar; nc.err = c.w.err;
             const int r = node_fused(nc, c.st);
             if (r != LLS_ERR_UNSUPPORTED) {
                 LLS_TRY(r);
@@ -300,7 +299,6 @@ static int qr_rec(QrCtx& c, int c0, int w) {
 static int run_qr(int m, int n, const float* A, int lda, float* R, int ldr, const lls_options& o,
                   const Knobs& k, QrWs& w, cudaStream_t st, ColumnGate* gate = nullptr, double* anorm2 = nullptr) {
     LLS_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * w.cnt_words, st));
-    LLS_CUDA_TRY(cudaMemsetAsync(w.colmax, 0, sizeof(unsigned) * (size_t)n, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.nbar, 0, sizeof(unsigned) * 4, st));
     LLS_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 16, st));
     if (!gate) {
@@ -528,13 +526,12 @@ static int lls_panel_qr_impl(int m, int b, int prec, float* W, int ldw, void* Wh
 }
 
 struct BlockWs {
-    PanelWs p; float* part; unsigned* colmax;
+    PanelWs p; float* part;
 };
 
 static void block_layout(WsArena& ar, int m, BlockWs& w) {
     panel_layout(ar, m, w.p);
     w.part = ar.take<float>(block_fused_part_floats());
-    w.colmax = ar.take<unsigned>(16);
 }
 
 size_t lls_panel_block_qr_workspace_size(int m, int w1, int w2) {
@@ -559,7 +556,7 @@ static int lls_panel_block_qr_impl(int m, int w1, int w2, int prec, float* W, in
     bc.W = W; bc.ldw = ldw; bc.Wh = Wh; bc.ldh = ldh; bc.R = R; bc.ldr = ldr;
     bc.m = m; bc.c0 = 0; bc.w1 = w1; bc.w2 = w2; bc.lowp = lowp_code(prec);
     bc.rbuf = w.p.rbuf; bc.cnt = w.p.cnt; bc.part = w.part; bc.part_floats = block_fused_part_floats();
-    bc.colmax = w.colmax; bc.err = w.p.err;
+    bc.err = w.p.err;
     if (!block_fused_supported(bc)) return LLS_ERR_UNSUPPORTED;
     const size_t wt = (size_t)(w1 + w2);
     LLS_CUDA_TRY(cudaMemset2DAsync(R, sizeof(float) * (size_t)ldr, 0, sizeof(float) * wt, wt, stream));

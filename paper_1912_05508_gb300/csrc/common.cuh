@@ -211,7 +211,10 @@ __device__ __forceinline__ float warp_max_f(float v) {
 // last arrival resets the count and advances the generation with a single add of
 // 2^32 - nblocks. The count is left at zero. The wait is bounded by kSpinLimitNs, after which
 // the error word is set and the caller must return. Returns false when the barrier timed out
-// or an error was already flagged.
+// or an error was flagged before this arrival. The error word is read together with the
+// arrival (both loads in flight at once), so a flag raised by another CTA while this one
+// waits is seen at the next barrier: a CTA that returned on an error never arrives there,
+// and the waiting CTAs read the error word while they poll.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
     __syncthreads();
@@ -219,9 +222,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
     if (threadIdx.x == 0) {
         unsigned long long* word = reinterpret_cast<unsigned long long*>(bar);
         __threadfence();
+        const int e0 = *(volatile int*)err;
         const unsigned long long old = atomicAdd(word, 1ull);
         const unsigned gen = (unsigned)(old >> 32);
-        int ok = 1;
+        int ok = e0 == DEV_OK ? 1 : 0;
         if ((unsigned)(old & 0xffffffffull) == nblocks - 1) {
             atomicAdd(word, (1ull << 32) - (unsigned long long)nblocks);
         } else {
@@ -240,7 +244,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
             }
         }
         __threadfence();
-        if (*(volatile int*)err != DEV_OK) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

@@ -52,7 +52,6 @@ struct BlockCall {
     int lowp;              // 0 FP16, 1 BF16
     float* rbuf; unsigned* cnt;
     float* part; size_t part_floats;
-    unsigned* colmax;      // 16 words, zero on entry (left zero)
     int* err;
 };
 int block_fused_qr(const BlockCall& c, cudaStream_t st);
@@ -106,7 +105,6 @@ struct NodeCall {
     float* R; int ldr;
     float* part; size_t part_floats;              // >= node_fused_part_floats(m)
     void* R12l; int* f;                           // >= 32 x 32 low-precision values; w2 ints
-    unsigned* colmax;                             // n words, zero on entry (left zero)
     unsigned* bar;                                // 2 words, zero on entry (left zero)
     int* err;
 };

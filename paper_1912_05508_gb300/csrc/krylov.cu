@@ -32,6 +32,8 @@
 // branch decisions; the grid barriers are bounded (common.cuh) and report a timeout.
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -42,9 +44,7 @@ constexpr int kKWarps = kKThreads / 32;
 constexpr int kRowTile = 1024;    // rows per A t work item (four rows per thread)
 constexpr int kColChunkMin = 48;  // columns per A t work item: chosen per launch in [48, 96]
 constexpr int kColChunkMax = 96;  // so that the items fill whole waves of the grid
-constexpr int kRowChunk = 1024;   // rows per A^T r work item (staged in shared memory); 4096
-                                  // items at m = 32768, n = 4096 fill 9 waves of 456 CTAs
-constexpr int kColGroup = 32;     // columns per A^T r work item (4 per warp)
+constexpr int kRowChunkCap = 4096;   // rows of r a CTA stages for the A^T r pass (at least; n when wider)
 constexpr int kMaxRestarts = 3;
 constexpr int kPrefetchCols = 8;  // L2 prefetch distance of the A passes (columns, or 32-lane steps)
 constexpr int kNPart = 4;         // block-partial slots
@@ -66,6 +66,7 @@ struct KArgs {
     int max_iter, target, x_zero;
     int nrt, nck, nrc, ncg;
     int colchunk;                // columns per A t work item
+    int at_rows, at_cpr;         // A^T r pass: rows per row chunk, CTAs per row chunk
     double *v1part, *v2part;     // fused engine: per-CTA partial A^T q and A^T r, [grid][n]
     int aligned16;               // A and lda allow 16-byte copies of 4-row column segments
     const float4* At;            // row-block copy of A: At[blk * n + j] = A[4 blk .. 4 blk + 3, j], or null
@@ -313,69 +314,70 @@ __device__ void a_times_partials(const KArgs& a) {
 }
 
 // upart[rc][j] = sum_{i in row chunk rc} A[i, j] * v_i for v (length m) in global memory.
-// v's chunk is staged in shared memory; each lane reads 4 consecutive rows per step.
-// Each CTA takes a contiguous range of the items in row-chunk-major order (ranges differ in
-// length by at most one), so it stages a row chunk of v once for all its items in that chunk.
+// The m rows are cut into nrc chunks of at_rows rows; CTA c works on chunk c / at_cpr only, so
+// it stages that chunk of v in shared memory once per pass (CTAs from nrc * at_cpr on have no
+// work here). A work item is one column per warp: the column group g covers columns
+// 8 g .. 8 g + 7. The at_cpr CTAs of a chunk take the groups in interleaved order from the last
+// group down (CTA k of the chunk: g = ncg - 1 - k, then g - at_cpr, ...), so at any time the
+// grid reads one band of columns, and the pass starts with the columns that the A t pass before
+// it (increasing columns) read last and that are still in L2. Each lane reads 4 consecutive
+// rows per step.
 __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
                                   const float2* __restrict__ vdf = nullptr) {
-    const int items = a.nrc * a.ncg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int it0 = (int)((long long)blockIdx.x * items / gridDim.x);
-    const int it1 = (int)((long long)(blockIdx.x + 1) * items / gridDim.x);
-    int staged = -1;
-    for (int it = it0; it < it1; ++it) {
-        const int rc = it / a.ncg, cg = it % a.ncg;
-        const int r0 = rc * kRowChunk, rows = min(a.m - r0, kRowChunk);
-        if (rc != staged) {                       // uniform across the CTA
-            __syncthreads();
-            if (vdf) {
-                for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
-            } else {
-                for (int i = threadIdx.x; i < rows; i += kKThreads) {
-                    float hi, lo;
-                    split_df(__ldcg(v + r0 + i), hi, lo);
-                    k_dsm[i] = make_float2(hi, lo);
-                }
-            }
-            __syncthreads();
-            staged = rc;
+    const int K = a.at_cpr, L = a.at_rows;
+    const int rc = (int)blockIdx.x / K, k = (int)blockIdx.x % K;
+    if (rc >= a.nrc) return;                      // uniform across the CTA
+    const int r0 = rc * L, rows = min(a.m - r0, L);
+    if (rows <= 0) return;
+    __syncthreads();                              // earlier users of k_dsm are done
+    if (vdf) {
+        for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
+    } else {
+        for (int i = threadIdx.x; i < rows; i += kKThreads) {
+            float hi, lo;
+            split_df(__ldcg(v + r0 + i), hi, lo);
+            k_dsm[i] = make_float2(hi, lo);
         }
-        if (!LLS_INB(r0 >= 0 && r0 + rows <= a.m)) continue;
-        const bool full = a.aligned16 && rows == kRowChunk;
-        for (int jj = 0; jj < kColGroup / kKWarps; ++jj) {
-            const int j = cg * kColGroup + warp * (kColGroup / kKWarps) + jj;
-            if (j >= a.n) break;
-            const float* col = a.A + (size_t)j * a.lda + r0;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-            if (full && jj + 1 < kColGroup / kKWarps && j + 1 < a.n)   // the warp's next column, 4 KB
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(col + a.lda + 32 * (threadIdx.x & 31)));
-            if (full) {
-                const float4* col4 = reinterpret_cast<const float4*>(col);
+    }
+    __syncthreads();
+    if (!LLS_INB(r0 >= 0 && r0 + rows <= a.m && rows <= L)) return;
+    const bool full = a.aligned16 && (rows & 3) == 0;
+    const int nq = rows >> 2;
+    for (int g = a.ncg - 1 - k; g >= 0; g -= K) {
+        const int j = g * kKWarps + warp;
+        if (j >= a.n) continue;
+        const float* col = a.A + (size_t)j * a.lda + r0;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+        if (full) {
+            const float4* col4 = reinterpret_cast<const float4*>(col);
 #pragma unroll 4
-                for (int q = lane; q < kRowChunk / 4; q += 32) {
-                    if (q + 32 * kPrefetchCols < kRowChunk / 4)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(col4 + q + 32 * kPrefetchCols));
-                    const float4 av = __ldg(col4 + q);
-                    const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
-                    dot2_step(s0, c0, av.x, w0.x, w0.y);
-                    dot2_step(s1, c1, av.y, w1.x, w1.y);
-                    dot2_step(s2, c2, av.z, w2.x, w2.y);
-                    dot2_step(s3, c3, av.w, w3.x, w3.y);
-                }
-            } else {
-                for (int i = lane; i < rows; i += 32) {
-                    const float2 w = k_dsm[i];
-                    dot2_step(s0, c0, __ldg(col + i), w.x, w.y);
-                }
+            for (int q = lane; q < nq; q += 32) {
+                if (q + 32 * kPrefetchCols < nq)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(col4 + q + 32 * kPrefetchCols));
+                const float4 av = __ldg(col4 + q);
+                const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
+                dot2_step(s0, c0, av.x, w0.x, w0.y);
+                dot2_step(s1, c1, av.y, w1.x, w1.y);
+                dot2_step(s2, c2, av.z, w2.x, w2.y);
+                dot2_step(s3, c3, av.w, w3.x, w3.y);
             }
-            // combine the four chains, then the 32 lanes, in double-float
-            float t, e;
-            two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
-            two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
-            two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
-            warp_sum_df(s0, c0);
-            if (lane == 0 && LLS_INB(rc < a.nrc && j < a.n)) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
+            // the start of this warp's next column (4 KB) into L2
+            if (g - K >= 0 && (g - K) * kKWarps + warp < a.n && 32 * lane < rows)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(col - (size_t)K * kKWarps * a.lda + 32 * lane));
+        } else {
+            for (int i = lane; i < rows; i += 32) {
+                const float2 w = k_dsm[i];
+                dot2_step(s0, c0, __ldg(col + i), w.x, w.y);
+            }
         }
+        // combine the four chains, then the 32 lanes, in double-float
+        float t, e;
+        two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+        two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
+        two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
+        warp_sum_df(s0, c0);
+        if (lane == 0 && LLS_INB(rc < a.nrc && j < a.n)) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
     }
 }
 
@@ -1142,7 +1144,7 @@ adjoint_kernel(AdjArgs aa) {
 
 // ---------------------------------------------------------------------------------------
 struct KLayout {
-    int nrt, nck, nrc, ncg, colchunk;
+    int nrt, nck, nrc, ncg, colchunk, at_rows, at_cpr;
     size_t off_r, off_q, off_t, off_p, off_s, off_u, off_d, off_qpart, off_upart, off_v1, off_v2, off_bpart,
         off_bar, off_rdf, off_tdf, off_udf, off_pdf, off_tile, total;
 };
@@ -1169,13 +1171,36 @@ static int pick_col_chunk(int m, int n, int grid) {
     return best;
 }
 
+// Rows staged for the A^T r pass at most (the vector space reserved in shared memory).
+static int at_rows_cap(int n) { return n > kRowChunkCap ? n : kRowChunkCap; }
+
+// The A^T r pass: R row chunks of L rows (L a multiple of 4, at most at_rows_cap(n)), K = grid / R
+// CTAs per chunk, groups of 8 columns. Every CTA streams L x 8 elements per item, so the pass
+// takes about ceil(ncg / K) * L; the R with the least such time wins (fewest chunks on ties).
+// At m = 32768, n = 4096 on 456 CTAs: 8 chunks of 4096 rows, 57 CTAs each, 512 groups in at
+// most 9 items per CTA (8.98 on average).
+static void at_plan(int m, int n, int grid, int& R, int& L, int& K) {
+    const long long ncg = ceil_div(n, kKWarps);
+    const int cap = at_rows_cap(n);
+    long long best = -1;
+    R = 1; L = (m + 3) & ~3; K = grid < 1 ? 1 : grid;
+    for (int r = 1; r <= grid; ++r) {
+        const int l = (ceil_div(m, r) + 3) & ~3;
+        if (l > cap) continue;
+        if ((long long)(r - 1) * l >= m) break;   // the last chunk would be empty
+        const int k = grid / r;
+        const long long cost = (ncg + k - 1) / k * l;
+        if (best < 0 || cost < best) { best = cost; R = r; L = l; K = k; }
+    }
+}
+
 static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     KLayout L;
     L.nrt = ceil_div(m, kRowTile);
     L.colchunk = pick_col_chunk(m, n, grid < 1 ? 1 : grid);
     L.nck = ceil_div(n, L.colchunk);
-    L.nrc = ceil_div(m, kRowChunk);
-    L.ncg = ceil_div(n, kColGroup);
+    at_plan(m, n, grid < 1 ? 1 : grid, L.nrc, L.at_rows, L.at_cpr);
+    L.ncg = ceil_div(n, kKWarps);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
     L.off_r = take(8ull * m);
@@ -1186,7 +1211,10 @@ static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     L.off_u = take(8ull * n);
     L.off_d = take(8ull * n);
     L.off_qpart = take(8ull * m * ceil_div(n, kColChunkMin));   // room for the narrowest width (most partials)
-    L.off_upart = take(8ull * n * L.nrc);
+    // room for the most row chunks any grid up to this one can take, so a scratch sized for
+    // the largest grid holds every smaller grid's layout
+    const long long rmax = std::min<long long>(grid < 1 ? 1 : grid, ceil_div(m, 4));
+    L.off_upart = take(8ull * n * (size_t)rmax);
     L.off_v1 = take(8ull * n * grid);
     L.off_v2 = take(8ull * n * grid);
     L.off_bpart = take(8ull * kNPart * grid);
@@ -1317,6 +1345,7 @@ static int launch_cgls(KArgs& a, const KrylovCall& c, char* base, size_t smem, i
     a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
     a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
     a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg; a.colchunk = L.colchunk;
+    a.at_rows = L.at_rows; a.at_cpr = L.at_cpr;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&a};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kKThreads), args, smem, st));
@@ -1357,7 +1386,7 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
             default: return launch_cgls<16>(a, c, base, smem, sms, st);
         }
     }
-    a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
+    a.vec_floats = 2 * at_rows_cap(c.n);
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;
     if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
     return launch_cgls<0>(a, c, base, smem, sms, st, lsqr);
@@ -1374,7 +1403,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.tol = c.tol; a.max_iter = c.max_iter; a.target = LLS_TARGET_FP64; a.x_zero = 1;
     a.hist = nullptr;
     a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
-    a.vec_floats = 2 * (c.n > kRowChunk ? c.n : kRowChunk);
+    a.vec_floats = 2 * at_rows_cap(c.n);
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;
     if (smem > 220 * 1024) return LLS_ERR_UNSUPPORTED;
     aa.g = c.g; aa.bvec = c.b; aa.xsol = c.x; aa.gA = c.gA; aa.ldga = c.ldga; aa.gb = c.gb;
@@ -1401,6 +1430,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.rdf = (float2*)(base + L.off_rdf); a.tdf = (float2*)(base + L.off_tdf);
     a.udf = (float2*)(base + L.off_udf); a.pdf = (float2*)(base + L.off_pdf);
     a.nrt = L.nrt; a.nck = L.nck; a.nrc = L.nrc; a.ncg = L.ncg; a.colchunk = L.colchunk;
+    a.at_rows = L.at_rows; a.at_cpr = L.at_cpr;
     LLS_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
     void* args[] = {&aa};
     LLS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)adjoint_kernel, dim3(grid), dim3(kKThreads), args, smem, st));

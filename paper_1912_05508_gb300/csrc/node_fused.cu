@@ -2,18 +2,22 @@
 // launch, with the same rounding points as the tensor-core path:
 //
 //   A. every CTA owns 256 rows: it loads its rows of Q1 (product precision) and A2 (FP32)
-//      and folds the column maxima of |A2| into a device array;             -> grid barrier
-//   B. e_j from the maxima (FP16: max * 2^e_j in [2^14, 2^15); BF16: e_j = 0), the CTA's
-//      rows of A2 rounded as round(A2 * 2^e_j), and the CTA's partial Q1l^T A2l by
-//      warp-level FP16/BF16 products with FP32 accumulation;               -> grid barrier
-//   C. CTA j sums column j of the partials in a fixed order, R12 = sum * 2^-e_j goes to R,
-//      f_j from max |R12_:j|, R12l = round(R12 * 2^f_j);                   -> grid barrier
+//      and forms the column maxima of |A2| over those rows;
+//   B. e_j from the CTA's maxima (FP16: max * 2^e_j in [2^14, 2^15); BF16: e_j = 0), the
+//      CTA's rows of A2 rounded as round(A2 * 2^e_j), and the CTA's partial Q1l^T A2l by
+//      warp-level FP16/BF16 products with FP32 accumulation, times 2^-e_j; -> grid barrier
+//   C. CTA j sums column j of the partials in a fixed order into R12 (to R), f_j from
+//      max |R12_:j|, R12l = round(R12 * 2^f_j);                            -> grid barrier
 //   D. every CTA updates its rows: A2 -= (Q1l R12l) * 2^-f_j, in FP32.
 //
 // At narrow nodes the four separate kernels of the wide-node path (cast, projection,
 // split-K reduce, update) each cost a launch and a pass through L2 for a few MB of data; here
 // the rows stay on chip from A to D. Results equal the wide-node path's up to the order of
-// the FP32 accumulation. Every grid-barrier wait is bounded.
+// the FP32 accumulation: the wide-node path scales column j by the exponent of its maximum
+// over all rows, each CTA here by the exponent of its own rows' maximum (never smaller).
+// Power-of-two scaling commutes with rounding to FP16 and with the FP32 accumulation while
+// the values stay normal, so each partial times 2^-e_j is the same number either way, and
+// no grid barrier is needed to agree on the exponents. Every grid-barrier wait is bounded.
 #include <mma.h>
 
 #include "cgs2.cuh"
@@ -39,7 +43,6 @@ struct NodeArgs {
     float* part;                         // gridDim.x partial planes of W1 x W1 (column-major)
     void* R12l;                          // W1 x W1 scaled low-precision R12 (column-major)
     int* f;                              // w2 exponents of R12's columns
-    unsigned* colmax;                    // n words: bits of max |A2_:j| (zero on entry and exit)
     unsigned* bar;                       // grid barrier words (count, generation)
     int* err;
 };
@@ -53,8 +56,8 @@ struct NodeSmem {
     __align__(32) float Us[kNT][W1 + 4]; // update products, row-major
     float red[2][kNW][32];               // column maxima, up to two chunks of 32 columns
     float sc[W1];                        // 2^e_j (phase B), 2^-f_j (phase D)
+    float einv[W1];                      // 2^-e_j (phase B)
     float part_g[kNT];
-    float colm[W1];
 };
 
 template <typename TL> struct WmmaT;
@@ -94,21 +97,17 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             sm.red[c][warp][lane] = warp_transpose_max<kCh>(mx);
         }
         __syncthreads();
-        if (t < w2 && LLS_INB(t < W1)) {
+        if (t < W1) {
             float m = 0.f;
 #pragma unroll
             for (int q = 0; q < kNW; ++q) m = fmaxf(m, sm.red[t / kCh][q][t % kCh]);
-            atomicMax(a.colmax + cA + t, __float_as_uint(m));
-        }
-        if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
-        if (t < W1) {
-            const float m = t < w2 ? __uint_as_float(__ldcg(a.colmax + cA + t)) : 0.f;
-            sm.colm[t] = m;
-            sm.sc[t] = pow2f(scale_exponent(a.kind, m));
+            const int e = scale_exponent(a.kind, t < w2 ? m : 0.f);
+            sm.sc[t] = pow2f(e);
+            sm.einv[t] = pow2f(-e);
         }
     } else if (t < W1) {
-        sm.colm[t] = 0.f;
         sm.sc[t] = 1.f;
+        sm.einv[t] = 1.f;
     }
     __syncthreads();
 
@@ -130,8 +129,15 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             wmma::load_matrix_sync(fb, reinterpret_cast<const WT*>(&sm.As[nt * 16][k0]), kLdK);
             wmma::mma_sync(acc, fa, fb, acc);
         }
+        // the tile through shared memory (Us is free until phase D), unscaled by 2^-e_j (exact)
+        float* us = &sm.Us[0][0] + tile * 256;
+        wmma::store_matrix_sync(us, acc, 16, wmma::mem_col_major);
+        __syncwarp();
         float* pp = a.part + (size_t)blockIdx.x * (W1 * W1) + (size_t)(nt * 16) * W1 + mt * 16;   // plane of W1 x W1
-        wmma::store_matrix_sync(pp, acc, W1, wmma::mem_col_major);
+        for (int e = lane; e < 256; e += 32) {
+            const int i = e & 15, j = e >> 4;
+            pp[(size_t)j * W1 + i] = us[e] * sm.einv[nt * 16 + j];
+        }
     }
     if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
 
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
             float tot = 0.f;
 #pragma unroll
             for (int q = 0; q < G; ++q) tot += sm.part_g[q * W1 + t];
-            r12 = tot * pow2f(-scale_exponent(a.kind, sm.colm[j]));
+            r12 = tot;
             if (t < w1 && LLS_INB(a.c0 + t < a.ldr)) a.R[(size_t)(a.c0 + t) + (size_t)(cA + j) * a.ldr] = r12;
         }
         float mx = (t < w1) ? fabsf(r12) : 0.f;
@@ -185,7 +191,6 @@ __global__ void __launch_bounds__(kNT) node_fused_kernel(NodeArgs a) {
     if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
 
     // ---- D: A2 -= (Q1l R12l) * 2^-f_j ------------------------------------------------------
-    if (blockIdx.x == 0 && t < w2) a.colmax[cA + t] = 0u;   // every CTA read the maxima before barrier 2
     for (int i = t; i < W1 * W1; i += kNT)
         reinterpret_cast<unsigned short*>(&sm.Rl[0][0])[i] = __ldcg(reinterpret_cast<const unsigned short*>(a.R12l) + i);
     if (t < W1) sm.sc[t] = t < w2 ? pow2f(-__ldcg(a.f + t)) : 0.f;
@@ -264,7 +269,7 @@ int node_fused(const NodeCall& c, cudaStream_t st) {
     NodeArgs a;
     a.W = c.W; a.ldw = c.ldw; a.Wh = c.Wh; a.ldh = c.ldh;
     a.m = c.m; a.c0 = c.c0; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;
-    a.R = c.R; a.ldr = c.ldr; a.part = c.part; a.R12l = c.R12l; a.f = c.f; a.colmax = c.colmax;
+    a.R = c.R; a.ldr = c.ldr; a.part = c.part; a.R12l = c.R12l; a.f = c.f;
     a.bar = c.bar; a.err = c.err;
     if (c.lowp == 0) return c.w1 <= 16 ? launch_node<__half, 16>(a, st) : launch_node<__half, 32>(a, st);
     return c.w1 <= 16 ? launch_node<__nv_bfloat16, 16>(a, st) : launch_node<__nv_bfloat16, 32>(a, st);

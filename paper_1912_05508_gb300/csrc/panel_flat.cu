@@ -539,16 +539,20 @@ __global__ void __launch_bounds__(kFT, 1) panel_flat_kernel(FlatArgs a) {
 // second panel in registers:
 //   1. panel of columns [c0, c0 + w1) (panel_body): Q1 rows in registers, Q1l = round(Q1) in
 //      shared memory (the copy the panel also stores to Wh);
-//   2. FP16: the CTA's column maxima of |A2| folded into device words (atomicMax on the bit
-//      patterns) -> grid barrier -> e_j; A2l = round(A2 2^e_j); CTA 0 clears the words
-//      after the next barrier;
-//   3. the CTA's partial Q1l^T A2l (warp MMAs, FP32 accumulation, fixed-order warp sum)
-//      -> grid barrier -> every CTA sums the P0 partials in the same fixed order, so all hold
-//      the same R12 = sum 2^-e_j (CTA 0 writes it to R), f_j and R12l = round(R12 2^f_j);
+//   2. FP16: e_j from the column maxima of |A2| over the CTA's own rows; A2l = round(A2 2^e_j);
+//   3. the CTA's partial Q1l^T A2l (warp MMAs, FP32 accumulation, fixed-order warp sum),
+//      times 2^-e_j -> grid barrier -> every CTA sums the P0 partials in the same fixed order,
+//      so all hold the same R12 (CTA 0 writes it to R), f_j and R12l = round(R12 2^f_j);
 //   4. A2 -= (Q1l R12l) 2^-f_j for the CTA's rows (warp MMAs, FP32), in registers;
 //   5. panel of columns [c0 + w1, c0 + w1 + w2) on the updated rows.
 // The rounding points are those of the separate kernels (Alg. 2 with the column scaling of
-// Sec. 3.1.2); only the order of the FP32 accumulations differs.
+// Sec. 3.1.2); only the order of the FP32 accumulations differs. The separate kernels scale
+// column j by one exponent e_j from its maximum over all rows; here each CTA takes the
+// exponent of its own rows' maximum, which is never smaller. Scaling by a power of two
+// commutes with rounding to FP16 and with the FP32 accumulation while the values stay
+// normal, so every partial times 2^-e_j is the same number either way (where the common
+// exponent would leave a value among FP16's subnormals the CTA's exponent keeps more of
+// it), and the grid barrier that a common exponent needs is saved.
 
 constexpr int kBlkLdK = 8;          // padding (halves) of the K-contiguous operand rows
 constexpr int kUsLd = 20;           // row stride (floats) of the update products
@@ -558,7 +562,6 @@ constexpr int kBlockMaxP0 = kStackRows / 16;   // CTAs of a one-level panel of w
 struct BlockArgs {
     FlatArgs p1, p2;                // the two panels
     float* part;                    // P0 x 256 projection partials
-    unsigned* colmax;               // 16 words: bits of max |A2_:j| (zero on entry, left zero)
     int w1, w2, kind;               // kind: 1 FP16 column scaling, 0 none (BF16)
 };
 
@@ -597,7 +600,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
 #pragma unroll
         for (int i = 0; i < 16; ++i) bs.Qs[i][t + r * kFT] = LowPrec<TL>::from_float(v[r][i]);
 
-    // 2. A2 rows; FP16 column scaling from the global column maxima
+    // 2. A2 rows; FP16 column scaling from the column maxima over this CTA's rows
     load_rows<16, RL>(a.p1, a.p1.c0 + w1, v, s, rows, w2);
     if (a.kind != 0) {
         float mx[16];
@@ -611,16 +614,11 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         const float wm = warp_transpose_max<16>(mx);
         if (lane < 16) bs.red[warp][lane] = wm;
         __syncthreads();
-        if (t < w2 && LLS_INB(t < 16)) {
+        if (t < 16) {
             float x = 0.f;
 #pragma unroll
             for (int q = 0; q < kFW; ++q) x = fmaxf(x, bs.red[q][t]);
-            atomicMax(a.colmax + t, __float_as_uint(x));   // non-negative floats order as their bits
-        }
-        if (!grid_barrier(a.p1.bar, P0, a.p1.err)) return false;
-        if (t < 16) {
-            const float x = t < w2 ? __uint_as_float(__ldcg(a.colmax + t)) : 0.f;
-            const int ej = scale_exponent(1, x);
+            const int ej = scale_exponent(1, t < w2 ? x : 0.f);
             bs.sc[t] = pow2f(ej);
             bs.einv[t] = pow2f(-ej);
         }
@@ -657,11 +655,10 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         float x = 0.f;
 #pragma unroll
         for (int q = 0; q < kFW; ++q) x += bs.wp[q][t];   // entry (t mod 16, t / 16)
+        x *= bs.einv[t >> 4];                              // exact: a power of two
         if (LLS_INB((int)blockIdx.x < kBlockMaxP0 && t < 256)) a.part[(size_t)blockIdx.x * 256 + t] = x;
     }
     if (!grid_barrier(a.p1.bar, P0, a.p1.err)) return false;
-    // every CTA has read the column maxima before the barrier above: CTA 0 clears them
-    if (blockIdx.x == 0 && a.kind != 0 && t < w2) a.colmax[t] = 0u;
     {
         // entry t summed over the P0 partials in a fixed order; all loads are issued first
         const float* p = a.part + t;
@@ -679,7 +676,7 @@ __device__ __forceinline__ bool block_node(const BlockArgs& a, float (&v)[RL][16
         const float tot = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         const int i = t & 15, j = t >> 4;
         const bool live = i < w1 && j < w2;
-        const float r12 = live ? tot * bs.einv[j] : 0.f;
+        const float r12 = live ? tot : 0.f;
         bs.r12[j][i] = r12;
         if (blockIdx.x == 0 && live && LLS_INB(a.p1.c0 + i < a.p1.ldr))
             a.p1.R[(size_t)(a.p1.c0 + i) + (size_t)(a.p1.c0 + w1 + j) * a.p1.ldr] = r12;
@@ -925,7 +922,7 @@ int block_fused_qr(const BlockCall& c, cudaStream_t st) {
     a.p2 = p;
     a.p2.c0 = c.c0 + c.w1;
     a.p2.b = c.w2;
-    a.part = c.part; a.colmax = c.colmax; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;
+    a.part = c.part; a.w1 = c.w1; a.w2 = c.w2; a.kind = c.lowp == 0 ? 1 : 0;
     if (c.lowp == 0) return launch_block_shape<__half>(a, rl, rr, st);
     return launch_block_shape<__nv_bfloat16>(a, rl, rr, st);
 }
