@@ -111,8 +111,8 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
                    const int* __restrict__ e, const int* __restrict__ sq, float* __restrict__ R12, int ldr,
                    TL* __restrict__ R12l, int ldrl, int* __restrict__ f, int kind, const int* __restrict__ err) {
     // Threads split as (row slot i0 < rp) x (split group g < G): group g sums splits
-    // g, g + G, ... (four independent loads per trip); the groups are then added in order
-    // g = 0, 1, ..., so the result does not depend on timing.
+    // g, g + G, ... in that order (sixteen loads issued per trip before they are added); the
+    // groups are then added in order g = 0, 1, ..., so the result does not depend on timing.
     __shared__ float s_part[256];
     __shared__ float s_red[8];
     __shared__ int s_f;
@@ -138,6 +138,13 @@ proj_reduce_kernel(const float* __restrict__ part, int splits, int w1, int w2,
         if (i < w1) {
             const float* p = part + (size_t)i + (size_t)j * w1;
             int z = g;
+            for (; z + 15 * G < splits; z += 16 * G) {
+                float x[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) x[u] = __ldg(p + (size_t)(z + u * G) * plane);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) s += x[u];
+            }
             for (; z + 3 * G < splits; z += 4 * G) {
                 const float a = __ldg(p + (size_t)z * plane), b = __ldg(p + (size_t)(z + G) * plane);
                 const float c = __ldg(p + (size_t)(z + 2 * G) * plane), d = __ldg(p + (size_t)(z + 3 * G) * plane);

@@ -424,7 +424,8 @@ __device__ __forceinline__ bool panel_body(const FlatArgs& a, float (&v)[RL][B],
     float* rb = a.rbuf + (size_t)blockIdx.x * (B * B);
     if (LLS_INB((int)blockIdx.x < a.P0))
         for (int i = t; i < B * B; i += kFT) rb[i] = sm.Rs[i / B][i % B];
-    __threadfence();
+    // no fence per thread: the grid barrier's CTA barrier followed by its thread 0's fence
+    // releases every thread's stores before the arrival
     __syncthreads();
     for (int i = t; i < B * (B + 1); i += kFT) (&sm.Rs[0][0])[i] = 0.f;
 
@@ -800,6 +801,7 @@ static int launch_flat(FlatArgs& a, cudaStream_t st) {
 
 template <typename TL, int RL, int RR>
 static int launch_block(BlockArgs& a, cudaStream_t st) {
+    static_assert(block_smem_bytes<TL, RL>() <= 227 * 1024, "shared memory of one CTA");
     constexpr int kMaxDev = 64;
     static int cap[kMaxDev];
     static bool done[kMaxDev];

@@ -9,9 +9,16 @@ Cases (each a few GB at most on the device, inputs larger than L2):
                Krylov iterations;
     block      the lowest recursion node (two 16-column panels and the node between them)
                on 32768 rows, three calls;
-    small      the 1024 x 128 LSQR solve to the FP32 target, three calls.
-The krylov case keeps its generated input in the temporary folder, so a second run of the
-same command (under a profiler, where torch's linear-algebra plugin may not load) reuses it.
+    small      the 1024 x 128 LSQR solve to the FP32 target, three calls;
+    solve      the benchmark's solve, 32768 x 4096 (geometric spectrum, kappa = 1e3, seed 2,
+               FP16 products, CGLS to the FP64 target), with the implementation choices the
+               autotuner picks for it on a GB300 (panel width 16, blocks and narrow nodes as
+               single launches, the persistent update with the one-tile-per-CTA projection;
+               recorded here, not measured, so a profiler cannot change them), two solves:
+               the launch list of the second is the steady-state one (512 MiB of A).
+The krylov and solve cases keep their generated inputs in the temporary folder, so a second run
+of the same command (under a profiler, where torch's linear-algebra plugin may not load) reuses
+them.
 """
 from __future__ import annotations
 
@@ -45,19 +52,28 @@ def products():
     torch.cuda.synchronize()
 
 
-def krylov():
+def _problem(m, n, seed, dev):
+    """The geometric-spectrum problem (kappa = 1e3) of the given seed, generated on the device
+    once and kept in the temporary folder: a second run of the same command (under a profiler,
+    where torch's linear-algebra plugin may not load) reuses it."""
     import torch
-    from . import lls, synth
-    dev = torch.device("cuda", 0)
-    path = os.path.join(tempfile.gettempdir(), "lls_profile_krylov_16384x4096.pt")
+    from . import synth
+    path = os.path.join(tempfile.gettempdir(), f"lls_profile_{m}x{n}_seed{seed}.pt")
     if os.path.exists(path):
         d = torch.load(path)
-        A = torch.empty((4096, 16384), dtype=torch.float32, device=dev).t()
+        A = torch.empty((n, m), dtype=torch.float32, device=dev).t()
         A.copy_(d["A"])
-        b = d["b"].to(dev)
-    else:
-        A, b, _ = synth.svd_lls_torch(16384, 4096, "geometric", 1e3, seed=3, device=dev)
-        torch.save({"A": A.cpu(), "b": b.cpu()}, path)
+        return A, d["b"].to(dev)
+    A, b, _ = synth.svd_lls_torch(m, n, "geometric", 1e3, seed=seed, device=dev)
+    torch.save({"A": A.cpu(), "b": b.cpu()}, path)
+    return A, b
+
+
+def krylov():
+    import torch
+    from . import lls
+    dev = torch.device("cuda", 0)
+    A, b = _problem(16384, 4096, 3, dev)
     lls.solve(A, b, panel_width=16, max_iter=6, tol=1e-300, check=False)
     torch.cuda.synchronize()
 
@@ -90,7 +106,21 @@ def small():
     torch.cuda.synchronize()
 
 
-CASES = {"products": products, "krylov": krylov, "block": block, "small": small}
+def solve():
+    import torch
+    from . import lls
+    dev = torch.device("cuda", 0)
+    A, b = _problem(32768, 4096, 2, dev)
+    t = lls.lls_tuning()
+    t.panel_width, t.node_mode, t.gemm_kernel, t.batched_ctas_per_sm, t.krylov_ctas = 16, 0, 2, 0, 0
+    assert lls.lls_tuning_set(0, 32768, 4096, lls.make_options(prec="fp16", target="fp64"), t) == 0
+    for _ in range(2):
+        x, info = lls.solve(A, b, prec="fp16", target="fp64")
+        torch.cuda.synchronize()
+    print("iters", info["iters"], "eta", info["eta"])
+
+
+CASES = {"products": products, "krylov": krylov, "block": block, "small": small, "solve": solve}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
