@@ -101,9 +101,26 @@ __device__ __forceinline__ void stage_vec(const double* __restrict__ v, int len)
     __syncthreads();
 }
 
-// Copy a vector already split into double-float pairs into shared memory.
+// Copy a vector already split into double-float pairs into shared memory. Sixteen loads per
+// thread are issued before the first is stored, so a vector of up to 4096 entries costs one
+// round trip to L2 instead of one per 256 entries.
 __device__ __forceinline__ void stage_df(const float2* __restrict__ v, int len) {
-    for (int i = threadIdx.x; i < len; i += kKThreads) k_dsm[i] = __ldcg(v + i);
+    int i = threadIdx.x;
+    for (; i + 15 * kKThreads < len; i += 16 * kKThreads) {
+        float2 x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = __ldcg(v + i + u * kKThreads);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) k_dsm[i + u * kKThreads] = x[u];
+    }
+    {
+        float2 x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = i + u * kKThreads < len ? __ldcg(v + i + u * kKThreads) : float2{};
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if (i + u * kKThreads < len) k_dsm[i + u * kKThreads] = x[u];
+    }
     __syncthreads();
 }
 
@@ -127,12 +144,24 @@ __device__ __forceinline__ void block_partial(double v, double* bpart, int k) {
     }
 }
 
-// Fixed-order sum of slot k over all blocks (identical in every CTA).
+// Fixed-order sum of slot k over all blocks (identical in every CTA). Lane l adds the blocks
+// l, l + 32, ... in that order; its first sixteen loads are all issued before the additions.
 __device__ __forceinline__ double grid_total(const double* bpart, int k) {
     __shared__ double s_tot;
     if (threadIdx.x < 32) {
+        const double* p = bpart + (size_t)k * gridDim.x;
+        const int g = (int)gridDim.x;
+        double x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int i = (int)threadIdx.x + 32 * u;
+            x[u] = i < g ? __ldcg(p + i) : 0.0;
+        }
         double s = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += __ldcg(bpart + (size_t)k * gridDim.x + i);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if ((int)threadIdx.x + 32 * u < g) s += x[u];
+        for (int i = (int)threadIdx.x + 512; i < g; i += 32) s += __ldcg(p + i);
         s = warp_sum_d(s);
         if (threadIdx.x == 0) s_tot = s;
     }
@@ -167,6 +196,21 @@ __device__ __forceinline__ double sum_parts_quad(const double* __restrict__ p, i
     double s0 = 0.0, s1 = 0.0;
     if (valid) {
         int k = sub;
+        // the first eight trips' sixteen loads are all issued before the (ordered) additions
+        if (k + 60 < count) {
+            double x0[8], x1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                x0[u] = __ldcg(p + (size_t)(k + 8 * u) * stride);
+                x1[u] = __ldcg(p + (size_t)(k + 8 * u + 4) * stride);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s0 += x0[u];
+                s1 += x1[u];
+            }
+            k += 64;
+        }
 #pragma unroll 4   // loads of later trips issue ahead of the (ordered) additions
         for (; k + 4 < count; k += 8) {
             s0 += __ldcg(p + (size_t)k * stride);
@@ -207,11 +251,10 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
             const float4* col4 = reinterpret_cast<const float4*>(col);
             const int qe = bhi / 4;
             int q = blo / 4 + lane;
-            // four 16-byte loads in flight per lane (a column of 4096 entries is 8 trips)
-            for (; q + 96 < qe; q += 128) {
-                const float4 a0 = __ldg(col4 + q), a1 = __ldg(col4 + q + 32);
-                const float4 a2 = __ldg(col4 + q + 64), a3 = __ldg(col4 + q + 96);
-                const float2* v = k_dsm + 4 * q;
+            // four 16-byte loads per trip (a column of 4096 entries is 8 trips); the next trip's
+            // loads are issued before this trip's products, so eight are in flight per lane
+            auto trip = [&](const float4& a0, const float4& a1, const float4& a2, const float4& a3, int qq) {
+                const float2* v = k_dsm + 4 * qq;
                 dot2_step(s0, c0, a0.x, v[0].x, v[0].y);
                 dot2_step(s1, c1, a1.x, v[128].x, v[128].y);
                 dot2_step(s2, c2, a2.x, v[256].x, v[256].y);
@@ -228,6 +271,24 @@ __device__ double tri_gemv(const float* __restrict__ X, int n, bool upper, doubl
                 dot2_step(s1, c1, a1.w, v[131].x, v[131].y);
                 dot2_step(s2, c2, a2.w, v[259].x, v[259].y);
                 dot2_step(s3, c3, a3.w, v[387].x, v[387].y);
+            };
+            if (q + 96 < qe) {
+                float4 a0 = __ldg(col4 + q), a1 = __ldg(col4 + q + 32);
+                float4 a2 = __ldg(col4 + q + 64), a3 = __ldg(col4 + q + 96);
+                for (;;) {
+                    const int qn = q + 128;
+                    if (qn + 96 < qe) {
+                        const float4 b0 = __ldg(col4 + qn), b1 = __ldg(col4 + qn + 32);
+                        const float4 b2 = __ldg(col4 + qn + 64), b3 = __ldg(col4 + qn + 96);
+                        trip(a0, a1, a2, a3, q);
+                        a0 = b0; a1 = b1; a2 = b2; a3 = b3;
+                        q = qn;
+                    } else {
+                        trip(a0, a1, a2, a3, q);
+                        q = qn;
+                        break;
+                    }
+                }
             }
             for (; q < qe; q += 32) {
                 const float4 a0 = __ldg(col4 + q);
