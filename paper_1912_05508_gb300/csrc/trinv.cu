@@ -54,9 +54,12 @@ __global__ void diag_block_inverse_kernel(const float* __restrict__ R, int ldr, 
 // One batched product per tree depth, 64 x 64 tiles, FP32. For node (c0, w1, w2):
 //   phase 0:  T   = R12 M22      (w1 x w2, K = w2; T stored where M12 will go, in tmp)
 //   phase 1:  M12 = -M11 T       (w1 x w2, K = w1)
-// M22 and M11 are upper triangular, so the K loop skips their zero blocks.
-constexpr int kTB = 64, kTK = 16;
-__global__ void __launch_bounds__(256)
+// M22 and M11 are upper triangular, so the K loop skips their zero blocks. 64 threads per tile,
+// each holding 8 x 8 results (rows tx*4 + u and 32 + tx*4 + u, columns likewise with ty), so
+// four 16-byte shared reads feed 64 FMAs; every result is one chain of FMAs over k in
+// increasing order.
+constexpr int kTB = 64, kTK = 16, kTT = 64;
+__global__ void __launch_bounds__(kTT)
 trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __restrict__ M,
                      float* __restrict__ tmp, int n, NodeList nl) {
     const int node = blockIdx.z;
@@ -85,24 +88,30 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
     }
     // two shared-memory stages: the global loads of step k + 1 are issued into registers
     // before step k's products, so their latency overlaps the arithmetic; one barrier a step
-    __shared__ __align__(16) float As[2][kTK][kTB + 4];
-    __shared__ __align__(16) float Bs[2][kTK][kTB + 4];
+    __shared__ __align__(16) float As[2][kTK][kTB + 4];   // As[k][i]
+    __shared__ __align__(16) float Bs[2][kTK][kTB + 4];   // Bs[k][j]
     const int t = threadIdx.x;
-    const int ti = (t % 16) * 4, tj = (t / 16) * 4;
-    float acc[4][4] = {};
+    const int tx = t % 8, ty = t / 8;
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
     // phase 0: B = M22 upper triangular, rows k <= j; phase 1: A = M11 upper, columns k >= i
     const int kbeg = phase == 1 ? (i0 / kTK) * kTK : 0;
     const int kend = phase == 0 ? min(K, j0 + kTB) : K;
-    float ra[4], rb[4];
+    float ra[kTK], rb[kTK];
     auto fetch = [&](int k0) {
+        const int gi = i0 + t;                            // A: row t of the tile, 16 k
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = t + r * 256;
-            const int ii = idx % kTB, kk = idx / kTB;
-            const int gi = i0 + ii, gk = k0 + kk;
+        for (int r = 0; r < kTK; ++r) {
+            const int gk = k0 + r;
             ra[r] = (gi < w1 && gk < K) ? A[(size_t)gi + (size_t)gk * lda] : 0.f;
-            const int kk2 = idx % kTK, jj = idx / kTK;
-            const int gj = j0 + jj, gk2 = k0 + kk2;
+        }
+        const int kk2 = t % kTK;                          // B: k = t mod 16, columns t / 16 + 4 r
+#pragma unroll
+        for (int r = 0; r < kTK; ++r) {
+            const int gj = j0 + t / kTK + 4 * r, gk2 = k0 + kk2;
             rb[r] = (gj < w2 && gk2 < K) ? B[(size_t)gk2 + (size_t)gj * ldb] : 0.f;
         }
     };
@@ -110,33 +119,33 @@ trinv_batched_kernel(int phase, const float* __restrict__ R, int ldr, float* __r
     int stage = 0;
     for (int k0 = kbeg; k0 < kend; k0 += kTK, stage ^= 1) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = t + r * 256;
-            As[stage][idx / kTB][idx % kTB] = ra[r];
-            Bs[stage][idx % kTK][idx / kTK] = rb[r];
+        for (int r = 0; r < kTK; ++r) {
+            As[stage][r][t] = ra[r];
+            Bs[stage][t % kTK][t / kTK + 4 * r] = rb[r];
         }
         __syncthreads();
         if (k0 + kTK < kend) fetch(k0 + kTK);
 #pragma unroll
         for (int kk = 0; kk < kTK; ++kk) {
-            // 16-byte reads: the 16 lanes of a half-warp read 16 distinct A segments, the two
-            // half-warps the same ones (broadcast); all lanes of a half-warp one B segment
-            const float4 a4 = *reinterpret_cast<const float4*>(&As[stage][kk][ti]);
-            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[stage][kk][tj]);
-            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[stage][kk][tx * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[stage][kk][32 + tx * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[stage][kk][ty * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[stage][kk][32 + ty * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int j = j0 + tj + v;
+    for (int v = 0; v < 8; ++v) {
+        const int j = j0 + (v < 4 ? ty * 4 + v : 32 + ty * 4 + v - 4);
         if (j >= w2) continue;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + ti + u;
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + (u < 4 ? tx * 4 + u : 32 + tx * 4 + u - 4);
             if (i < w1) C[(size_t)i + (size_t)j * n] = alpha * acc[u][v];
         }
     }
@@ -263,7 +272,7 @@ int tri_inverse(const float* R, int ldr, int n, int pw, float* Minv, float* Mt, 
         for (int phase = 0; phase < 2; ++phase) {
             LLS_TRY(for_chunks(lvl, [&](const NodeList& nl, int mw1, int mw2) -> int {
                 dim3 grid(ceil_div(mw1, kTB), ceil_div(mw2, kTB), nl.count);
-                trinv_batched_kernel<<<grid, 256, 0, st>>>(phase, R, ldr, Minv, tmp, n, nl);
+                trinv_batched_kernel<<<grid, kTT, 0, st>>>(phase, R, ldr, Minv, tmp, n, nl);
                 LLS_LAUNCH_CHECK("trinv_batched", st);
                 return (int)LLS_OK;
             }));
