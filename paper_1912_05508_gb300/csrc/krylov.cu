@@ -1,9 +1,10 @@
 // R-preconditioned CGLS (Alg. 5, Sec. 3.2.3) as one persistent cooperative kernel.
 //
 // Products with A: the default engine makes two passes over A per iteration: q = A t as
-// per-column-chunk partial sums over 1024-row tiles, then, after the r update, u = A^T r as
-// per-row-chunk partial sums over 32-column groups; every partial is summed in a fixed
-// order. An optional one-pass engine (LLS_KRYLOV=onepass, CGLS with n <= 4096) streams a
+// per-column-chunk partial sums over 1024-row tiles (columns in increasing order over the
+// grid's waves), then, after the r update, u = A^T r as per-row-chunk partial sums, each CTA
+// staying on one row chunk and taking groups of 8 columns from the last column down; every
+// partial is summed in a fixed order. An optional one-pass engine (LLS_KRYLOV=onepass, CGLS with n <= 4096) streams a
 // row-block copy of A in 4-row blocks through a double-buffered shared-memory ring
 // (cp.async); for each block the CTA forms q = A t on those rows (block-wide reduction),
 // then accumulates A^T q and A^T r for its columns from the same shared-memory copy, and
