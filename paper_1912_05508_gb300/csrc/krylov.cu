@@ -388,58 +388,61 @@ __device__ void at_times_partials(const KArgs& a, const double* __restrict__ v,
                                   const float2* __restrict__ vdf = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = a.at_cpr, L = a.at_rows;
-    const int rc = (int)blockIdx.x / K, k = (int)blockIdx.x % K;
-    if (rc >= a.nrc) return;                      // uniform across the CTA
-    const int r0 = rc * L, rows = min(a.m - r0, L);
-    if (rows <= 0) return;
-    __syncthreads();                              // earlier users of k_dsm are done
-    if (vdf) {
-        for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
-    } else {
-        for (int i = threadIdx.x; i < rows; i += kKThreads) {
-            float hi, lo;
-            split_df(__ldcg(v + r0 + i), hi, lo);
-            k_dsm[i] = make_float2(hi, lo);
-        }
-    }
-    __syncthreads();
-    if (!LLS_INB(r0 >= 0 && r0 + rows <= a.m && rows <= L)) return;
-    const bool full = a.aligned16 && (rows & 3) == 0;
-    const int nq = rows >> 2;
-    for (int g = a.ncg - 1 - k; g >= 0; g -= K) {
-        const int j = g * kKWarps + warp;
-        if (j >= a.n) continue;
-        const float* col = a.A + (size_t)j * a.lda + r0;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-        if (full) {
-            const float4* col4 = reinterpret_cast<const float4*>(col);
-#pragma unroll 4
-            for (int q = lane; q < nq; q += 32) {
-                if (q + 32 * kPrefetchCols < nq)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(col4 + q + 32 * kPrefetchCols));
-                const float4 av = __ldg(col4 + q);
-                const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
-                dot2_step(s0, c0, av.x, w0.x, w0.y);
-                dot2_step(s1, c1, av.y, w1.x, w1.y);
-                dot2_step(s2, c2, av.z, w2.x, w2.y);
-                dot2_step(s3, c3, av.w, w3.x, w3.y);
-            }
-            // the start of this warp's next column (4 KB) into L2
-            if (g - K >= 0 && (g - K) * kKWarps + warp < a.n && 32 * lane < rows)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(col - (size_t)K * kKWarps * a.lda + 32 * lane));
+    const int k = (int)blockIdx.x % K;
+    // one chunk per CTA when the chunks' CTAs fit the grid (the step then passes nrc), else
+    // (K = 1) the chunks c, c + grid, ...; uniform across the CTA
+    for (int rc = (int)blockIdx.x / K; rc < a.nrc; rc += (int)gridDim.x / K) {
+        const int r0 = rc * L, rows = min(a.m - r0, L);
+        if (rows <= 0) break;
+        __syncthreads();                              // earlier users of k_dsm are done
+        if (!LLS_INB(r0 >= 0 && r0 + rows <= a.m && rows <= L && 2 * rows <= a.vec_floats)) break;
+        if (vdf) {
+            for (int i = threadIdx.x; i < rows; i += kKThreads) k_dsm[i] = __ldcg(vdf + r0 + i);
         } else {
-            for (int i = lane; i < rows; i += 32) {
-                const float2 w = k_dsm[i];
-                dot2_step(s0, c0, __ldg(col + i), w.x, w.y);
+            for (int i = threadIdx.x; i < rows; i += kKThreads) {
+                float hi, lo;
+                split_df(__ldcg(v + r0 + i), hi, lo);
+                k_dsm[i] = make_float2(hi, lo);
             }
         }
-        // combine the four chains, then the 32 lanes, in double-float
-        float t, e;
-        two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
-        two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
-        two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
-        warp_sum_df(s0, c0);
-        if (lane == 0 && LLS_INB(rc < a.nrc && j < a.n)) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
+        __syncthreads();
+        const bool full = a.aligned16 && (rows & 3) == 0;
+        const int nq = rows >> 2;
+        for (int g = a.ncg - 1 - k; g >= 0; g -= K) {
+            const int j = g * kKWarps + warp;
+            if (j >= a.n) continue;
+            const float* col = a.A + (size_t)j * a.lda + r0;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+            if (full) {
+                const float4* col4 = reinterpret_cast<const float4*>(col);
+#pragma unroll 4
+                for (int q = lane; q < nq; q += 32) {
+                    if (q + 32 * kPrefetchCols < nq)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(col4 + q + 32 * kPrefetchCols));
+                    const float4 av = __ldg(col4 + q);
+                    const float2 w0 = k_dsm[4 * q], w1 = k_dsm[4 * q + 1], w2 = k_dsm[4 * q + 2], w3 = k_dsm[4 * q + 3];
+                    dot2_step(s0, c0, av.x, w0.x, w0.y);
+                    dot2_step(s1, c1, av.y, w1.x, w1.y);
+                    dot2_step(s2, c2, av.z, w2.x, w2.y);
+                    dot2_step(s3, c3, av.w, w3.x, w3.y);
+                }
+                // the start of this warp's next column (4 KB) into L2
+                if (g - K >= 0 && (g - K) * kKWarps + warp < a.n && 32 * lane < rows)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(col - (size_t)K * kKWarps * a.lda + 32 * lane));
+            } else {
+                for (int i = lane; i < rows; i += 32) {
+                    const float2 w = k_dsm[i];
+                    dot2_step(s0, c0, __ldg(col + i), w.x, w.y);
+                }
+            }
+            // combine the four chains, then the 32 lanes, in double-float
+            float t, e;
+            two_sum(s0, s1, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c1), e);
+            two_sum(s2, s3, t, e); s2 = t; c2 = __fadd_rn(__fadd_rn(c2, c3), e);
+            two_sum(s0, s2, t, e); s0 = t; c0 = __fadd_rn(__fadd_rn(c0, c2), e);
+            warp_sum_df(s0, c0);
+            if (lane == 0 && LLS_INB(rc < a.nrc && j < a.n)) a.upart[(size_t)rc * a.n + j] = join_df(s0, c0);
+        }
     }
 }
 
@@ -1236,16 +1239,20 @@ static int pick_col_chunk(int m, int n, int grid) {
 // Rows staged for the A^T r pass at most (the vector space reserved in shared memory).
 static int at_rows_cap(int n) { return n > kRowChunkCap ? n : kRowChunkCap; }
 
-// The A^T r pass: R row chunks of L rows (L a multiple of 4, at most at_rows_cap(n)), K = grid / R
-// CTAs per chunk, groups of 8 columns. Every CTA streams L x 8 elements per item, so the pass
-// takes about ceil(ncg / K) * L; the R with the least such time wins (fewest chunks on ties).
-// At m = 32768, n = 4096 on 456 CTAs: 8 chunks of 4096 rows, 57 CTAs each, 512 groups in at
-// most 9 items per CTA (8.98 on average).
+// The A^T r pass: R row chunks of L rows (L a multiple of 4, at most at_rows_cap(n) rounded down
+// to a multiple of 4, the rows a CTA can stage), K = grid / R CTAs per chunk, groups of 8 columns.
+// Every CTA streams L x 8 elements per item, so the pass takes about ceil(ncg / K) * L; the R
+// with the least such time wins (fewest chunks on ties). At m = 32768, n = 4096 on 456 CTAs:
+// 8 chunks of 4096 rows, 57 CTAs each, 512 groups in at most 9 items per CTA (8.98 on average).
+// When even R = grid leaves chunks taller than the staging room, R is the fewest chunks that fit
+// and each CTA takes the chunks c, c + grid, ... one after another (K = 1).
+static int at_rows_fit(int n) { return at_rows_cap(n) & ~3; }
+
 static void at_plan(int m, int n, int grid, int& R, int& L, int& K) {
     const long long ncg = ceil_div(n, kKWarps);
-    const int cap = at_rows_cap(n);
+    const int cap = at_rows_fit(n);
+    if (grid < 1) grid = 1;
     long long best = -1;
-    R = 1; L = (m + 3) & ~3; K = grid < 1 ? 1 : grid;
     for (int r = 1; r <= grid; ++r) {
         const int l = (ceil_div(m, r) + 3) & ~3;
         if (l > cap) continue;
@@ -1254,6 +1261,18 @@ static void at_plan(int m, int n, int grid, int& R, int& L, int& K) {
         const long long cost = (ncg + k - 1) / k * l;
         if (best < 0 || cost < best) { best = cost; R = r; L = l; K = k; }
     }
+    if (best < 0) {   // more chunks than CTAs
+        R = ceil_div(m, cap);
+        L = (ceil_div(m, R) + 3) & ~3;
+        K = 1;
+    }
+}
+
+// Row chunks the A^T r pass can take on grids of at most `grid` CTAs (room for its partials).
+static long long at_rows_max_chunks(int m, int n, int grid) {
+    const long long a = std::min<long long>(grid < 1 ? 1 : grid, ceil_div(m, 4));
+    const long long b = ceil_div(m, at_rows_fit(n)) + 1;
+    return a > b ? a : b;
 }
 
 static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
@@ -1275,8 +1294,7 @@ static KLayout k_layout(int m, int n, int grid, bool tiled = false) {
     L.off_qpart = take(8ull * m * ceil_div(n, kColChunkMin));   // room for the narrowest width (most partials)
     // room for the most row chunks any grid up to this one can take, so a scratch sized for
     // the largest grid holds every smaller grid's layout
-    const long long rmax = std::min<long long>(grid < 1 ? 1 : grid, ceil_div(m, 4));
-    L.off_upart = take(8ull * n * (size_t)rmax);
+    L.off_upart = take(8ull * n * (size_t)at_rows_max_chunks(m, n, grid));
     L.off_v1 = take(8ull * n * grid);
     L.off_v2 = take(8ull * n * grid);
     L.off_bpart = take(8ull * kNPart * grid);

@@ -54,6 +54,19 @@ def test_ragged_and_degenerate_shapes(m, n):
     assert metrics.forward_error(x, xs) <= 10 * p.kappa * 1e-12
 
 
+@pytest.mark.parametrize("krylov", ["cgls", "lsqr"])
+@pytest.mark.parametrize("m,n", [(20000, 3), (70001, 5), (4099, 13)])
+def test_tall_problems_on_small_grids(m, n, krylov):
+    # few columns give a grid of one or a few CTAs; the A^T r pass then has more row chunks (of
+    # at most 4096 staged rows) than CTAs and each CTA takes several, restaging its vector chunk
+    p = synth.svd_lls(m, n, "geometric", 1e2, seed=m + n)
+    x, info = run(p, prec="fp16", target="fp64", krylov=krylov)
+    xs = direct.lls(p.A, p.b)
+    assert info["status"] == 0, info
+    assert metrics.eta_kw(p.A, p.b, x) <= 1e-12
+    assert metrics.forward_error(x, xs) <= 10 * p.kappa * 1e-12
+
+
 def test_singular_is_reported():
     p = synth.svd_lls(500, 30, "geometric", 10.0, seed=4)
     A = p.A.copy()
