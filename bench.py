@@ -232,8 +232,8 @@ def run_reference(args):
 NCU_TRAFFIC = {"block": (54.846992e9 * 79.264e-6, 1.0, "panel_flat.cu", "d9c64e926cb88eff"),
                "tc_projection": (134252288 + 3640064, 16384, "gemm_persist.cu", "e6322d58344b9a4e"),
                "tc_update": (209890560 + 82324480, 16384, "gemm_persist.cu", "e6322d58344b9a4e"),
-               "cgls": (4115031000 + 62517504, 15 * 4.0 * 16384 * 4096 + 14 * 4.0 * 4096 * 4097 / 2,
-                        "krylov.cu", "3f2267b6a2ef60bb")}
+               "cgls": (4120058000 + 62745344, 15 * 4.0 * 16384 * 4096 + 14 * 4.0 * 4096 * 4097 / 2,
+                        "krylov.cu", "8a52e08a690e00b6")}
 
 
 def source_digest(name):

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <map>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -574,7 +575,7 @@ static void lls_layout(WsArena& ar, int m, int n, const lls_options& o, QrWs& w,
     const size_t ds = direct_start_scratch_bytes(m, n);   // the direct start borrows the Krylov scratch
     if (ks_bytes < ds) ks_bytes = ds;
     ks = ar.take<char>(ks_bytes);
-    hist = ar.take<double>(kHistLen);
+    hist = ar.take<double>(kHistLen + kPhaseLen);   // the history, then the CGLS phase log
 }
 
 static size_t solve_ws_bytes(int m, int n, const lls_options& o) {
@@ -617,6 +618,17 @@ struct SolveCall {
 };
 
 // The solve on `st`; gate non-null when W fills in chunks on another stream (host input).
+// LLS_LOG=1: the Krylov stop quantity of every iteration on stderr; LLS_LOG=2 adds the median
+// time of each phase of the CGLS iteration (between consecutive grid barriers, seen by CTA 0).
+static int log_level() {
+    static const int lv = [] {
+        const char* v = getenv("LLS_LOG");
+        if (!v || !v[0] || v[0] == '0') return 0;
+        return v[0] == '2' ? 2 : 1;
+    }();
+    return lv;
+}
+
 static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool capturing, ColumnGate* gate) {
     const int m = c.m, n = c.n;
     if (ev) record_phase(ev[0], st, capturing);
@@ -638,6 +650,10 @@ static int solve_body(SolveCall& c, cudaStream_t st, cudaEvent_t* ev, bool captu
     kc.scratch = c.ks; kc.scratch_bytes = c.kb; kc.dev_err = c.w.err; kc.dev_info = c.w.dinfo;
     kc.x_zero = c.o.x0 == LLS_X0_ZERO ? 1 : 0;
     kc.hist = c.hist;
+    if (c.hist && log_level() >= 2) {
+        kc.phases = reinterpret_cast<unsigned long long*>(c.hist + kHistLen);
+        LLS_CUDA_TRY(cudaMemsetAsync(kc.phases, 0, sizeof(unsigned long long) * kPhaseLen, st));
+    }
     kc.ctas = c.k.krylov_ctas;
     LLS_TRY(krylov_solve(kc, st));
     if (ev) record_phase(ev[2], st, capturing);
@@ -648,12 +664,40 @@ static int enqueue_solve(void* p, cudaStream_t st, cudaEvent_t* ev, bool capturi
     return solve_body(*(SolveCall*)p, st, ev, capturing, nullptr);
 }
 
-static bool log_enabled() {
-    static const bool on = [] {
-        const char* v = getenv("LLS_LOG");
-        return v && v[0] && v[0] != '0';
-    }();
-    return on;
+
+// LLS_LOG=2: per phase of the CGLS iteration, the median over the logged iterations of the time
+// from one grid barrier to the next (phase 1 starts at the top of the iteration), in us. The
+// log holds a stamp per grid barrier of CTA 0, iteration tops marked by the top bit.
+static void print_phases(const unsigned long long* ph_dev, cudaStream_t stream) {
+    std::vector<unsigned long long> t((size_t)kPhaseLen);
+    if (cudaMemcpyAsync(t.data(), ph_dev, sizeof(unsigned long long) * kPhaseLen, cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return;
+    constexpr unsigned long long kTop = 1ull << 63;
+    constexpr int P = 8;   // grid barriers per iteration of the two-pass engine
+    std::vector<std::vector<double>> d(P);
+    std::vector<double> tot;
+    for (int i = 0; i + P < kPhaseLen; ++i) {
+        if (!(t[(size_t)i] & kTop)) continue;
+        bool ok = true;
+        for (int k = 1; k <= P && ok; ++k) {
+            const unsigned long long a = t[(size_t)i + k - 1] & ~kTop, b = t[(size_t)i + k];
+            ok = !(b & kTop) && b > a;
+        }
+        if (!ok) continue;   // an iteration that ended early (stop test) or was not reached
+        for (int k = 1; k <= P; ++k)
+            d[(size_t)k - 1].push_back((double)(t[(size_t)i + k] - (t[(size_t)i + k - 1] & ~kTop)) * 1e-3);
+        tot.push_back((double)(t[(size_t)i + P] - (t[(size_t)i] & ~kTop)) * 1e-3);
+    }
+    if (tot.empty()) return;
+    auto med = [](std::vector<double> v) {
+        std::sort(v.begin(), v.end());
+        return v[v.size() / 2];
+    };
+    fprintf(stderr, "[lls log] CGLS phases, median us over %zu iterations:", tot.size());
+    for (int k = 0; k < P; ++k) fprintf(stderr, " %d:%.1f", k + 1, med(d[(size_t)k]));
+    fprintf(stderr, " total:%.1f\n", med(tot));
 }
 
 // LLS_LOG=1: the stop quantity of every iteration (eta_est for the FP64 target, the forward
@@ -679,7 +723,8 @@ static int finish_info(const QrWs& w, cudaEvent_t* ev, lls_info* info, cudaStrea
     LLS_CUDA_TRY(cudaMemcpyAsync(hinfo, w.dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, stream));
     LLS_CUDA_TRY(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     LLS_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (hist && log_enabled()) print_history(hist, (int)hinfo[0], m, n, stream);
+    if (hist && log_level() >= 1) print_history(hist, (int)hinfo[0], m, n, stream);
+    if (hist && log_level() >= 2) print_phases(reinterpret_cast<const unsigned long long*>(hist + kHistLen), stream);
     cudaEventElapsedTime(&info->qr_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&info->krylov_ms, ev[1], ev[2]);
     info->iters = (int)hinfo[0];

@@ -144,11 +144,13 @@ struct KrylovCall {
     double* dev_info;       // [iters, eta, fwd, res, atr, anorm, xnorm, status]
     int x_zero = 1;         // 1: start from x = 0; 0: start from the x the vector holds
     double* hist = nullptr; // kHistLen doubles: the stop quantity after each iteration, or null
+    unsigned long long* phases = nullptr;   // kPhaseLen entries: CGLS phase log (LLS_LOG=2), or null
     int ctas = 0;           // CTAs of the persistent kernel, 0 = from the problem size
 };
 // CTAs the Krylov kernel takes for an m x n problem when not told otherwise.
 int krylov_default_ctas(int m, int n);
 constexpr int kHistLen = 4096;   // iterations whose stop quantity the history keeps
+constexpr int kPhaseLen = 4096;  // entries of the CGLS phase log
 // one_pass: room for the one-pass CGLS engine's row-block copy of A (used when n <= 4096).
 size_t krylov_scratch_bytes(int m, int n, int grid, bool one_pass = false);
 int krylov_solve(const KrylovCall& c, cudaStream_t st);

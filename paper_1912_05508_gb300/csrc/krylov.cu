@@ -75,6 +75,7 @@ struct KArgs {
                                      // vectors are produced so no CTA re-splits a whole vector
     int vec_floats;              // floats reserved at the start of dynamic smem for vectors
     double* hist;                // the stop quantity after each iteration (kHistLen entries), or null
+    unsigned long long* phases;  // CGLS phase log (kPhaseLen entries), or null
 };
 
 // The stop quantity of iteration `it` into the history (block 0, thread 0; the value is the
@@ -649,7 +650,16 @@ __device__ double reduce_u(const KArgs& a, double alpha, bool use_v1, int gtid, 
     return sq;
 }
 
-#define KB_SYNC() do { if (!grid_barrier(a.bar, gridDim.x, a.err)) return; } while (0)
+#define KB_SYNC() do { if (!grid_barrier(a.bar, gridDim.x, a.err)) return; KB_AFTER_SYNC; } while (0)
+#define KB_AFTER_SYNC ((void)0)
+
+// Phase log of the CGLS iteration (LLS_LOG=2): CTA 0 appends %globaltimer after every grid
+// barrier and, with the top bit set, at the top of every iteration of the loop.
+__device__ __forceinline__ void phase_stamp(const KArgs& a, int& ph, bool top) {
+    if (a.phases && blockIdx.x == 0 && threadIdx.x == 0 && ph < kPhaseLen)
+        a.phases[ph] = globaltimer_ns() | (top ? (1ull << 63) : 0ull);
+    ++ph;
+}
 
 // NC > 0: fused engine with NC columns per thread; NC == 0: two-pass engine.
 template <int NC>
@@ -661,6 +671,9 @@ cgls_kernel(KArgs a) {
     int iters = 0, status = 1, apasses = 0, mpasses = 0;
     double eta = 0.0, fwd = 0.0, rn2 = 0.0, un2 = 0.0, xn2 = 0.0, gamma = 0.0;
     bool xzero = a.x_zero != 0;
+    int ph = 0;                    // entries of the phase log so far
+#undef KB_AFTER_SYNC
+#define KB_AFTER_SYNC phase_stamp(a, ph, false)
 
     for (int restart = 0; restart <= kMaxRestarts; ++restart) {
         // ---- true residual r = b - A x ----
@@ -767,6 +780,7 @@ cgls_kernel(KArgs a) {
 
         // ---- iterate ----
         while (iters < a.max_iter) {
+            phase_stamp(a, ph, true);
             // t = M p
             stage_df(a.pdf, a.n);
             tri_gemv(a.Mt, a.n, false, a.t, a.tdf);
@@ -869,6 +883,9 @@ cgls_kernel(KArgs a) {
         a.info[11] = mpasses;
     }
 }
+
+#undef KB_AFTER_SYNC
+#define KB_AFTER_SYNC ((void)0)
 
 // ---------------------------------------------------------------------------------------
 // LSQR (Paige and Saunders; Sec. 5 names it as the stable equivalent of CGLS) on the same
@@ -1452,6 +1469,7 @@ int krylov_solve(const KrylovCall& c, cudaStream_t st) {
     a.mnorm2 = c.dev_info + 9;
     a.tol = c.tol; a.max_iter = c.max_iter; a.target = c.target; a.x_zero = c.x_zero;
     a.hist = c.hist;
+    a.phases = c.phases;
     a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
     char* base = (char*)c.scratch;
     if (nc > 0) {
@@ -1482,6 +1500,7 @@ int adjoint_solve(const AdjointCall& c, cudaStream_t st) {
     a.err = c.dev_err; a.info = c.dev_info; a.anorm2 = nullptr; a.mnorm2 = nullptr;
     a.tol = c.tol; a.max_iter = c.max_iter; a.target = LLS_TARGET_FP64; a.x_zero = 1;
     a.hist = nullptr;
+    a.phases = nullptr;
     a.aligned16 = (((uintptr_t)c.A & 15) == 0) && (c.lda % 4 == 0);
     a.vec_floats = 2 * at_rows_cap(c.n);
     const size_t smem = sizeof(float) * (size_t)a.vec_floats;
