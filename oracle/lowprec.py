@@ -28,10 +28,6 @@ def round_fp16(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
 
 
-def round_fp32(x: np.ndarray) -> np.ndarray:
-    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
-
-
 def round_bf16(x: np.ndarray) -> np.ndarray:
     """Round to bfloat16 (8-bit significand), round-to-nearest-even.
 
